@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Throughput of the prismatic DG hot path on one GB300 (or N independent replicas).
+
+Metric: 3D DoF-updates per second = 6 P n_fields3D / (time of one full internal
+step), P prisms, reported for the mixed FP32/FP64 form (``value``) with the plain
+FP64 form beside it, plus the achieved fraction of the HBM roofline of the
+dominant kernel.  ``python bench.py --gpus N --steps K --warmup W``; under
+torchrun every rank runs its own replica (independent problem, weak scaling) and
+rank 0 prints one JSON line.  ``--impl reference`` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "3D DoF-updates/s per time step (mixed vs FP64, 1 GB300), % of HBM roofline"
+UNIT = "DoF-updates/s"
+
+
+# ---------------------------------------------------------------------------
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="basin_tracer", choices=sorted(wl.WORKLOADS))
+    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), src="measured")
+    return dict(hbm_gbs=6800.0, src="fallback")
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1])); mx.append(float(r[2]))
+            except Exception:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"])
+        load = [s for s in sm if s > 0.5 * max(sm)]
+        return dict(sm_mhz=statistics.median(load), sm_max_mhz=max(mx), reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+# ---------------------------------------------------------------------------
+def tracer_inputs(name: str):
+    W = wl.WORKLOADS[name]
+    m = W["mesh"]()
+    if name == "square_tracer":
+        u, v = wl.c1_velocity(m)
+        T = wl.c1_tracer(m)
+    else:
+        u, v = wl.basin_velocity(m)
+        T = wl.c2_initial_state(m)["T"]
+    return m, W, dict(U=u, V=v, T=T, ETA=np.zeros(3 * m.n_tri))
+
+
+def stage_bytes(m, esz: int) -> float:
+    """Algorithmic bytes of one fused tracer-stage launch (average of the 3 stages):
+    per prism the stage reads T_p and T_n (stage 1: one array), u, v, W and writes T,
+    34 values on average; per triangle the geometry, adjacency and both elevations."""
+    P, nt = m.n_prisms, m.n_tri
+    per_prism = 34.0 * esz
+    per_tri = (252.0 if esz == 8 else 172.0)
+    return P * per_prism + nt * per_tri
+
+
+def run_ours(args, rank: int, world: int):
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2605_16082_gb300 import slim
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    m, W, fields = tracer_inputs(args.workload)
+    dt = W["dt"]
+    dofs = 6.0 * m.n_prisms * 1
+    precs = {"both": ["mixed", "fp64"], "mixed": ["mixed"], "fp64": ["fp64"]}[args.precision]
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    res = {}
+    clocks = None
+    for pname in precs:
+        prec = slim.SLIM_MIXED if pname == "mixed" else slim.SLIM_FP64
+        par = slim.slim_params_default(kappa_v=W["kappa_v"])
+        mod = slim.Model(m, prec, par)
+        for k, v in fields.items():
+            mod.upload(k, v)
+        t = 0.0
+        for _ in range(args.warmup):
+            slim.slim_step(mod.state, t, dt, sh); t += dt
+        torch.cuda.synchronize()
+        barrier(world)
+        sampler = ClockSampler(dev) if pname == precs[0] else None
+        if sampler:
+            sampler.start()
+        n_k = slim.slim_step_kernel_count(mod.state)
+        slim.slim_profile_begin(mod.state, n_k * args.steps + 8)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier(world)
+        e0.record(stream)
+        for _ in range(args.steps):
+            slim.slim_step(mod.state, t, dt, sh); t += dt
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = e0.elapsed_time(e1)
+        phases = slim.slim_profile_end(mod.state)
+        if sampler:
+            clocks = sampler.stop()
+        slim.slim_state_check(mod.state, sh)
+        ms = allmax(ms, world)
+        ms_step = ms / args.steps
+        dom = max(phases, key=lambda k: phases[k][0])
+        dom_ms = phases[dom][0] / phases[dom][1]
+        esz = 8 if pname == "fp64" else 4
+        ab = stage_bytes(m, esz) if dom == "tracer_stage" else float("nan")
+        r = dict(value=world * dofs / (ms_step / 1e3), ms_per_step=ms_step, phases=phases,
+                 dominant=dom, dom_ms=dom_ms, alg_bytes=ab, gpu_launches=n_k * args.steps)
+        # end to end through the public API with pinned host buffers
+        if not args.no_e2e:
+            pin = {k: torch.tensor(v, dtype=torch.float64).pin_memory() for k, v in fields.items()}
+            outT = torch.empty(6 * m.n_prisms, dtype=torch.float64).pin_memory()
+            outE = torch.empty(3 * m.n_tri, dtype=torch.float64).pin_memory()
+            ids = {k: slim.FIELD[k] for k in pin}
+            torch.cuda.synchronize()
+            barrier(world)
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                for k, buf in pin.items():
+                    slim.slim_state_upload_ptr(mod.state, ids[k], buf.data_ptr(), sh)
+                slim.slim_step(mod.state, t, dt, sh); t += dt
+                slim.slim_state_download_ptr(mod.state, slim.FIELD["T"], outT.data_ptr(), sh)
+                slim.slim_state_download_ptr(mod.state, slim.FIELD["ETA"], outE.data_ptr(), sh)
+            torch.cuda.synchronize()
+            barrier(world)
+            e2e_s = allmax(time.perf_counter() - t0, world) / args.steps
+            r["e2e"] = dict(value=world * dofs / e2e_s, unit=UNIT,
+                            h2d_bytes_per_step=int(sum(b.numel() * 8 for b in pin.values())),
+                            d2h_bytes_per_step=int((outT.numel() + outE.numel()) * 8))
+        mod.close()
+        res[pname] = r
+    return m, res, clocks
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(x: float, world: int) -> float:
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(args, m, W, seconds: float):
+    """The oracle as it stands on a bounded sample of the workload: a compact patch
+    of consecutive (Hilbert-ordered) columns, stepped until ``seconds`` elapse."""
+    from oracle import tracer as otr
+    from oracle.mesh import OMesh
+    from workloads.meshes import Mesh
+    n_patch = min(m.n_tri, 1200)
+    idx = np.arange(n_patch)
+    bnd = m.bnd[idx].copy()
+    sub = Mesh(xy=m.xy, tri=m.tri[idx], h_tri=m.h_tri[idx], n_layers=m.n_layers[idx], bnd=bnd,
+               levels=m.levels)
+    # cut edges become walls; open-boundary edges stay open
+    topo = wl.meshes._tag_boundary(sub.xy, sub.tri, None)
+    sub.bnd = np.where((topo == 1) & (bnd == 2), 2, topo).astype(np.int8)
+    om = OMesh(sub)
+    if args.workload == "square_tracer":
+        u, v = wl.c1_velocity(sub); T = wl.c1_tracer(sub)
+    else:
+        u, v = wl.basin_velocity(sub); T = wl.c2_initial_state(sub)["T"]
+    P = om.P
+    u, v, T = otr.to3(u, P), otr.to3(v, P), otr.to3(T, P)
+    eta = np.zeros((3, sub.n_tri))
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        eta, T, _ = otr.tracer_step(om, eta, T, u, v, W["dt"], W["kappa_v"])
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    per_step = el / steps
+    return dict(value=6.0 * P / per_step, unit=UNIT, cores=1, kind="oracle",
+                sample=f"{sub.n_tri} columns x {int(sub.n_layers.max())} layers ({P} prisms) of "
+                       f"{args.workload}, {steps} steps in {el:.1f} s, numpy FP64, 1 thread")
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    W = wl.WORKLOADS[args.workload]
+    cfg = dict(workload=args.workload, scheme=W["scheme"], dt=W.get("dt"),
+               l2="working set per step > L2 (no flush needed)")
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        m = W["mesh"]()
+        cfg.update(n_tri=m.n_tri, n_prisms=m.n_prisms, layers=int(m.n_layers.max()))
+        cb = oracle_sample(args, m, W, max(2.0, args.cpu_seconds * args.steps / 20.0))
+        line = dict(impl="reference", metric=METRIC, value=cb["value"], unit=UNIT, n_gpus=args.gpus,
+                    steps=args.steps, warmup=args.warmup, ms_per_step=6.0 * m.n_prisms / cb["value"] * 1e3,
+                    higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                    data="synthetic", config=cfg, cpu_baseline=cb,
+                    e2e=dict(value=cb["value"], unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+        print(json.dumps(line))
+        return
+    m, res, clocks = run_ours(args, rank, world)
+    cfg.update(n_tri=m.n_tri, n_prisms=m.n_prisms, layers=int(m.n_layers.max()),
+               parallelism=f"replicas{world}")
+    if rank != 0:
+        return
+    pk = peaks()
+    head = res.get("mixed") or res["fp64"]
+    hname = "mixed" if "mixed" in res else "fp64"
+
+    def roof(r):
+        ach = r["alg_bytes"] / (r["dom_ms"] / 1e3) / 1e9
+        return dict(kernel=r["dominant"], bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s",
+                    frac=ach / pk["hbm_gbs"], traffic=None, peak_src=pk["src"],
+                    launch_ms=r["dom_ms"])
+
+    line = dict(metric=METRIC, value=head["value"], unit=UNIT, n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=head["ms_per_step"], higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f32+f64" if hname == "mixed" else "f64",
+                data="synthetic", config=cfg, roofline=roof(head), clocks=clocks,
+                gpu_launches=head["gpu_launches"], phases_ms={k: v[0] for k, v in head["phases"].items()})
+    if "e2e" in head:
+        line["e2e"] = head["e2e"]
+    if "fp64" in res and hname != "fp64":
+        f = res["fp64"]
+        line["fp64"] = dict(value=f["value"], ms_per_step=f["ms_per_step"], roofline=roof(f),
+                            e2e=f.get("e2e"), phases_ms={k: v[0] for k, v in f["phases"].items()})
+    if not args.no_cpu:
+        line["cpu_baseline"] = oracle_sample(args, m, W, args.cpu_seconds)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

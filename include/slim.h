@@ -1,0 +1,255 @@
+/*
+ * slim.h - C ABI of the GB300 (sm_103a) implementation of the 3D discontinuous
+ * Galerkin ocean-model hot path of arXiv 2605.16082 (SLIM): the element-wise
+ * residual of the extruded prismatic P1xP1 mesh, the depth integration that
+ * couples the 3D and 2D modes, and the column-wise implicit vertical solves.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Mesh.  n_tri counter-clockwise triangles, each extruded into a column of
+ *   n_layers[t] prisms (Sec. 1, Sec. 2.1).  Prism p = col_off[t] + k is layer k
+ *   (k = 0 at the surface) of column t, col_off the exclusive prefix sum of
+ *   n_layers.  P = total prisms.  Edge e of a triangle joins its vertices e and
+ *   (e+1) % 3.
+ * 3D nodal fields (6P values): node (c, a, p) at index (c*3 + a)*P + p, c = 0 the
+ *   top node and c = 1 the bottom node of prism p, a the triangle vertex.  The
+ *   six node planes stream contiguously down every column (the structure-of-
+ *   arrays order of Sec. 2.1, field -> node -> column -> layer).
+ * 2D nodal fields (3*n_tri values): vertex a of triangle t at index a*n_tri + t.
+ * Host pointers are read (or written) during the call only and stay owned by
+ *   the caller.  Device pointers ("_dev") are caller-owned, contiguous, and must
+ *   hold the stated number of elements of the state's compute type: double for
+ *   SLIM_FP64, float for SLIM_MIXED (except where a signature says double).
+ * Streams are cudaStream_t passed as void* (0 = legacy default stream).  Work is
+ *   enqueued asynchronously unless stated otherwise.
+ * Errors: every call returns slim_status; nothing is thrown across the ABI.
+ *   slim_last_error() gives a human-readable message for the calling thread.
+ *   Device-side conditions (non-finite values, exhausted waits) are latched in a
+ *   device flag and reported by slim_state_check().
+ * Thread safety: calls on different states are independent; calls on one state
+ *   must not overlap on the host.
+ */
+#ifndef SLIM_H
+#define SLIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct slim_mesh slim_mesh;
+typedef struct slim_state slim_state;
+
+typedef enum {
+  SLIM_OK = 0,
+  SLIM_ERR_ARG = 1,        /* invalid argument (null pointer, size, enum)          */
+  SLIM_ERR_MESH = 2,       /* inconsistent mesh (orientation, adjacency, layers)   */
+  SLIM_ERR_CUDA = 3,       /* a CUDA runtime call failed                            */
+  SLIM_ERR_OOM = 4,        /* device allocation failed                              */
+  SLIM_ERR_NONFINITE = 5,  /* a kernel produced NaN or Inf                          */
+  SLIM_ERR_CFL = 6,        /* time step above the stability estimate                */
+  SLIM_ERR_BOUNDS = 7,     /* an index left its range                               */
+  SLIM_ERR_TIMEOUT = 8,    /* a bounded device wait gave up                         */
+  SLIM_ERR_UNSUPPORTED = 9 /* combination not available (scheme, precision, field)  */
+} slim_status;
+
+typedef enum { SLIM_FP64 = 0, SLIM_MIXED = 1 } slim_precision;
+
+/* Time scheme of slim_step. */
+typedef enum {
+  /* transport frozen over the step, SSP-RK3 explicit horizontal terms with an
+     implicit vertical solve in every stage (tracer workload) */
+  SLIM_SCHEME_TRACER = 0,
+  /* two-stage split-IMEX internal step with subcycled 2D external mode
+     (Sec. 2, Eqs. 11-14) */
+  SLIM_SCHEME_SPLIT = 1
+} slim_scheme;
+
+/* Field identifiers for upload / download. */
+enum {
+  SLIM_FIELD_T = 0,    /* 3D temperature (or the passive tracer)                      */
+  SLIM_FIELD_S = 1,    /* 3D salinity                                                 */
+  SLIM_FIELD_U = 2,    /* 3D horizontal velocity, x component [m/s]                   */
+  SLIM_FIELD_V = 3,    /* 3D horizontal velocity, y component                         */
+  SLIM_FIELD_W = 4,    /* 3D vertex-weighted vertical flux of the last continuity solve */
+  SLIM_FIELD_R_X = 5,  /* 3D horizontal baroclinic pressure gradient r, x (Eq. 8)     */
+  SLIM_FIELD_R_Y = 6,
+  SLIM_FIELD_T_EXT = 7, /* open-boundary exterior profile of T (upload only resets it) */
+  SLIM_FIELD_S_EXT = 8, /* open-boundary exterior profile of S                          */
+  SLIM_FIELD_ETA = 16, /* 2D elevation [m]                                            */
+  SLIM_FIELD_QX = 17,  /* 2D depth-integrated transport [m^2/s]                       */
+  SLIM_FIELD_QY = 18,
+  SLIM_FIELD_ETA_NEXT = 19, /* 2D elevation at the end of the last continuity solve  */
+  SLIM_FIELD_QBAR_X = 20,   /* 2D time-averaged transport of the last external run    */
+  SLIM_FIELD_QBAR_Y = 21
+};
+
+typedef struct slim_params {
+  double g;            /* gravity [m/s^2]                                  */
+  double rho0;         /* reference density [kg/m^3]                       */
+  double coriolis_f;   /* Coriolis parameter [1/s]                         */
+  double eos_alpha;    /* linear EOS thermal expansion [1/K]               */
+  double eos_beta;     /* linear EOS haline contraction [1/psu]            */
+  double eos_T0, eos_S0;
+  double kappa_v;      /* vertical tracer diffusivity [m^2/s]              */
+  double nu_v;         /* vertical viscosity [m^2/s]                       */
+  double kappa_h;      /* horizontal tracer diffusivity [m^2/s]            */
+  double nu_h;         /* horizontal viscosity [m^2/s]                     */
+  double drag_cd;      /* quadratic bottom drag coefficient                */
+  double flux_top;     /* prescribed kappa dT/dz at the surface (tracer)   */
+  double flux_bot;     /* prescribed kappa dT/dz at the bed (tracer)       */
+  double penalty_v;    /* vertical SIPG penalty factor (sigma = p kappa / min dz) */
+  double penalty_h;    /* horizontal SIPG penalty factor (sigma = p nu / r_in)    */
+  double tide_amp;     /* open-boundary elevation amplitude [m]            */
+  double tide_period;  /* open-boundary elevation period [s]               */
+  int scheme;          /* slim_scheme                                      */
+  int n_sub;           /* external-mode steps per internal step (split)    */
+  int tile_prisms;     /* prisms per thread block (0 = default 256)        */
+  int check_every;     /* slim_step checks the device error flag every n steps (0 = never) */
+} slim_params;
+
+/* Fill *p with the defaults: g 9.81, rho0 1025, f 1e-4, alpha 2e-4, beta 7.6e-4,
+   T0 10, S0 35, kappa_v = nu_v = 1e-3, kappa_h = nu_h = 0, Cd 2.5e-3, no boundary
+   fluxes, penalty_v 4, penalty_h 6, tide 1 m / 44712 s, SLIM_SCHEME_TRACER,
+   n_sub 20, tile 256, check_every 0.  Returns SLIM_ERR_ARG for a null pointer. */
+slim_status slim_params_default(slim_params* p);
+
+const char* slim_status_string(slim_status s);
+/* Message of the last failing call on this thread ("" if none). */
+const char* slim_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Mesh (Sec. 1 "prismatic mesh made by extruding the 2D mesh"; Sec. 2.1)
+ *
+ * xy        [2*n_vert]  vertex coordinates, x0 y0 x1 y1 ...
+ * tri       [3*n_tri]   counter-clockwise vertex indices
+ * h_tri     [3*n_tri]   rest water depth (> 0) at each triangle vertex, tri-major
+ *                       (t*3 + a); equal across triangles for sigma layers, a
+ *                       staircase depth for z-levels
+ * n_layers  [n_tri]     layers of each column, 1..SLIM_MAX_LAYERS
+ * levels    [n_levels]  rest interface depths 0 = z_0 > z_1 > ... for z-level
+ *                       layering (interface k of a column with N layers sits at
+ *                       levels[k] for k < N and at -h at the bed), or NULL for
+ *                       uniform sigma layers
+ * bnd       [3*n_tri]   per edge (t*3 + e): 0 interior, 1 wall, 2 open boundary
+ *
+ * Builds the edge adjacency, the per-triangle geometry and the thread-block
+ * tiling on the host and copies them to the current CUDA device.  Errors:
+ * SLIM_ERR_ARG (null/size), SLIM_ERR_MESH (clockwise triangle, edge shared by
+ * more than two triangles, interior edge tagged as boundary or vice versa),
+ * SLIM_ERR_OOM / SLIM_ERR_CUDA.  On error *out is NULL.
+ * ------------------------------------------------------------------------- */
+#define SLIM_MAX_LAYERS 128
+slim_status slim_mesh_create(const double* xy, int n_vert, const int* tri, int n_tri,
+                             const double* h_tri, const int* n_layers, const double* levels,
+                             int n_levels, const signed char* bnd, int tile_prisms,
+                             slim_mesh** out);
+void slim_mesh_destroy(slim_mesh* m);
+/* Sizes of a mesh (any pointer may be NULL). */
+slim_status slim_mesh_info(const slim_mesh* m, int64_t* n_prisms, int* n_tri, int* max_layers,
+                           int* n_tiles);
+
+/* ---------------------------------------------------------------------------
+ * State: device buffers of all fields of one simulation, in the precision's
+ * compute type (SLIM_MIXED: 3D fields in float, 2D elevation, transport and
+ * their time averages in double).  Fields start at zero.  The mesh must outlive
+ * the state.  Errors: SLIM_ERR_ARG, SLIM_ERR_OOM, SLIM_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+slim_status slim_state_alloc(const slim_mesh* m, slim_precision prec, const slim_params* par,
+                             slim_state** out);
+void slim_state_free(slim_state* s);
+/* Replace the parameters (same scheme); takes effect at the next call. */
+slim_status slim_state_set_params(slim_state* s, const slim_params* par);
+/* Copy a field from host doubles (6P or 3*n_tri values, layout above) into the
+   state, converting to the compute type; enqueued on the stream, the host
+   buffer must stay valid until the stream reaches the copy (synchronous for
+   pageable memory).  Uploading T or S also sets the open-boundary exterior
+   profile of that tracer. */
+slim_status slim_state_upload(slim_state* s, int field, const double* host, void* stream);
+/* Copy a field to host doubles; synchronises the stream. */
+slim_status slim_state_download(slim_state* s, int field, double* host, void* stream);
+/* Device address and element size (4 or 8) of a field buffer of the state. */
+slim_status slim_state_field_ptr(slim_state* s, int field, void** dev, int* elem_size);
+/* Read and clear the device error flag (synchronises the stream). */
+slim_status slim_state_check(slim_state* s, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Hot-path operations
+ * ------------------------------------------------------------------------- */
+
+/* slim_rhs3d: horizontal residual of a 3D tracer field (Eq. 6, horizontal part):
+ *   out[c,a,p] = int_K q T . grad(phi_a) psi_c  -  sum_faces int phi_a psi_c (q.n)^ T^
+ * with the layer transport q = (dz/2) u of the state's velocity at the state's
+ * elevation, face transport averaged over both sides, T^ upwind at the face
+ * quadrature points, no flux through walls.  field: SLIM_FIELD_T or _S.
+ * out_dev: 6P elements of the compute type. */
+slim_status slim_rhs3d(slim_state* s, int field, void* out_dev, void* stream);
+
+/* slim_continuity: with the transport frozen at the state's elevation eta,
+ * (i) the depth-integrated continuity (Eq. 2): (J_h/6)(eta' - eta)/dt equals the
+ *     column sum of the horizontal residual of T = 1, written to SLIM_FIELD_ETA_NEXT
+ *     in double (FP64 in both precisions);
+ * (ii) the vertical flux of every vertex column from the bottom-up column system
+ *     of Eq. 17 (printed D_vd pattern), written to SLIM_FIELD_W.
+ * The state's eta is not modified. */
+slim_status slim_continuity(slim_state* s, double dt, void* stream);
+
+/* slim_rhs2d: for SLIM_SCHEME_TRACER, the depth-integrated horizontal residual of
+ * T = 1 per 2D node (the right-hand side of Eq. 2 in weak form), 3*n_tri doubles.
+ * For SLIM_SCHEME_SPLIT, the 2D external-mode residual (mass, then the two
+ * momentum components: 9*n_tri doubles) at time t of the state's eta, Qx, Qy
+ * with the last 3D source term. */
+slim_status slim_rhs2d(slim_state* s, double t, double* out_dev, void* stream);
+
+/* slim_vertical_solve: one implicit vertical solve per vertex column,
+ *   (M - beta_dt A) x = rhs + beta_dt b
+ * M the lumped 2x2-per-layer mass at the state's elevation, A the vertical
+ * upwind advection by the state's W plus SIPG diffusion (kappa_v for T/S, nu_v
+ * for U/V), b the prescribed boundary fluxes (Sec. 2.4 system, 2x2 blocks per
+ * layer).  rhs_dev, out_dev: 6P elements of the compute type; they may alias. */
+slim_status slim_vertical_solve(slim_state* s, int field, double beta_dt, const void* rhs_dev,
+                                void* out_dev, void* stream);
+
+/* slim_step: one complete internal step t -> t + dt of the state's scheme.
+ * SLIM_SCHEME_TRACER: continuity, then three SSP-RK3 stages for T, then eta <-
+ * eta'.  SLIM_SCHEME_SPLIT: the two-stage split-IMEX step with 2D subcycles. */
+slim_status slim_step(slim_state* s, double t, double dt, void* stream);
+
+/* slim_tracer_mass: sum over all nodes of (M T) for field T or S at the state's
+ * elevation, accumulated in double with compensated (Neumaier) sums in a fixed
+ * order (deterministic).  Writes one double to *mass_host; synchronises. */
+slim_status slim_tracer_mass(slim_state* s, int field, double* mass_host, void* stream);
+
+/* Number of kernels slim_step launches per call (for launch accounting). */
+int slim_step_kernel_count(const slim_state* s);
+
+/* ---------------------------------------------------------------------------
+ * Phase timing: while profiling is on, slim_step records a CUDA event pair on
+ * its stream around every kernel it launches, tagged with the phase below.
+ * ------------------------------------------------------------------------- */
+enum {
+  SLIM_PHASE_CONTINUITY = 0,   /* elevation update + vertical flux (Eq. 2, Eq. 17)   */
+  SLIM_PHASE_TRACER_STAGE = 1, /* fused horizontal residual + vertical solve         */
+  SLIM_PHASE_HPG = 2,          /* density + baroclinic pressure gradient (Alg. 1)    */
+  SLIM_PHASE_MOM_PRED = 3,     /* 3D horizontal momentum prediction + vertical sum   */
+  SLIM_PHASE_EXT2D = 4,        /* 2D external-mode stages                             */
+  SLIM_PHASE_MOMENTUM = 5,     /* 3D momentum update (implicit or explicit)          */
+  SLIM_PHASE_TRACERS = 6,      /* 3D T, S update (implicit or explicit)              */
+  SLIM_PHASE_MISC = 7,         /* small 2D kernels and copies                        */
+  SLIM_PHASE_COUNT = 8
+};
+/* Start recording (at most max_launches kernel launches; later ones are not
+   timed).  Errors: SLIM_ERR_ARG, SLIM_ERR_CUDA. */
+slim_status slim_profile_begin(slim_state* s, int max_launches);
+/* Synchronise the recorded events, write the summed milliseconds and the launch
+   count of every phase to ms[SLIM_PHASE_COUNT] and launches[SLIM_PHASE_COUNT]
+   (either may be NULL) and stop recording. */
+slim_status slim_profile_end(slim_state* s, double* ms, int* launches);
+const char* slim_phase_name(int phase);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLIM_H */

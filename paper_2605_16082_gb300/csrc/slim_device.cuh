@@ -1,0 +1,295 @@
+// Device building blocks of the prismatic P1xP1 DG hot path (sm_103a).
+//
+// Everything here works on one prism (thread per prism) or one vertex column
+// (thread per column) of a thread-block tile: a run of consecutive triangles
+// whose columns hold at most TP prisms, staged in shared memory so that the
+// six node planes of every field are read and written coalesced.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "slim_internal.h"
+
+namespace slim {
+
+// Gauss-Legendre points on [0,1]: (1 -/+ 1/sqrt(3)) / 2
+#define SLIM_GL1 0.21132486540518711775
+#define SLIM_GL2 0.78867513459481288225
+
+template <typename R> struct Geo;
+template <> struct Geo<double> {
+  static __device__ __forceinline__ double jh(const DevMesh& m, int t) { return m.jh[t]; }
+  static __device__ __forceinline__ double gx(const DevMesh& m, int i) { return m.gx[i]; }
+  static __device__ __forceinline__ double gy(const DevMesh& m, int i) { return m.gy[i]; }
+  static __device__ __forceinline__ double nx(const DevMesh& m, int i) { return m.enx[i]; }
+  static __device__ __forceinline__ double ny(const DevMesh& m, int i) { return m.eny[i]; }
+  static __device__ __forceinline__ double len(const DevMesh& m, int i) { return m.elen[i]; }
+};
+template <> struct Geo<float> {
+  static __device__ __forceinline__ float jh(const DevMesh& m, int t) { return m.jh_f[t]; }
+  static __device__ __forceinline__ float gx(const DevMesh& m, int i) { return m.gx_f[i]; }
+  static __device__ __forceinline__ float gy(const DevMesh& m, int i) { return m.gy_f[i]; }
+  static __device__ __forceinline__ float nx(const DevMesh& m, int i) { return m.enx_f[i]; }
+  static __device__ __forceinline__ float ny(const DevMesh& m, int i) { return m.eny_f[i]; }
+  static __device__ __forceinline__ float len(const DevMesh& m, int i) { return m.elen_f[i]; }
+};
+
+// Rest thickness of layer k of a column of N layers at a vertex of rest depth h:
+// h/N for sigma layers, the level spacing (the column's own depth at the bed)
+// for z-levels.
+__device__ __forceinline__ double dz_rest(const DevMesh& m, double h, int k, int N) {
+  if (m.n_levels == 0) return h / (double)N;
+  double top = m.levels[k];
+  double bot = (k + 1 < N) ? m.levels[k + 1] : -h;
+  return top - bot;
+}
+// Thickness at elevation eta: interfaces stretch with the column, z = eta + (1 + eta/h) zhat.
+__device__ __forceinline__ double dz_at(const DevMesh& m, double h, double eta, int k, int N) {
+  return dz_rest(m, h, k, N) * (1.0 + eta / h);
+}
+
+// ---------------------------------------------------------------------------
+// tile bookkeeping
+// ---------------------------------------------------------------------------
+struct Tile {
+  int t0, nt, p0, np;
+};
+
+template <int TP>
+__device__ __forceinline__ Tile load_tile(const DevMesh& m, int* s_off) {
+  Tile tl;
+  tl.t0 = m.tile_t0[blockIdx.x];
+  tl.nt = m.tile_t0[blockIdx.x + 1] - tl.t0;
+  tl.p0 = m.col_off[tl.t0];
+  for (int i = threadIdx.x; i <= tl.nt; i += TP) s_off[i] = m.col_off[tl.t0 + i] - tl.p0;
+  __syncthreads();
+  tl.np = s_off[tl.nt];
+  return tl;
+}
+
+// local triangle of local prism i (largest j with s_off[j] <= i)
+__device__ __forceinline__ int tile_tri_of(const int* s_off, int nt, int i) {
+  int lo = 0, hi = nt - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (s_off[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// horizontal residual of one prism
+//   out[c][a] = int q T . grad(phi_a) psi_c J_h  -  sum_e int phi_a psi_c (q.n)^ T^
+// q = (dz/2) u nodal, dz at elevation eta_q.  UNIT: T = 1 (continuity).
+// Volume term in closed form: with the P1 mass M2_be = J_h (1 + d_be)/24 and the
+// triple integrals G3_dfc = int psi_d psi_f psi_c (1/2 if d = f = c, else 1/6),
+//   X_c = sum_{d,f} G3_dfc sum_{b,e} M2_be q_bd T_ef,   out_vol[c][a] = grad(phi_a) . X_c
+// Lateral faces: 2 x 2 Gauss points, mean transport of both sides, upwind T.
+// ---------------------------------------------------------------------------
+template <typename R, bool UNIT>
+__device__ __forceinline__ void prism_rh(const DevMesh& m, int t, int k, int p, int N,
+                                         const R* __restrict__ U, const R* __restrict__ V,
+                                         const R* __restrict__ T, const R* __restrict__ Text,
+                                         const double* __restrict__ eta_q, R out[2][3]) {
+  const int nt = m.n_tri, P = m.P;
+  R qx[2][3], qy[2][3], Tv[2][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double h = m.h[a * nt + t];
+    R hz = (R)(0.5 * dz_at(m, h, eta_q[a * nt + t], k, N));
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      int idx = (c * 3 + a) * P + p;
+      qx[c][a] = hz * U[idx];
+      qy[c][a] = hz * V[idx];
+      Tv[c][a] = UNIT ? (R)1 : T[idx];
+    }
+  }
+  const R jh = Geo<R>::jh(m, t);
+  // volume term
+  R Xx[2], Xy[2];
+  {
+    R Yx[2][2], Yy[2][2];
+    const R w24 = jh * (R)(1.0 / 24.0);
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      R sqx = qx[d][0] + qx[d][1] + qx[d][2];
+      R sqy = qy[d][0] + qy[d][1] + qy[d][2];
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        if (UNIT) {
+          Yx[d][f] = (R)4 * w24 * sqx;
+          Yy[d][f] = (R)4 * w24 * sqy;
+        } else {
+          R st = Tv[f][0] + Tv[f][1] + Tv[f][2];
+          R px = qx[d][0] * Tv[f][0] + qx[d][1] * Tv[f][1] + qx[d][2] * Tv[f][2];
+          R py = qy[d][0] * Tv[f][0] + qy[d][1] * Tv[f][1] + qy[d][2] * Tv[f][2];
+          Yx[d][f] = w24 * (sqx * st + px);
+          Yy[d][f] = w24 * (sqy * st + py);
+        }
+      }
+    }
+    const R h2 = (R)0.5, h6 = (R)(1.0 / 6.0);
+    Xx[0] = h2 * Yx[0][0] + h6 * (Yx[0][1] + Yx[1][0] + Yx[1][1]);
+    Xx[1] = h2 * Yx[1][1] + h6 * (Yx[0][0] + Yx[0][1] + Yx[1][0]);
+    Xy[0] = h2 * Yy[0][0] + h6 * (Yy[0][1] + Yy[1][0] + Yy[1][1]);
+    Xy[1] = h2 * Yy[1][1] + h6 * (Yy[0][0] + Yy[0][1] + Yy[1][0]);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R gxa = Geo<R>::gx(m, a * nt + t), gya = Geo<R>::gy(m, a * nt + t);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) out[c][a] = gxa * Xx[c] + gya * Xy[c];
+  }
+  // lateral faces
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int nb = m.nbr[e * nt + t];
+    if (nb == -1) continue;  // wall
+    const int a0 = e, a1 = (e + 1) % 3;
+    const R nxe = Geo<R>::nx(m, e * nt + t), nye = Geo<R>::ny(m, e * nt + t);
+    const R half_len = (R)0.5 * Geo<R>::len(m, e * nt + t);
+    R qo[2][2], To[2][2], qb[2][2], Tb[2][2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      qo[0][c] = qx[c][a0] * nxe + qy[c][a0] * nye;
+      qo[1][c] = qx[c][a1] * nxe + qy[c][a1] * nye;
+      To[0][c] = Tv[c][a0];
+      To[1][c] = Tv[c][a1];
+    }
+    bool has_nb = false;
+    if (nb >= 0) {
+      const int off = m.col_off[nb];
+      const int Nn = m.col_off[nb + 1] - off;
+      if (k >= Nn) continue;  // wall against a shallower neighbour column
+      has_nb = true;
+      const int pn = off + k;
+      const int loc = m.nloc[e * nt + t];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int l = j ? ((loc >> 2) & 3) : (loc & 3);
+        const R hz = (R)(0.5 * dz_at(m, m.h[l * nt + nb], eta_q[l * nt + nb], k, Nn));
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int idx = (c * 3 + l) * P + pn;
+          qb[j][c] = hz * (U[idx] * nxe + V[idx] * nye);
+          Tb[j][c] = UNIT ? (R)1 : T[idx];
+        }
+      }
+    } else {  // open boundary: interior transport, exterior tracer on inflow
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          qb[j][c] = qo[j][c];
+          Tb[j][c] = (UNIT || Text == nullptr) ? To[j][c]
+                                               : Text[(c * 3 + (j ? a1 : a0)) * P + p];
+        }
+    }
+#pragma unroll
+    for (int gs = 0; gs < 2; ++gs) {
+      const R b0 = gs ? (R)SLIM_GL1 : (R)SLIM_GL2;  // basis of vertex a0 along the edge
+      const R b1 = gs ? (R)SLIM_GL2 : (R)SLIM_GL1;
+#pragma unroll
+      for (int gz = 0; gz < 2; ++gz) {
+        const R z0 = gz ? (R)SLIM_GL2 : (R)SLIM_GL1;  // psi_top at the point
+        const R z1 = gz ? (R)SLIM_GL1 : (R)SLIM_GL2;
+        const R B00 = b0 * z0, B01 = b0 * z1, B10 = b1 * z0, B11 = b1 * z1;
+        const R qno = B00 * qo[0][0] + B01 * qo[0][1] + B10 * qo[1][0] + B11 * qo[1][1];
+        R qn = qno;
+        if (has_nb) {
+          const R qnb = B00 * qb[0][0] + B01 * qb[0][1] + B10 * qb[1][0] + B11 * qb[1][1];
+          qn = (R)0.5 * (qno + qnb);
+        }
+        R Tup;
+        if (UNIT) {
+          Tup = (R)1;
+        } else if (qn > (R)0) {
+          Tup = B00 * To[0][0] + B01 * To[0][1] + B10 * To[1][0] + B11 * To[1][1];
+        } else {
+          Tup = B00 * Tb[0][0] + B01 * Tb[0][1] + B10 * Tb[1][0] + B11 * Tb[1][1];
+        }
+        const R f = half_len * qn * Tup;
+        out[0][a0] -= f * B00;
+        out[1][a0] -= f * B01;
+        out[0][a1] -= f * B10;
+        out[1][a1] -= f * B11;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// vertical operator: block row k of K = M - bdt A for one vertex column
+// (2x2 blocks; D couples layer k to itself, L to layer k-1, U to layer k+1).
+// A = vertical upwind advection by the vertex-weighted flux W (interface i
+// carries W_{i,top}, 0 on the bed) + omega x SIPG diffusion; M = omega (dz/2) G.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Row {
+  R D[2][2], L[2][2], U[2][2];
+};
+
+template <typename R>
+__device__ __forceinline__ void assemble_row(int k, int N, R omega, R dzm, R dz, R dzp, R W0, R W1,
+                                             R Wn, R kap, R pen, R bdt, Row<R>& row) {
+  R A[2][2] = {{0, 0}, {0, 0}}, AL[2][2] = {{0, 0}, {0, 0}}, AU[2][2] = {{0, 0}, {0, 0}};
+  // advection, volume: A[c][d] = dpsi_c sum_e W_e G_ed
+  const R g0 = (R)(1.0 / 3.0) * ((R)2 * W0 + W1);
+  const R g1 = (R)(1.0 / 3.0) * (W0 + (R)2 * W1);
+  A[0][0] += (R)0.5 * g0; A[0][1] += (R)0.5 * g1;
+  A[1][0] -= (R)0.5 * g0; A[1][1] -= (R)0.5 * g1;
+  // advection, top interface of layer k
+  if (k == 0 || W0 > (R)0) A[0][0] -= W0; else AL[0][1] -= W0;
+  // advection, bottom interface
+  if (k + 1 < N) {
+    if (Wn > (R)0) AU[1][0] += Wn; else A[1][1] += Wn;
+  }
+  // diffusion, element stiffness
+  const R ke = omega * kap / dz;
+  A[0][0] -= ke; A[0][1] += ke; A[1][0] += ke; A[1][1] -= ke;
+  if (k > 0) {
+    const R sg = pen * kap / fmin(dzm, dz);
+    const R cm = kap / ((R)2 * dzm), c0 = kap / ((R)2 * dz);
+    A[0][0] -= omega * (sg - (R)2 * c0);
+    A[0][1] -= omega * c0;
+    A[1][0] -= omega * c0;
+    AL[0][0] -= omega * (-cm);
+    AL[0][1] -= omega * (cm + c0 - sg);
+    AL[1][1] -= omega * (-c0);
+  }
+  if (k + 1 < N) {
+    const R sg = pen * kap / fmin(dz, dzp);
+    const R c0 = kap / ((R)2 * dz), cp = kap / ((R)2 * dzp);
+    A[0][1] -= omega * c0;
+    A[1][0] -= omega * c0;
+    A[1][1] -= omega * (sg - (R)2 * c0);
+    AU[0][0] -= omega * (-c0);
+    AU[1][0] -= omega * (c0 + cp - sg);
+    AU[1][1] -= omega * (-cp);
+  }
+  const R mw = omega * (R)0.5 * dz;
+  const R m2 = mw * (R)(2.0 / 3.0), m1 = mw * (R)(1.0 / 3.0);
+  row.D[0][0] = m2 - bdt * A[0][0];
+  row.D[0][1] = m1 - bdt * A[0][1];
+  row.D[1][0] = m1 - bdt * A[1][0];
+  row.D[1][1] = m2 - bdt * A[1][1];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      row.L[i][j] = -bdt * AL[i][j];
+      row.U[i][j] = -bdt * AU[i][j];
+    }
+}
+
+// 2x2 helpers
+template <typename R>
+__device__ __forceinline__ void inv2(const R a[2][2], R o[2][2]) {
+  const R r = (R)1 / (a[0][0] * a[1][1] - a[0][1] * a[1][0]);
+  o[0][0] = a[1][1] * r; o[0][1] = -a[0][1] * r;
+  o[1][0] = -a[1][0] * r; o[1][1] = a[0][0] * r;
+}
+
+}  // namespace slim

@@ -1,0 +1,55 @@
+// Launchers of the device kernels (host-callable, one per operation and precision).
+#pragma once
+
+#include "slim_internal.h"
+
+namespace slim {
+
+enum : int {
+  SLIM_ERRBIT_NONFINITE = 1,
+  SLIM_ERRBIT_BOUNDS = 2,
+  SLIM_ERRBIT_TIMEOUT = 4,
+};
+
+struct StageParams {
+  double kappa;      // vertical diffusivity of the solved field
+  double penalty;    // vertical SIPG penalty factor
+  double flux_top;   // prescribed kappa dT/dz at the surface
+  double flux_bot;   // prescribed kappa dT/dz at the bed
+};
+
+template <typename R>
+cudaError_t launch_continuity(const DevMesh& m, int TP, const R* U, const R* V, const double* eta,
+                              double* eta_out, R* W, double dt, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_tracer_stage(const DevMesh& m, int TP, const R* U, const R* V, const R* Tn,
+                                const R* Tp, const R* Text, const R* W, R* Tout,
+                                const double* eta_n, const double* eta_np1, double th_p,
+                                double th_s, double alpha, double beta, double dt,
+                                const StageParams& sp, int* err, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_rhs3d(const DevMesh& m, int TP, const R* U, const R* V, const R* T,
+                         const R* Text, const double* eta, R* out, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_vertical_solve(const DevMesh& m, int TP, const R* W, const double* eta,
+                                  const R* rhs, R* out, double bdt, const StageParams& sp,
+                                  int* err, cudaStream_t st);
+
+// rhs2d of the tracer scheme: column sums of R_h(q, 1), 3*n_tri doubles
+template <typename R>
+cudaError_t launch_column_divergence(const DevMesh& m, int TP, const R* U, const R* V,
+                                     const double* eta, double* out, cudaStream_t st);
+
+// mass: block partials (2 doubles per tile: sum, compensation) then one final block
+template <typename R>
+cudaError_t launch_mass(const DevMesh& m, int TP, const R* T, const double* eta, double* partials,
+                        double* result, cudaStream_t st);
+
+// float <-> double conversion
+cudaError_t launch_convert_d2f(const double* in, float* out, size_t n, cudaStream_t st);
+cudaError_t launch_convert_f2d(const float* in, double* out, size_t n, cudaStream_t st);
+
+}  // namespace slim

@@ -1,0 +1,11 @@
+// Split-IMEX internal step with the subcycled 2D external mode.
+#pragma once
+
+#include "slim_internal.h"
+
+namespace slim {
+size_t split_aux2d_len(const DevMesh& m);
+slim_status split_rhs2d(slim_state* s, double t, double* out, cudaStream_t st);
+slim_status split_step(slim_state* s, double t, double dt, cudaStream_t st);
+int split_kernel_count(const slim_state* s);
+}  // namespace slim

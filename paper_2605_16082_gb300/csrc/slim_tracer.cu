@@ -1,0 +1,489 @@
+// Kernels of the tracer path: continuity (vertical flux), SSP-RK3 stage with the
+// fused horizontal residual + implicit vertical solve, standalone residual and
+// vertical solve, compensated tracer-mass reduction.
+//
+// Every kernel runs one thread block per tile of whole columns (at most TP
+// prisms).  Phase 1 is thread-per-prism: coalesced loads of the six node planes,
+// the horizontal residual with lateral-neighbour gathers through the adjacency
+// table (no atomics), results staged in shared memory.  Phase 2 is thread-per-
+// vertex-column: the column recursion or the 2x2-block Thomas sweep on shared
+// memory.  Phase 3 writes the six node planes back coalesced.
+#include <float.h>
+
+#include <algorithm>
+
+#include "slim_device.cuh"
+#include "slim_kernels.h"
+
+namespace slim {
+
+// ---------------------------------------------------------------------------
+// continuity: eta' (FP64) and the vertex-weighted vertical flux W
+//   (J_h/6)(eta' - eta)/dt = sum_column R_h(q, 1)                        (Eq. 2)
+//   F_{k,c} = R_h(q,1)_{k,c} - (J_h/12)(dz'_k - dz_k)/dt
+//   bottom-up D_vd recursion (Eq. 17):  s = 0 at the bed,
+//     W_{k,top} = F_top + F_bot + s,  W_{k,bot} = F_bot - F_top + s,  s = W_{k,top}
+// With DIV_ONLY the kernel writes the column sums (the depth-integrated weak
+// divergence) instead and stops.
+// ---------------------------------------------------------------------------
+template <typename R, int TP, bool DIV_ONLY>
+__global__ void __launch_bounds__(TP) k_continuity(DevMesh m, const R* __restrict__ U,
+                                                   const R* __restrict__ V,
+                                                   const double* __restrict__ eta,
+                                                   double* __restrict__ eta_out,
+                                                   R* __restrict__ W, double dt) {
+  __shared__ int s_off[TP + 1];
+  __shared__ R s_F[6][TP];
+  const Tile tl = load_tile<TP>(m, s_off);
+  const int i = threadIdx.x;
+  if (i < tl.np) {
+    const int lt = tile_tri_of(s_off, tl.nt, i);
+    const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
+    R out[2][3];
+    prism_rh<R, true>(m, t, k, tl.p0 + i, N, U, V, nullptr, nullptr, eta, out);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) s_F[c * 3 + a][i] = out[c][a];
+  }
+  __syncthreads();
+  const int nt = m.n_tri;
+  for (int j = threadIdx.x; j < 3 * tl.nt; j += TP) {
+    const int a = j / tl.nt, lt = j - a * tl.nt;
+    const int t = tl.t0 + lt, base = s_off[lt], N = s_off[lt + 1] - base;
+    double D = 0.0;
+    for (int k = 0; k < N; ++k) D += (double)s_F[a][base + k] + (double)s_F[3 + a][base + k];
+    if (DIV_ONLY) {
+      eta_out[a * nt + t] = D;
+      continue;
+    }
+    const double jh = m.jh[t], h = m.h[a * nt + t];
+    const double e0 = eta[a * nt + t];
+    const double e1 = e0 + dt * D / (jh / 6.0);
+    eta_out[a * nt + t] = e1;
+    // dz'_k - dz_k = dz_rest_k (e1 - e0) / h
+    const double dm_fac = (jh / 12.0) * (e1 - e0) / (h * dt);
+    R s = (R)0;
+    for (int k = N - 1; k >= 0; --k) {
+      const R dm = (R)(dm_fac * dz_rest(m, h, k, N));
+      const R ft = s_F[a][base + k] - dm, fb = s_F[3 + a][base + k] - dm;
+      const R wt = ft + fb + s;
+      const R wb = fb - ft + s;
+      s_F[a][base + k] = wt;
+      s_F[3 + a][base + k] = wb;
+      s = wt;
+    }
+  }
+  if (DIV_ONLY) return;
+  __syncthreads();
+  if (i < tl.np) {
+#pragma unroll
+    for (int r = 0; r < 6; ++r) W[r * m.P + tl.p0 + i] = s_F[r][i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2x2-block Thomas sweep of one vertex column (vertex a of triangle t) on
+// shared memory.  Wt/Wb: vertex-weighted flux at the top/bottom node of every
+// layer; bt/bb: right-hand side, overwritten by the solution; C: 4 scratch rows
+// holding D'^-1 U of the forward sweep.  Indices are local prisms base + k.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void column_thomas(const DevMesh& m, int t, int a, int base, int N,
+                                              double eta_s, const R* Wt, const R* Wb, R* bt,
+                                              R* bb, R* C0, R* C1, R* C2, R* C3, R kap, R pen,
+                                              R bdt, R flux_top, R flux_bot) {
+  const int nt = m.n_tri;
+  const double h = m.h[a * nt + t];
+  const R omega = (R)(m.jh[t] / 6.0);
+  R z0 = 0, z1 = 0;
+  R c00 = 0, c01 = 0, c10 = 0, c11 = 0;
+  R dz = (R)dz_at(m, h, eta_s, 0, N);
+  R dzm = dz;
+  for (int k = 0; k < N; ++k) {
+    const int i = base + k;
+    const R dzp = (k + 1 < N) ? (R)dz_at(m, h, eta_s, k + 1, N) : dz;
+    const R Wn = (k + 1 < N) ? Wt[i + 1] : (R)0;
+    Row<R> row;
+    assemble_row<R>(k, N, omega, dzm, dz, dzp, Wt[i], Wb[i], Wn, kap, pen, bdt, row);
+    R b0 = bt[i], b1 = bb[i];
+    if (k == 0) b0 += bdt * omega * flux_top;
+    if (k == N - 1) b1 -= bdt * omega * flux_bot;
+    // D' = D - L C_{k-1},  y = b - L z_{k-1}
+    R Dp[2][2];
+    Dp[0][0] = row.D[0][0] - (row.L[0][0] * c00 + row.L[0][1] * c10);
+    Dp[0][1] = row.D[0][1] - (row.L[0][0] * c01 + row.L[0][1] * c11);
+    Dp[1][0] = row.D[1][0] - (row.L[1][0] * c00 + row.L[1][1] * c10);
+    Dp[1][1] = row.D[1][1] - (row.L[1][0] * c01 + row.L[1][1] * c11);
+    const R y0 = b0 - (row.L[0][0] * z0 + row.L[0][1] * z1);
+    const R y1 = b1 - (row.L[1][0] * z0 + row.L[1][1] * z1);
+    R Di[2][2];
+    inv2<R>(Dp, Di);
+    z0 = Di[0][0] * y0 + Di[0][1] * y1;
+    z1 = Di[1][0] * y0 + Di[1][1] * y1;
+    c00 = Di[0][0] * row.U[0][0] + Di[0][1] * row.U[1][0];
+    c01 = Di[0][0] * row.U[0][1] + Di[0][1] * row.U[1][1];
+    c10 = Di[1][0] * row.U[0][0] + Di[1][1] * row.U[1][0];
+    c11 = Di[1][0] * row.U[0][1] + Di[1][1] * row.U[1][1];
+    bt[i] = z0;
+    bb[i] = z1;
+    C0[i] = c00; C1[i] = c01; C2[i] = c10; C3[i] = c11;
+    dzm = dz;
+    dz = dzp;
+  }
+  // back substitution x_k = z_k - C_k x_{k+1}
+  R x0 = z0, x1 = z1;
+  for (int k = N - 2; k >= 0; --k) {
+    const int i = base + k;
+    const R n0 = bt[i] - (C0[i] * x0 + C1[i] * x1);
+    const R n1 = bb[i] - (C2[i] * x0 + C3[i] * x1);
+    bt[i] = n0;
+    bb[i] = n1;
+    x0 = n0;
+    x1 = n1;
+  }
+}
+
+// shared-memory carve-up of the solve kernels
+template <typename R, int TP>
+struct SolveSmem {
+  static constexpr size_t off_b = ((TP + 1) * sizeof(int) + 15) / 16 * 16;
+  static constexpr size_t off_W = off_b + 6 * TP * sizeof(R);
+  static constexpr size_t off_C = off_W + 6 * TP * sizeof(R);
+  static constexpr size_t off_eta = off_C + 12 * TP * sizeof(R);
+  static constexpr size_t bytes = off_eta + 3 * TP * sizeof(double);
+};
+
+template <typename R, int TP>
+__device__ __forceinline__ void solve_tile_columns(const DevMesh& m, const Tile& tl,
+                                                   const int* s_off, R* s_b, R* s_W, R* s_C,
+                                                   const double* s_eta, const StageParams& sp,
+                                                   double bdt) {
+  for (int j = threadIdx.x; j < 3 * tl.nt; j += TP) {
+    const int a = j / tl.nt, lt = j - a * tl.nt;
+    const int t = tl.t0 + lt, base = s_off[lt], N = s_off[lt + 1] - base;
+    R* C = s_C + (size_t)a * 4 * TP;
+    column_thomas<R>(m, t, a, base, N, s_eta[a * TP + lt], s_W + a * TP, s_W + (3 + a) * TP,
+                     s_b + a * TP, s_b + (3 + a) * TP, C, C + TP, C + 2 * TP, C + 3 * TP,
+                     (R)sp.kappa, (R)sp.penalty, (R)bdt, (R)sp.flux_top, (R)sp.flux_bot);
+  }
+}
+
+template <typename R, int TP>
+__device__ __forceinline__ void write_tile(const DevMesh& m, const Tile& tl, const R* s_b,
+                                           R* out, int* __restrict__ err) {
+  const int i = threadIdx.x;
+  if (i < tl.np) {
+    bool ok = true;
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      const R x = s_b[r * TP + i];
+      ok &= (bool)isfinite(x);
+      out[(size_t)r * m.P + tl.p0 + i] = x;
+    }
+    if (!ok) atomicOr(err, (int)SLIM_ERRBIT_NONFINITE);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// SSP-RK3 stage (fused): T_out solves, per vertex column,
+//   (M(eta_s) - beta dt A) T_out = alpha M(eta_n) T_n
+//                                  + beta (M(eta_p) T_p + dt R_h(q(eta_n), T_p)) + beta dt b
+// with eta_x = (1 - th_x) eta_n + th_x eta_np1 and M the lumped 2x2 mass.
+// ---------------------------------------------------------------------------
+template <typename R, int TP>
+__global__ void __launch_bounds__(TP) k_tracer_stage(
+    DevMesh m, const R* __restrict__ U, const R* __restrict__ V, const R* Tn,
+    const R* __restrict__ Tp, const R* __restrict__ Text, const R* __restrict__ W,
+    R* Tout, const double* __restrict__ eta_n, const double* __restrict__ eta_np1,
+    double th_p, double th_s, double alpha, double beta, double dt, StageParams sp,
+    int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using L = SolveSmem<R, TP>;
+  int* s_off = reinterpret_cast<int*>(smem);
+  R* s_b = reinterpret_cast<R*>(smem + L::off_b);
+  R* s_W = reinterpret_cast<R*>(smem + L::off_W);
+  R* s_C = reinterpret_cast<R*>(smem + L::off_C);
+  double* s_eta = reinterpret_cast<double*>(smem + L::off_eta);
+  const Tile tl = load_tile<TP>(m, s_off);
+  const int nt = m.n_tri;
+  for (int j = threadIdx.x; j < 3 * tl.nt; j += TP) {
+    const int a = j / tl.nt, lt = j - a * tl.nt, t = tl.t0 + lt;
+    const double en = eta_n[a * nt + t];
+    s_eta[a * TP + lt] = en + th_s * (eta_np1[a * nt + t] - en);
+  }
+  const int i = threadIdx.x;
+  if (i < tl.np) {
+    const int lt = tile_tri_of(s_off, tl.nt, i);
+    const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
+    const int p = tl.p0 + i;
+    R out[2][3];
+    prism_rh<R, false>(m, t, k, p, N, U, V, Tp, Text, eta_n, out);
+    const double w6 = m.jh[t] / 6.0;
+    const R G2 = (R)(2.0 / 3.0), G1 = (R)(1.0 / 3.0);
+    const R al = (R)alpha, be = (R)beta, dtr = (R)dt;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double h = m.h[a * nt + t];
+      const double en = eta_n[a * nt + t];
+      const double ep = en + th_p * (eta_np1[a * nt + t] - en);
+      const R mn = (R)(w6 * 0.5 * dz_at(m, h, en, k, N));
+      const R mp = (R)(w6 * 0.5 * dz_at(m, h, ep, k, N));
+      const R tn0 = Tn[(size_t)(0 * 3 + a) * m.P + p], tn1 = Tn[(size_t)(1 * 3 + a) * m.P + p];
+      const R tp0 = Tp[(size_t)(0 * 3 + a) * m.P + p], tp1 = Tp[(size_t)(1 * 3 + a) * m.P + p];
+      s_b[a * TP + i] = al * mn * (G2 * tn0 + G1 * tn1) + be * (mp * (G2 * tp0 + G1 * tp1) + dtr * out[0][a]);
+      s_b[(3 + a) * TP + i] = al * mn * (G1 * tn0 + G2 * tn1) + be * (mp * (G1 * tp0 + G2 * tp1) + dtr * out[1][a]);
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) s_W[r * TP + i] = W[(size_t)r * m.P + p];
+  }
+  __syncthreads();
+  solve_tile_columns<R, TP>(m, tl, s_off, s_b, s_W, s_C, s_eta, sp, beta * dt);
+  __syncthreads();
+  write_tile<R, TP>(m, tl, s_b, Tout, err);
+}
+
+// standalone vertical solve: (M(eta) - bdt A) x = rhs + bdt b
+template <typename R, int TP>
+__global__ void __launch_bounds__(TP) k_vertical_solve(DevMesh m, const R* __restrict__ W,
+                                                       const double* __restrict__ eta,
+                                                       const R* rhs, R* out, double bdt,
+                                                       StageParams sp, int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using L = SolveSmem<R, TP>;
+  int* s_off = reinterpret_cast<int*>(smem);
+  R* s_b = reinterpret_cast<R*>(smem + L::off_b);
+  R* s_W = reinterpret_cast<R*>(smem + L::off_W);
+  R* s_C = reinterpret_cast<R*>(smem + L::off_C);
+  double* s_eta = reinterpret_cast<double*>(smem + L::off_eta);
+  const Tile tl = load_tile<TP>(m, s_off);
+  const int nt = m.n_tri;
+  for (int j = threadIdx.x; j < 3 * tl.nt; j += TP) {
+    const int a = j / tl.nt, lt = j - a * tl.nt;
+    s_eta[a * TP + lt] = eta[a * nt + tl.t0 + lt];
+  }
+  const int i = threadIdx.x;
+  if (i < tl.np) {
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      s_b[r * TP + i] = rhs[(size_t)r * m.P + tl.p0 + i];
+      s_W[r * TP + i] = W[(size_t)r * m.P + tl.p0 + i];
+    }
+  }
+  __syncthreads();
+  solve_tile_columns<R, TP>(m, tl, s_off, s_b, s_W, s_C, s_eta, sp, bdt);
+  __syncthreads();
+  write_tile<R, TP>(m, tl, s_b, out, err);
+}
+
+// standalone horizontal residual
+template <typename R, int TP>
+__global__ void __launch_bounds__(TP) k_rhs3d(DevMesh m, const R* __restrict__ U,
+                                              const R* __restrict__ V, const R* __restrict__ T,
+                                              const R* __restrict__ Text,
+                                              const double* __restrict__ eta, R* __restrict__ out) {
+  __shared__ int s_off[TP + 1];
+  const Tile tl = load_tile<TP>(m, s_off);
+  const int i = threadIdx.x;
+  if (i >= tl.np) return;
+  const int lt = tile_tri_of(s_off, tl.nt, i);
+  const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
+  R o[2][3];
+  prism_rh<R, false>(m, t, k, tl.p0 + i, N, U, V, T, Text, eta, o);
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[(size_t)(c * 3 + a) * m.P + tl.p0 + i] = o[c][a];
+}
+
+// ---------------------------------------------------------------------------
+// tracer mass sum_nodes (M T) = sum_p sum_a (J_h/12) dz_a (T_top,a + T_bot,a),
+// compensated pairwise (TwoSum) reduction in a fixed order: deterministic.
+// ---------------------------------------------------------------------------
+struct CSum {
+  double s, c;
+};
+__device__ __forceinline__ CSum csum_add(CSum x, CSum y) {
+  const double s = x.s + y.s;
+  const double bp = s - x.s;
+  const double err = (x.s - (s - bp)) + (y.s - bp);  // TwoSum
+  return {s, x.c + y.c + err};
+}
+
+template <int TP>
+__device__ __forceinline__ CSum block_csum(CSum v, double* s_s, double* s_c) {
+  s_s[threadIdx.x] = v.s;
+  s_c[threadIdx.x] = v.c;
+  __syncthreads();
+  for (int w = TP / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      CSum r = csum_add({s_s[threadIdx.x], s_c[threadIdx.x]},
+                        {s_s[threadIdx.x + w], s_c[threadIdx.x + w]});
+      s_s[threadIdx.x] = r.s;
+      s_c[threadIdx.x] = r.c;
+    }
+    __syncthreads();
+  }
+  return {s_s[0], s_c[0]};
+}
+
+template <typename R, int TP>
+__global__ void __launch_bounds__(TP) k_mass_partial(DevMesh m, const R* __restrict__ T,
+                                                     const double* __restrict__ eta,
+                                                     double* __restrict__ part) {
+  __shared__ int s_off[TP + 1];
+  __shared__ double s_s[TP], s_c[TP];
+  const Tile tl = load_tile<TP>(m, s_off);
+  const int i = threadIdx.x;
+  CSum v = {0.0, 0.0};
+  if (i < tl.np) {
+    const int lt = tile_tri_of(s_off, tl.nt, i);
+    const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
+    const int p = tl.p0 + i, nt = m.n_tri;
+    const double w12 = m.jh[t] / 12.0;
+    for (int a = 0; a < 3; ++a) {
+      const double dz = dz_at(m, m.h[a * nt + t], eta[a * nt + t], k, N);
+      const double x = w12 * dz * ((double)T[(size_t)a * m.P + p] + (double)T[(size_t)(3 + a) * m.P + p]);
+      v = csum_add(v, {x, 0.0});
+    }
+  }
+  CSum r = block_csum<TP>(v, s_s, s_c);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = r.s;
+    part[2 * blockIdx.x + 1] = r.c;
+  }
+}
+
+template <int TP>
+__global__ void __launch_bounds__(TP) k_mass_final(const double* __restrict__ part, int n,
+                                                   double* __restrict__ result) {
+  __shared__ double s_s[TP], s_c[TP];
+  CSum v = {0.0, 0.0};
+  for (int j = threadIdx.x; j < n; j += TP) v = csum_add(v, {part[2 * j], part[2 * j + 1]});
+  CSum r = block_csum<TP>(v, s_s, s_c);
+  if (threadIdx.x == 0) result[0] = r.s + r.c;
+}
+
+// ---------------------------------------------------------------------------
+// conversions
+// ---------------------------------------------------------------------------
+__global__ void k_d2f(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+__global__ void k_f2d(const float* __restrict__ in, double* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+#define SLIM_TP_SWITCH(TP, ...) \
+  switch (TP) {                  \
+    case 128: { constexpr int TPc = 128; __VA_ARGS__; } break; \
+    case 256: { constexpr int TPc = 256; __VA_ARGS__; } break; \
+    case 512: { constexpr int TPc = 512; __VA_ARGS__; } break; \
+    default: return cudaErrorInvalidValue;              \
+  }
+
+template <typename KernelT>
+static cudaError_t set_smem(KernelT kern, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename R>
+cudaError_t launch_continuity(const DevMesh& m, int TP, const R* U, const R* V, const double* eta,
+                              double* eta_out, R* W, double dt, cudaStream_t st) {
+  SLIM_TP_SWITCH(TP, (k_continuity<R, TPc, false><<<m.n_tiles, TPc, 0, st>>>(m, U, V, eta, eta_out, W, dt)));
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_column_divergence(const DevMesh& m, int TP, const R* U, const R* V,
+                                     const double* eta, double* out, cudaStream_t st) {
+  SLIM_TP_SWITCH(TP, (k_continuity<R, TPc, true><<<m.n_tiles, TPc, 0, st>>>(m, U, V, eta, out, nullptr, 0.0)));
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_tracer_stage(const DevMesh& m, int TP, const R* U, const R* V, const R* Tn,
+                                const R* Tp, const R* Text, const R* W, R* Tout,
+                                const double* eta_n, const double* eta_np1, double th_p,
+                                double th_s, double alpha, double beta, double dt,
+                                const StageParams& sp, int* err, cudaStream_t st) {
+  SLIM_TP_SWITCH(TP, {
+    const size_t sm = SolveSmem<R, TPc>::bytes;
+    cudaError_t e = set_smem(k_tracer_stage<R, TPc>, sm);
+    if (e != cudaSuccess) return e;
+    k_tracer_stage<R, TPc><<<m.n_tiles, TPc, sm, st>>>(m, U, V, Tn, Tp, Text, W, Tout, eta_n,
+                                                       eta_np1, th_p, th_s, alpha, beta, dt, sp, err);
+  });
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_vertical_solve(const DevMesh& m, int TP, const R* W, const double* eta,
+                                  const R* rhs, R* out, double bdt, const StageParams& sp,
+                                  int* err, cudaStream_t st) {
+  SLIM_TP_SWITCH(TP, {
+    const size_t sm = SolveSmem<R, TPc>::bytes;
+    cudaError_t e = set_smem(k_vertical_solve<R, TPc>, sm);
+    if (e != cudaSuccess) return e;
+    k_vertical_solve<R, TPc><<<m.n_tiles, TPc, sm, st>>>(m, W, eta, rhs, out, bdt, sp, err);
+  });
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_rhs3d(const DevMesh& m, int TP, const R* U, const R* V, const R* T,
+                         const R* Text, const double* eta, R* out, cudaStream_t st) {
+  SLIM_TP_SWITCH(TP, (k_rhs3d<R, TPc><<<m.n_tiles, TPc, 0, st>>>(m, U, V, T, Text, eta, out)));
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_mass(const DevMesh& m, int TP, const R* T, const double* eta, double* partials,
+                        double* result, cudaStream_t st) {
+  SLIM_TP_SWITCH(TP, (k_mass_partial<R, TPc><<<m.n_tiles, TPc, 0, st>>>(m, T, eta, partials)));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_mass_final<256><<<1, 256, 0, st>>>(partials, m.n_tiles, result);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_d2f(const double* in, float* out, size_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+  k_d2f<<<blocks, 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_convert_f2d(const float* in, double* out, size_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+  k_f2d<<<blocks, 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+#define SLIM_INSTANTIATE(R)                                                                        \
+  template cudaError_t launch_continuity<R>(const DevMesh&, int, const R*, const R*, const double*, \
+                                            double*, R*, double, cudaStream_t);                     \
+  template cudaError_t launch_column_divergence<R>(const DevMesh&, int, const R*, const R*,         \
+                                                   const double*, double*, cudaStream_t);           \
+  template cudaError_t launch_tracer_stage<R>(const DevMesh&, int, const R*, const R*, const R*,    \
+                                              const R*, const R*, const R*, R*, const double*,      \
+                                              const double*, double, double, double, double,        \
+                                              double, const StageParams&, int*, cudaStream_t);      \
+  template cudaError_t launch_vertical_solve<R>(const DevMesh&, int, const R*, const double*,       \
+                                                const R*, R*, double, const StageParams&, int*,     \
+                                                cudaStream_t);                                      \
+  template cudaError_t launch_rhs3d<R>(const DevMesh&, int, const R*, const R*, const R*, const R*, \
+                                       const double*, R*, cudaStream_t);                            \
+  template cudaError_t launch_mass<R>(const DevMesh&, int, const R*, const double*, double*,        \
+                                      double*, cudaStream_t);
+
+SLIM_INSTANTIATE(double)
+SLIM_INSTANTIATE(float)
+
+}  // namespace slim

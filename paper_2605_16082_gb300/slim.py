@@ -1,0 +1,292 @@
+"""Python binding of libslim (ctypes): the C ABI of include/slim.h with the same
+names, argument marshalling only.  Every operation runs in the library's CUDA
+kernels; there is no fallback.  A missing library raises immediately.
+
+Device buffers are passed as integer addresses (e.g. ``tensor.data_ptr()``) and
+streams as integer handles (e.g. ``torch.cuda.current_stream().cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libslim.so")
+
+SLIM_FP64, SLIM_MIXED = 0, 1
+SLIM_SCHEME_TRACER, SLIM_SCHEME_SPLIT = 0, 1
+FIELD = dict(T=0, S=1, U=2, V=3, W=4, R_X=5, R_Y=6, T_EXT=7, S_EXT=8, ETA=16, QX=17, QY=18, ETA_NEXT=19,
+             QBAR_X=20, QBAR_Y=21)
+FIELD_IS_3D = {f: (v < 16) for f, v in FIELD.items()}
+
+# every symbol declared in include/slim.h
+EXPORTED = ["slim_params_default", "slim_status_string", "slim_last_error", "slim_mesh_create",
+            "slim_mesh_destroy", "slim_mesh_info", "slim_state_alloc", "slim_state_free",
+            "slim_state_set_params", "slim_state_upload", "slim_state_download",
+            "slim_state_field_ptr", "slim_state_check", "slim_rhs3d", "slim_continuity",
+            "slim_rhs2d", "slim_vertical_solve", "slim_step", "slim_tracer_mass",
+            "slim_step_kernel_count", "slim_profile_begin", "slim_profile_end",
+            "slim_phase_name"]
+PHASES = ["continuity", "tracer_stage", "hpg", "mom_pred", "ext2d", "momentum", "tracers", "misc"]
+
+
+class SlimParams(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "g", "rho0", "coriolis_f", "eos_alpha", "eos_beta", "eos_T0", "eos_S0", "kappa_v",
+        "nu_v", "kappa_h", "nu_h", "drag_cd", "flux_top", "flux_bot", "penalty_v", "penalty_h",
+        "tide_amp", "tide_period")] + [(n, C.c_int) for n in (
+        "scheme", "n_sub", "tile_prisms", "check_every")]
+
+
+class SlimError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+_lib = None
+_vp, _i, _d, _dp = C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double)
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        sig = {
+            "slim_params_default": ([C.POINTER(SlimParams)], _i),
+            "slim_status_string": ([_i], C.c_char_p),
+            "slim_last_error": ([], C.c_char_p),
+            "slim_mesh_create": ([_vp, _i, _vp, _i, _vp, _vp, _vp, _i, _vp, _i, C.POINTER(_vp)], _i),
+            "slim_mesh_destroy": ([_vp], None),
+            "slim_mesh_info": ([_vp, C.POINTER(C.c_int64), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)], _i),
+            "slim_state_alloc": ([_vp, _i, C.POINTER(SlimParams), C.POINTER(_vp)], _i),
+            "slim_state_free": ([_vp], None),
+            "slim_state_set_params": ([_vp, C.POINTER(SlimParams)], _i),
+            "slim_state_upload": ([_vp, _i, _vp, _vp], _i),
+            "slim_state_download": ([_vp, _i, _vp, _vp], _i),
+            "slim_state_field_ptr": ([_vp, _i, C.POINTER(_vp), C.POINTER(_i)], _i),
+            "slim_state_check": ([_vp, _vp], _i),
+            "slim_rhs3d": ([_vp, _i, _vp, _vp], _i),
+            "slim_continuity": ([_vp, _d, _vp], _i),
+            "slim_rhs2d": ([_vp, _d, _vp, _vp], _i),
+            "slim_vertical_solve": ([_vp, _i, _d, _vp, _vp, _vp], _i),
+            "slim_step": ([_vp, _d, _d, _vp], _i),
+            "slim_tracer_mass": ([_vp, _i, _dp, _vp], _i),
+            "slim_step_kernel_count": ([_vp], _i),
+            "slim_profile_begin": ([_vp, _i], _i),
+            "slim_profile_end": ([_vp, _dp, C.POINTER(_i)], _i),
+            "slim_phase_name": ([_i], C.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        L = lib()
+        raise SlimError(status, f"{L.slim_status_string(status).decode()}: {L.slim_last_error().decode()}")
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_vp)
+
+
+# ---------------------------------------------------------------------------
+# functional API (names of the C ABI)
+# ---------------------------------------------------------------------------
+def slim_params_default(**overrides) -> SlimParams:
+    p = SlimParams()
+    _check(lib().slim_params_default(C.byref(p)))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def slim_status_string(status: int) -> str:
+    return lib().slim_status_string(status).decode()
+
+
+def slim_mesh_create(xy, tri, h_tri, n_layers, bnd, levels=None, tile_prisms: int = 256) -> int:
+    xy = np.ascontiguousarray(xy, np.float64)
+    tri = np.ascontiguousarray(tri, np.int32)
+    h_tri = np.ascontiguousarray(h_tri, np.float64)
+    n_layers = np.ascontiguousarray(n_layers, np.int32)
+    bnd = np.ascontiguousarray(bnd, np.int8)
+    lev = None if levels is None else np.ascontiguousarray(levels, np.float64)
+    out = _vp()
+    _check(lib().slim_mesh_create(_ptr(xy), int(xy.shape[0]), _ptr(tri), int(tri.shape[0]),
+                                  _ptr(h_tri), _ptr(n_layers), None if lev is None else _ptr(lev),
+                                  0 if lev is None else int(lev.shape[0]), _ptr(bnd),
+                                  int(tile_prisms), C.byref(out)))
+    return out.value
+
+
+def slim_mesh_destroy(mesh: int) -> None:
+    lib().slim_mesh_destroy(mesh)
+
+
+def slim_mesh_info(mesh: int) -> dict:
+    P, nt, ml, ntl = C.c_int64(), _i(), _i(), _i()
+    _check(lib().slim_mesh_info(mesh, C.byref(P), C.byref(nt), C.byref(ml), C.byref(ntl)))
+    return dict(n_prisms=P.value, n_tri=nt.value, max_layers=ml.value, n_tiles=ntl.value)
+
+
+def slim_state_alloc(mesh: int, precision: int, params: SlimParams) -> int:
+    out = _vp()
+    _check(lib().slim_state_alloc(mesh, int(precision), C.byref(params), C.byref(out)))
+    return out.value
+
+
+def slim_state_free(state: int) -> None:
+    lib().slim_state_free(state)
+
+
+def slim_state_set_params(state: int, params: SlimParams) -> None:
+    _check(lib().slim_state_set_params(state, C.byref(params)))
+
+
+def slim_state_upload(state: int, field: int, host: np.ndarray, stream: int = 0) -> None:
+    a = np.ascontiguousarray(host, np.float64)
+    _check(lib().slim_state_upload(state, int(field), _ptr(a), stream))
+
+
+def slim_state_upload_ptr(state: int, field: int, host_ptr: int, stream: int = 0) -> None:
+    """Upload from a raw host address (e.g. pinned memory) of doubles."""
+    _check(lib().slim_state_upload(state, int(field), host_ptr, stream))
+
+
+def slim_state_download(state: int, field: int, n: int, stream: int = 0) -> np.ndarray:
+    out = np.empty(n, np.float64)
+    _check(lib().slim_state_download(state, int(field), _ptr(out), stream))
+    return out
+
+
+def slim_state_download_ptr(state: int, field: int, host_ptr: int, stream: int = 0) -> None:
+    """Download into a raw host address (e.g. pinned memory) of doubles; synchronises."""
+    _check(lib().slim_state_download(state, int(field), host_ptr, stream))
+
+
+def slim_state_field_ptr(state: int, field: int) -> tuple[int, int]:
+    p, es = _vp(), _i()
+    _check(lib().slim_state_field_ptr(state, int(field), C.byref(p), C.byref(es)))
+    return p.value, es.value
+
+
+def slim_state_check(state: int, stream: int = 0) -> None:
+    _check(lib().slim_state_check(state, stream))
+
+
+def slim_rhs3d(state: int, field: int, out_dev: int, stream: int = 0) -> None:
+    _check(lib().slim_rhs3d(state, int(field), out_dev, stream))
+
+
+def slim_continuity(state: int, dt: float, stream: int = 0) -> None:
+    _check(lib().slim_continuity(state, float(dt), stream))
+
+
+def slim_rhs2d(state: int, t: float, out_dev: int, stream: int = 0) -> None:
+    _check(lib().slim_rhs2d(state, float(t), out_dev, stream))
+
+
+def slim_vertical_solve(state: int, field: int, beta_dt: float, rhs_dev: int, out_dev: int,
+                        stream: int = 0) -> None:
+    _check(lib().slim_vertical_solve(state, int(field), float(beta_dt), rhs_dev, out_dev, stream))
+
+
+def slim_step(state: int, t: float, dt: float, stream: int = 0) -> None:
+    _check(lib().slim_step(state, float(t), float(dt), stream))
+
+
+def slim_tracer_mass(state: int, field: int, stream: int = 0) -> float:
+    out = C.c_double()
+    _check(lib().slim_tracer_mass(state, int(field), C.byref(out), stream))
+    return out.value
+
+
+def slim_step_kernel_count(state: int) -> int:
+    return int(lib().slim_step_kernel_count(state))
+
+
+def slim_profile_begin(state: int, max_launches: int) -> None:
+    _check(lib().slim_profile_begin(state, int(max_launches)))
+
+
+def slim_profile_end(state: int) -> dict:
+    """{phase name: (milliseconds, launches)} of the recorded launches."""
+    ms = (C.c_double * len(PHASES))()
+    n = (C.c_int * len(PHASES))()
+    _check(lib().slim_profile_end(state, ms, n))
+    return {PHASES[i]: (ms[i], n[i]) for i in range(len(PHASES)) if n[i] > 0}
+
+
+def slim_phase_name(phase: int) -> str:
+    return lib().slim_phase_name(int(phase)).decode()
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper owning a mesh and a state
+# ---------------------------------------------------------------------------
+class Model:
+    """A mesh plus one state, freed together.  ``mesh`` is any object with the
+    array attributes of ``workloads.Mesh`` (xy, tri, h_tri, n_layers, bnd, levels)."""
+
+    def __init__(self, mesh, precision: int = SLIM_FP64, params: SlimParams | None = None,
+                 tile_prisms: int | None = None):
+        self.params = params if params is not None else slim_params_default()
+        tp = tile_prisms if tile_prisms is not None else (self.params.tile_prisms or 256)
+        self.mesh_h = slim_mesh_create(mesh.xy, mesh.tri, mesh.h_tri, mesh.n_layers, mesh.bnd,
+                                       mesh.levels, tp)
+        self.info = slim_mesh_info(self.mesh_h)
+        self.P = self.info["n_prisms"]
+        self.n_tri = self.info["n_tri"]
+        self.precision = precision
+        try:
+            self.state = slim_state_alloc(self.mesh_h, precision, self.params)
+        except Exception:
+            slim_mesh_destroy(self.mesh_h)
+            raise
+
+    def n(self, field: str) -> int:
+        return 6 * self.P if FIELD_IS_3D[field] else 3 * self.n_tri
+
+    def upload(self, field: str, values, stream: int = 0) -> None:
+        a = np.asarray(values, np.float64).reshape(-1)
+        if a.shape[0] != self.n(field):
+            raise ValueError(f"{field}: expected {self.n(field)} values, got {a.shape[0]}")
+        slim_state_upload(self.state, FIELD[field], a, stream)
+
+    def download(self, field: str, stream: int = 0) -> np.ndarray:
+        return slim_state_download(self.state, FIELD[field], self.n(field), stream)
+
+    def ptr(self, field: str) -> int:
+        return slim_state_field_ptr(self.state, FIELD[field])[0]
+
+    def close(self) -> None:
+        if getattr(self, "state", None):
+            slim_state_free(self.state)
+            self.state = None
+        if getattr(self, "mesh_h", None):
+            slim_mesh_destroy(self.mesh_h)
+            self.mesh_h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

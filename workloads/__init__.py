@@ -8,9 +8,9 @@ computation.  Every generator is deterministic for a given seed.
 """
 from .meshes import (Mesh, square_mesh, basin_mesh, hilbert_order, permute_triangles,
                      c1_mesh, c2_mesh, c4_mesh)
-from .fields import (node_positions_sigma, c1_velocity, c1_tracer, c2_initial_state,
+from .fields import (node_positions_sigma, c1_velocity, c1_tracer, c2_initial_state, basin_velocity,
                      c4_initial_state, WORKLOADS)
 
 __all__ = ["Mesh", "square_mesh", "basin_mesh", "hilbert_order", "permute_triangles",
            "c1_mesh", "c2_mesh", "c4_mesh", "node_positions_sigma", "c1_velocity",
-           "c1_tracer", "c2_initial_state", "c4_initial_state", "WORKLOADS"]
+           "c1_tracer", "c2_initial_state", "basin_velocity", "c4_initial_state", "WORKLOADS"]

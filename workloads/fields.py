@@ -90,6 +90,21 @@ def c1_tracer(m: Mesh, L: float = 10e3, sigma_h: float = 1e3, sigma_v: float = 0
     return flat(np.exp(-r2 / (2 * sigma_h ** 2)) * np.exp(-(s - 0.5) ** 2 / (2 * sigma_v ** 2)))
 
 
+def basin_velocity(m: Mesh, Lx: float = 200e3, Ly: float = 100e3, umax: float = 0.5,
+                   shear: bool = True) -> tuple[np.ndarray, np.ndarray]:
+    """Velocity with zero normal component on the basin boundary, from the
+    streamfunction psi = sin^2(pi x/Lx) sin^2(pi y/Ly); optional depth shear."""
+    x, y, _, s = node_positions_sigma(m)
+    kx, ky = np.pi / Lx, np.pi / Ly
+    u = -np.sin(kx * x) ** 2 * ky * np.sin(2 * ky * y)
+    v = kx * np.sin(2 * kx * x) * np.sin(ky * y) ** 2
+    scale = umax / np.sqrt(u ** 2 + v ** 2).max()
+    if shear:
+        u = u * (1.5 - s)
+        v = v * (1.5 - s)
+    return flat(u * scale), flat(v * scale)
+
+
 # ----------------------------------------------------------------------------
 # baroclinic basin workload
 # ----------------------------------------------------------------------------
@@ -120,6 +135,8 @@ def dt_2d(m: Mesh, g: float = 9.81, cfl: float = 0.25) -> float:
 
 # name -> description used by tests and the bench
 WORKLOADS = {
+    "basin_tracer": dict(mesh=lambda: c2_mesh(200_000, 20, 0), dt=10.0, steps=100,
+                         kappa_v=1e-3, scheme="tracer"),
     "square_tracer": dict(mesh=lambda: c1_mesh(32, 10e3, 10), dt=5.0, steps=100,
                           kappa_v=1e-3, scheme="tracer"),
     "basin_baroclinic": dict(mesh=lambda: c2_mesh(200_000, 20, 0), steps=1000, n_sub=20,
