@@ -19,6 +19,10 @@ namespace slim {
 
 template <typename R> struct Geo;
 template <> struct Geo<double> {
+  static __device__ __forceinline__ double hN(const DevMesh& m, int i) { return m.hN[i]; }
+  static __device__ __forceinline__ double ih(const DevMesh& m, int i) { return m.ih[i]; }
+  static __device__ __forceinline__ double h(const DevMesh& m, int i) { return m.h[i]; }
+  static __device__ __forceinline__ double lev(const DevMesh& m, int k) { return m.levels[k]; }
   static __device__ __forceinline__ double jh(const DevMesh& m, int t) { return m.jh[t]; }
   static __device__ __forceinline__ double gx(const DevMesh& m, int i) { return m.gx[i]; }
   static __device__ __forceinline__ double gy(const DevMesh& m, int i) { return m.gy[i]; }
@@ -27,6 +31,10 @@ template <> struct Geo<double> {
   static __device__ __forceinline__ double len(const DevMesh& m, int i) { return m.elen[i]; }
 };
 template <> struct Geo<float> {
+  static __device__ __forceinline__ float hN(const DevMesh& m, int i) { return m.hN_f[i]; }
+  static __device__ __forceinline__ float ih(const DevMesh& m, int i) { return m.ih_f[i]; }
+  static __device__ __forceinline__ float h(const DevMesh& m, int i) { return m.h_f[i]; }
+  static __device__ __forceinline__ float lev(const DevMesh& m, int k) { return m.levels_f[k]; }
   static __device__ __forceinline__ float jh(const DevMesh& m, int t) { return m.jh_f[t]; }
   static __device__ __forceinline__ float gx(const DevMesh& m, int i) { return m.gx_f[i]; }
   static __device__ __forceinline__ float gy(const DevMesh& m, int i) { return m.gy_f[i]; }
@@ -35,18 +43,24 @@ template <> struct Geo<float> {
   static __device__ __forceinline__ float len(const DevMesh& m, int i) { return m.elen_f[i]; }
 };
 
-// Rest thickness of layer k of a column of N layers at a vertex of rest depth h:
-// h/N for sigma layers, the level spacing (the column's own depth at the bed)
-// for z-levels.
-__device__ __forceinline__ double dz_rest(const DevMesh& m, double h, int k, int N) {
-  if (m.n_levels == 0) return h / (double)N;
-  double top = m.levels[k];
-  double bot = (k + 1 < N) ? m.levels[k + 1] : -h;
+// Layer thickness at elevation eta in the compute type R, for the vertex column
+// entry i = a*n_tri + t: the interfaces stretch with the column, z = eta + (1 + eta/h) zhat,
+// so dz = dz_rest (1 + eta (1/h)) with dz_rest = h/N for sigma layers or the level
+// spacing (the column's own depth at the bed) for z-levels.  Division-free.
+template <typename R>
+__device__ __forceinline__ R dz_rest_r(const DevMesh& m, int i, int k, int N) {
+  if (m.n_levels == 0) return Geo<R>::hN(m, i);
+  const R top = Geo<R>::lev(m, k);
+  const R bot = (k + 1 < N) ? Geo<R>::lev(m, k + 1) : -Geo<R>::h(m, i);
   return top - bot;
 }
-// Thickness at elevation eta: interfaces stretch with the column, z = eta + (1 + eta/h) zhat.
-__device__ __forceinline__ double dz_at(const DevMesh& m, double h, double eta, int k, int N) {
-  return dz_rest(m, h, k, N) * (1.0 + eta / h);
+template <typename R>
+__device__ __forceinline__ R stretch_r(const DevMesh& m, int i, double eta) {
+  return (R)1 + (R)eta * Geo<R>::ih(m, i);
+}
+template <typename R>
+__device__ __forceinline__ R dz_r(const DevMesh& m, int i, double eta, int k, int N) {
+  return dz_rest_r<R>(m, i, k, N) * stretch_r<R>(m, i, eta);
 }
 
 // ---------------------------------------------------------------------------
@@ -96,8 +110,7 @@ __device__ __forceinline__ void prism_rh(const DevMesh& m, int t, int k, int p, 
   R qx[2][3], qy[2][3], Tv[2][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    double h = m.h[a * nt + t];
-    R hz = (R)(0.5 * dz_at(m, h, eta_q[a * nt + t], k, N));
+    const R hz = (R)0.5 * dz_r<R>(m, a * nt + t, eta_q[a * nt + t], k, N);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       int idx = (c * 3 + a) * P + p;
@@ -169,7 +182,7 @@ __device__ __forceinline__ void prism_rh(const DevMesh& m, int t, int k, int p, 
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int l = j ? ((loc >> 2) & 3) : (loc & 3);
-        const R hz = (R)(0.5 * dz_at(m, m.h[l * nt + nb], eta_q[l * nt + nb], k, Nn));
+        const R hz = (R)0.5 * dz_r<R>(m, l * nt + nb, eta_q[l * nt + nb], k, Nn);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const int idx = (c * 3 + l) * P + pn;
@@ -231,9 +244,10 @@ struct Row {
   R D[2][2], L[2][2], U[2][2];
 };
 
+// idzm, idz, idzp: reciprocals of the thicknesses of layers k-1, k, k+1.
 template <typename R>
-__device__ __forceinline__ void assemble_row(int k, int N, R omega, R dzm, R dz, R dzp, R W0, R W1,
-                                             R Wn, R kap, R pen, R bdt, Row<R>& row) {
+__device__ __forceinline__ void assemble_row(int k, int N, R omega, R idzm, R dz, R idz, R idzp,
+                                             R W0, R W1, R Wn, R kap, R pen, R bdt, Row<R>& row) {
   R A[2][2] = {{0, 0}, {0, 0}}, AL[2][2] = {{0, 0}, {0, 0}}, AU[2][2] = {{0, 0}, {0, 0}};
   // advection, volume: A[c][d] = dpsi_c sum_e W_e G_ed
   const R g0 = (R)(1.0 / 3.0) * ((R)2 * W0 + W1);
@@ -247,11 +261,11 @@ __device__ __forceinline__ void assemble_row(int k, int N, R omega, R dzm, R dz,
     if (Wn > (R)0) AU[1][0] += Wn; else A[1][1] += Wn;
   }
   // diffusion, element stiffness
-  const R ke = omega * kap / dz;
+  const R ke = omega * kap * idz;
   A[0][0] -= ke; A[0][1] += ke; A[1][0] += ke; A[1][1] -= ke;
   if (k > 0) {
-    const R sg = pen * kap / fmin(dzm, dz);
-    const R cm = kap / ((R)2 * dzm), c0 = kap / ((R)2 * dz);
+    const R sg = pen * kap * fmax(idzm, idz);
+    const R cm = (R)0.5 * kap * idzm, c0 = (R)0.5 * kap * idz;
     A[0][0] -= omega * (sg - (R)2 * c0);
     A[0][1] -= omega * c0;
     A[1][0] -= omega * c0;
@@ -260,8 +274,8 @@ __device__ __forceinline__ void assemble_row(int k, int N, R omega, R dzm, R dz,
     AL[1][1] -= omega * (-c0);
   }
   if (k + 1 < N) {
-    const R sg = pen * kap / fmin(dz, dzp);
-    const R c0 = kap / ((R)2 * dz), cp = kap / ((R)2 * dzp);
+    const R sg = pen * kap * fmax(idz, idzp);
+    const R c0 = (R)0.5 * kap * idz, cp = (R)0.5 * kap * idzp;
     A[0][1] -= omega * c0;
     A[1][0] -= omega * c0;
     A[1][1] -= omega * (sg - (R)2 * c0);

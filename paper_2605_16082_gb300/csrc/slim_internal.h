@@ -46,6 +46,12 @@ struct DevMesh {
   const int* nbr;        // [3][n_tri] neighbour triangle, -1 wall, -2 open boundary
   const int* nloc;       // [3][n_tri] neighbour-local vertices of own e, e+1: l0 | l1 << 2
   const double* levels;  // [n_levels] or null
+  const double* hN;      // [3][n_tri] h / N (rest layer thickness of sigma columns)
+  const double* ih;      // [3][n_tri] 1 / h
+  const float* hN_f;
+  const float* ih_f;
+  const float* h_f;
+  const float* levels_f;
   // float copies of the geometry for the mixed-precision kernels
   const float* jh_f;
   const float* gx_f;

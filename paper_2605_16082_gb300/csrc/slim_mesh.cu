@@ -187,6 +187,14 @@ extern "C" slim_status slim_mesh_create(const double* xy, int n_vert, const int*
   tile_t0.push_back(nt);
   std::vector<double> lev;
   if (levels) lev.assign(levels, levels + n_levels);
+  std::vector<double> hN(3 * nt), ih(3 * nt);
+  for (int t = 0; t < nt; ++t)
+    for (int a = 0; a < 3; ++a) {
+      hN[a * nt + t] = h[a * nt + t] / n_layers[t];
+      ih[a * nt + t] = 1.0 / h[a * nt + t];
+    }
+  std::vector<float> hNf(hN.begin(), hN.end()), ihf(ih.begin(), ih.end()), hf(h.begin(), h.end()),
+      levf(lev.begin(), lev.end());
 
   slim_mesh* m = new slim_mesh();
   m->tile_prisms = tile_prisms;
@@ -217,6 +225,12 @@ extern "C" slim_status slim_mesh_create(const double* xy, int n_vert, const int*
   UP(nbr, nbr);
   UP(nloc, nloc);
   UP(lev, levels);
+  UP(hN, hN);
+  UP(ih, ih);
+  UP(hNf, hN_f);
+  UP(ihf, ih_f);
+  UP(hf, h_f);
+  UP(levf, levels_f);
   UP(jhf, jh_f);
   UP(gxf, gx_f);
   UP(gyf, gy_f);
@@ -224,7 +238,7 @@ extern "C" slim_status slim_mesh_create(const double* xy, int n_vert, const int*
   UP(enyf, eny_f);
   UP(elenf, elen_f);
 #undef UP
-  if (!levels) d.levels = nullptr;
+  if (!levels) { d.levels = nullptr; d.levels_f = nullptr; }
   m->col_off_h = col_off;
   m->tile_t0_h = tile_t0;
   m->nbr_h = nbr;

@@ -57,15 +57,16 @@ __global__ void __launch_bounds__(TP) k_continuity(DevMesh m, const R* __restric
       eta_out[a * nt + t] = D;
       continue;
     }
-    const double jh = m.jh[t], h = m.h[a * nt + t];
-    const double e0 = eta[a * nt + t];
+    const int ia = a * nt + t;
+    const double jh = m.jh[t];
+    const double e0 = eta[ia];
     const double e1 = e0 + dt * D / (jh / 6.0);
-    eta_out[a * nt + t] = e1;
+    eta_out[ia] = e1;
     // dz'_k - dz_k = dz_rest_k (e1 - e0) / h
-    const double dm_fac = (jh / 12.0) * (e1 - e0) / (h * dt);
+    const double dm_fac = (jh / 12.0) * (e1 - e0) * m.ih[ia] / dt;
     R s = (R)0;
     for (int k = N - 1; k >= 0; --k) {
-      const R dm = (R)(dm_fac * dz_rest(m, h, k, N));
+      const R dm = (R)(dm_fac * dz_rest_r<double>(m, ia, k, N));
       const R ft = s_F[a][base + k] - dm, fb = s_F[3 + a][base + k] - dm;
       const R wt = ft + fb + s;
       const R wb = fb - ft + s;
@@ -93,19 +94,24 @@ __device__ __forceinline__ void column_thomas(const DevMesh& m, int t, int a, in
                                               double eta_s, const R* Wt, const R* Wb, R* bt,
                                               R* bb, R* C0, R* C1, R* C2, R* C3, R kap, R pen,
                                               R bdt, R flux_top, R flux_bot) {
-  const int nt = m.n_tri;
-  const double h = m.h[a * nt + t];
-  const R omega = (R)(m.jh[t] / 6.0);
+  const int ia = a * m.n_tri + t;
+  const R omega = (R)(m.jh[t] * (1.0 / 6.0));
+  const R st = stretch_r<R>(m, ia, eta_s);
   R z0 = 0, z1 = 0;
   R c00 = 0, c01 = 0, c10 = 0, c11 = 0;
-  R dz = (R)dz_at(m, h, eta_s, 0, N);
-  R dzm = dz;
+  R dz = dz_rest_r<R>(m, ia, 0, N) * st;
+  R idz = (R)1 / dz;
+  R idzm = idz;
   for (int k = 0; k < N; ++k) {
     const int i = base + k;
-    const R dzp = (k + 1 < N) ? (R)dz_at(m, h, eta_s, k + 1, N) : dz;
+    R dzp = dz, idzp = idz;
+    if (k + 1 < N) {
+      dzp = dz_rest_r<R>(m, ia, k + 1, N) * st;
+      idzp = (m.n_levels == 0) ? idz : (R)1 / dzp;
+    }
     const R Wn = (k + 1 < N) ? Wt[i + 1] : (R)0;
     Row<R> row;
-    assemble_row<R>(k, N, omega, dzm, dz, dzp, Wt[i], Wb[i], Wn, kap, pen, bdt, row);
+    assemble_row<R>(k, N, omega, idzm, dz, idz, idzp, Wt[i], Wb[i], Wn, kap, pen, bdt, row);
     R b0 = bt[i], b1 = bb[i];
     if (k == 0) b0 += bdt * omega * flux_top;
     if (k == N - 1) b1 -= bdt * omega * flux_bot;
@@ -128,8 +134,9 @@ __device__ __forceinline__ void column_thomas(const DevMesh& m, int t, int a, in
     bt[i] = z0;
     bb[i] = z1;
     C0[i] = c00; C1[i] = c01; C2[i] = c10; C3[i] = c11;
-    dzm = dz;
+    idzm = idz;
     dz = dzp;
+    idz = idzp;
   }
   // back substitution x_k = z_k - C_k x_{k+1}
   R x0 = z0, x1 = z1;
@@ -219,16 +226,17 @@ __global__ void __launch_bounds__(TP) k_tracer_stage(
     const int p = tl.p0 + i;
     R out[2][3];
     prism_rh<R, false>(m, t, k, p, N, U, V, Tp, Text, eta_n, out);
-    const double w6 = m.jh[t] / 6.0;
+    const R w12 = Geo<R>::jh(m, t) * (R)(1.0 / 12.0);
     const R G2 = (R)(2.0 / 3.0), G1 = (R)(1.0 / 3.0);
     const R al = (R)alpha, be = (R)beta, dtr = (R)dt;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double h = m.h[a * nt + t];
-      const double en = eta_n[a * nt + t];
-      const double ep = en + th_p * (eta_np1[a * nt + t] - en);
-      const R mn = (R)(w6 * 0.5 * dz_at(m, h, en, k, N));
-      const R mp = (R)(w6 * 0.5 * dz_at(m, h, ep, k, N));
+      const int ia = a * nt + t;
+      const double en = eta_n[ia];
+      const double ep = en + th_p * (eta_np1[ia] - en);
+      const R dr = dz_rest_r<R>(m, ia, k, N);
+      const R mn = w12 * dr * stretch_r<R>(m, ia, en);
+      const R mp = w12 * dr * stretch_r<R>(m, ia, ep);
       const R tn0 = Tn[(size_t)(0 * 3 + a) * m.P + p], tn1 = Tn[(size_t)(1 * 3 + a) * m.P + p];
       const R tp0 = Tp[(size_t)(0 * 3 + a) * m.P + p], tp1 = Tp[(size_t)(1 * 3 + a) * m.P + p];
       s_b[a * TP + i] = al * mn * (G2 * tn0 + G1 * tn1) + be * (mp * (G2 * tp0 + G1 * tp1) + dtr * out[0][a]);
@@ -340,9 +348,9 @@ __global__ void __launch_bounds__(TP) k_mass_partial(DevMesh m, const R* __restr
     const int lt = tile_tri_of(s_off, tl.nt, i);
     const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
     const int p = tl.p0 + i, nt = m.n_tri;
-    const double w12 = m.jh[t] / 12.0;
+    const double w12 = m.jh[t] * (1.0 / 12.0);
     for (int a = 0; a < 3; ++a) {
-      const double dz = dz_at(m, m.h[a * nt + t], eta[a * nt + t], k, N);
+      const double dz = dz_r<double>(m, a * nt + t, eta[a * nt + t], k, N);
       const double x = w12 * dz * ((double)T[(size_t)a * m.P + p] + (double)T[(size_t)(3 + a) * m.P + p]);
       v = csum_add(v, {x, 0.0});
     }
