@@ -142,29 +142,41 @@ slim_status tracer_step(slim_state* s, double dt, cudaStream_t st) {
   R* W = (R*)s->W;
   const R* Text = (const R*)s->Text;
   const StageParams sp = tracer_stage_params(s);
+  const R* st0 = (const R*)s->st_cur;
+  const R* st1 = (const R*)s->st_next;
   {
     ProfScope ps(s, SLIM_PHASE_CONTINUITY, st);
-    SLIM_LAUNCH(launch_continuity<R>(m, TP, U, V, s->eta, s->eta_next, W, dt, st));
+    SLIM_LAUNCH(launch_continuity<R>(m, TP, U, V, s->eta, st0, s->eta_next, (R*)s->st_next, W, dt, st));
   }
   // Shu-Osher SSP-RK3: (alpha, beta) = (0, 1), (3/4, 1/4), (1/3, 2/3);
   // stage elevations eta^{n+1}, (eta^n + eta^{n+1})/2, eta^{n+1}
   {
     ProfScope ps(s, SLIM_PHASE_TRACER_STAGE, st);
-    SLIM_LAUNCH(launch_tracer_stage<R>(m, TP, U, V, T, T, Text, W, T1, s->eta, s->eta_next, 0.0,
+    SLIM_LAUNCH(launch_tracer_stage<R>(m, TP, U, V, T, T, Text, W, T1, st0, st1, 0.0,
                                        1.0, 0.0, 1.0, dt, sp, s->err, st));
   }
   {
     ProfScope ps(s, SLIM_PHASE_TRACER_STAGE, st);
-    SLIM_LAUNCH(launch_tracer_stage<R>(m, TP, U, V, T, T1, Text, W, T2, s->eta, s->eta_next, 1.0,
+    SLIM_LAUNCH(launch_tracer_stage<R>(m, TP, U, V, T, T1, Text, W, T2, st0, st1, 1.0,
                                        0.5, 0.75, 0.25, dt, sp, s->err, st));
   }
   {
     ProfScope ps(s, SLIM_PHASE_TRACER_STAGE, st);
-    SLIM_LAUNCH(launch_tracer_stage<R>(m, TP, U, V, T, T2, Text, W, T, s->eta, s->eta_next, 0.5,
+    SLIM_LAUNCH(launch_tracer_stage<R>(m, TP, U, V, T, T2, Text, W, T, st0, st1, 0.5,
                                        1.0, 1.0 / 3.0, 2.0 / 3.0, dt, sp, s->err, st));
   }
   SLIM_CUDA_TRY(cudaMemcpyAsync(s->eta, s->eta_next, sizeof(double) * 3 * m.n_tri,
                                 cudaMemcpyDeviceToDevice, st));
+  SLIM_CUDA_TRY(cudaMemcpyAsync(s->st_cur, s->st_next, sizeof(R) * 3 * m.n_tri,
+                                cudaMemcpyDeviceToDevice, st));
+  return SLIM_OK;
+}
+
+slim_status refresh_stretch(slim_state* s, cudaStream_t st) {
+  if (s->prec == SLIM_FP64)
+    SLIM_LAUNCH(launch_stretch<double>(s->mesh->d, s->eta, (double*)s->st_cur, st));
+  else
+    SLIM_LAUNCH(launch_stretch<float>(s->mesh->d, s->eta, (float*)s->st_cur, st));
   return SLIM_OK;
 }
 
@@ -192,6 +204,10 @@ extern "C" slim_status slim_state_alloc(const slim_mesh* m, slim_precision prec,
   double** f2[] = {&s->eta, &s->eta_next, &s->Qx, &s->Qy, &s->Qbx, &s->Qby};
   for (double** f : f2)
     if ((st = dev_alloc(s, (void**)f, n2 * sizeof(double))) != SLIM_OK) { free_state(s); return st; }
+  void** fs[] = {&s->st_cur, &s->st_next};
+  for (void** f : fs)
+    if ((st = dev_alloc(s, f, n2 * s->esz)) != SLIM_OK) { free_state(s); return st; }
+  if ((st = refresh_stretch(s, 0)) != SLIM_OK) { free_state(s); return st; }
   s->aux2d_len = split_aux2d_len(m->d);
   if ((st = dev_alloc(s, (void**)&s->aux2d, s->aux2d_len * sizeof(double))) != SLIM_OK) { free_state(s); return st; }
   s->red_blocks = m->d.n_tiles;
@@ -233,6 +249,7 @@ extern "C" slim_status slim_state_upload(slim_state* s, int field, const double*
     SLIM_LAUNCH(launch_convert_d2f(s->stage64, (float*)r.ptr, n, st));
     if (ext) SLIM_CUDA_TRY(cudaMemcpyAsync(ext, r.ptr, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
   }
+  if (field == SLIM_FIELD_ETA) return refresh_stretch(s, st);
   return SLIM_OK;
 }
 
@@ -287,7 +304,7 @@ slim_status rhs3d_t(slim_state* s, int field, void* out, cudaStream_t st) {
   const R* T = (const R*)(field == SLIM_FIELD_T ? s->T : s->S);
   const R* Text = (const R*)(field == SLIM_FIELD_T ? s->Text : s->Sext);
   SLIM_LAUNCH(launch_rhs3d<R>(s->mesh->d, tile_of(s), (const R*)s->U, (const R*)s->V, T, Text,
-                              s->eta, (R*)out, st));
+                              (const R*)s->st_cur, (R*)out, st));
   return SLIM_OK;
 }
 }  // namespace
@@ -307,10 +324,12 @@ extern "C" slim_status slim_continuity(slim_state* s, double dt, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if (s->prec == SLIM_FP64)
     SLIM_LAUNCH(launch_continuity<double>(s->mesh->d, tile_of(s), (const double*)s->U, (const double*)s->V,
-                                          s->eta, s->eta_next, (double*)s->W, dt, st));
+                                          s->eta, (const double*)s->st_cur, s->eta_next,
+                                          (double*)s->st_next, (double*)s->W, dt, st));
   else
     SLIM_LAUNCH(launch_continuity<float>(s->mesh->d, tile_of(s), (const float*)s->U, (const float*)s->V,
-                                         s->eta, s->eta_next, (float*)s->W, dt, st));
+                                         s->eta, (const float*)s->st_cur, s->eta_next,
+                                         (float*)s->st_next, (float*)s->W, dt, st));
   return SLIM_OK;
 }
 
@@ -321,10 +340,10 @@ extern "C" slim_status slim_rhs2d(slim_state* s, double t, double* out_dev, void
   if (s->par.scheme == SLIM_SCHEME_SPLIT) return split_rhs2d(s, t, out_dev, st);
   if (s->prec == SLIM_FP64)
     SLIM_LAUNCH(launch_column_divergence<double>(s->mesh->d, tile_of(s), (const double*)s->U,
-                                                 (const double*)s->V, s->eta, out_dev, st));
+                                                 (const double*)s->V, (const double*)s->st_cur, out_dev, st));
   else
     SLIM_LAUNCH(launch_column_divergence<float>(s->mesh->d, tile_of(s), (const float*)s->U,
-                                                (const float*)s->V, s->eta, out_dev, st));
+                                                (const float*)s->V, (const float*)s->st_cur, out_dev, st));
   return SLIM_OK;
 }
 
@@ -341,11 +360,11 @@ extern "C" slim_status slim_vertical_solve(slim_state* s, int field, double beta
   }
   cudaStream_t st = (cudaStream_t)stream;
   if (s->prec == SLIM_FP64)
-    SLIM_LAUNCH(launch_vertical_solve<double>(s->mesh->d, tile_of(s), (const double*)s->W, s->eta,
+    SLIM_LAUNCH(launch_vertical_solve<double>(s->mesh->d, tile_of(s), (const double*)s->W, (const double*)s->st_cur,
                                               (const double*)rhs_dev, (double*)out_dev, beta_dt, sp,
                                               s->err, st));
   else
-    SLIM_LAUNCH(launch_vertical_solve<float>(s->mesh->d, tile_of(s), (const float*)s->W, s->eta,
+    SLIM_LAUNCH(launch_vertical_solve<float>(s->mesh->d, tile_of(s), (const float*)s->W, (const float*)s->st_cur,
                                              (const float*)rhs_dev, (float*)out_dev, beta_dt, sp,
                                              s->err, st));
   return SLIM_OK;

@@ -95,7 +95,8 @@ __device__ __forceinline__ int tile_tri_of(const int* s_off, int nt, int i) {
 // ---------------------------------------------------------------------------
 // horizontal residual of one prism
 //   out[c][a] = int q T . grad(phi_a) psi_c J_h  -  sum_e int phi_a psi_c (q.n)^ T^
-// q = (dz/2) u nodal, dz at elevation eta_q.  UNIT: T = 1 (continuity).
+// q = (dz/2) u nodal, dz = dz_rest x stretch st_q of the vertex column (the stretch
+// 1 + eta/h of the elevation the transport is frozen at).  UNIT: T = 1 (continuity).
 // Volume term in closed form: with the P1 mass M2_be = J_h (1 + d_be)/24 and the
 // triple integrals G3_dfc = int psi_d psi_f psi_c (1/2 if d = f = c, else 1/6),
 //   X_c = sum_{d,f} G3_dfc sum_{b,e} M2_be q_bd T_ef,   out_vol[c][a] = grad(phi_a) . X_c
@@ -105,12 +106,12 @@ template <typename R, bool UNIT>
 __device__ __forceinline__ void prism_rh(const DevMesh& m, int t, int k, int p, int N,
                                          const R* __restrict__ U, const R* __restrict__ V,
                                          const R* __restrict__ T, const R* __restrict__ Text,
-                                         const double* __restrict__ eta_q, R out[2][3]) {
+                                         const R* __restrict__ st_q, R out[2][3]) {
   const int nt = m.n_tri, P = m.P;
   R qx[2][3], qy[2][3], Tv[2][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const R hz = (R)0.5 * dz_r<R>(m, a * nt + t, eta_q[a * nt + t], k, N);
+    const R hz = (R)0.5 * dz_rest_r<R>(m, a * nt + t, k, N) * st_q[a * nt + t];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       int idx = (c * 3 + a) * P + p;
@@ -182,7 +183,7 @@ __device__ __forceinline__ void prism_rh(const DevMesh& m, int t, int k, int p, 
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int l = j ? ((loc >> 2) & 3) : (loc & 3);
-        const R hz = (R)0.5 * dz_r<R>(m, l * nt + nb, eta_q[l * nt + nb], k, Nn);
+        const R hz = (R)0.5 * dz_rest_r<R>(m, l * nt + nb, k, Nn) * st_q[l * nt + nb];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const int idx = (c * 3 + l) * P + pn;

@@ -32,6 +32,7 @@ struct DevMesh {
   int P;            // prisms
   int n_tiles;
   int max_layers;
+  int max_tile_tris; // most triangles in one tile
   int n_levels;     // 0 for sigma layers
   const int* col_off;    // [n_tri + 1]
   const int* tile_t0;    // [n_tiles + 1] first triangle of each thread-block tile
@@ -95,6 +96,7 @@ struct slim_state {
   void* Rx = nullptr; void* Ry = nullptr;       // baroclinic pressure gradient
   // 2D fields (double)
   double* eta = nullptr; double* eta_next = nullptr;
+  void* st_cur = nullptr; void* st_next = nullptr;  // stretch 1 + eta/h per vertex column (compute type)
   double* Qx = nullptr; double* Qy = nullptr;
   double* Qbx = nullptr; double* Qby = nullptr;
   double* aux2d = nullptr;  // scratch 2D storage (split scheme)

@@ -18,30 +18,35 @@ struct StageParams {
   double flux_bot;   // prescribed kappa dT/dz at the bed
 };
 
+// stretch 1 + eta/h of every vertex column
+template <typename R>
+cudaError_t launch_stretch(const DevMesh& m, const double* eta, R* st, cudaStream_t st_);
+
 template <typename R>
 cudaError_t launch_continuity(const DevMesh& m, int TP, const R* U, const R* V, const double* eta,
-                              double* eta_out, R* W, double dt, cudaStream_t st);
+                              const R* st_cur, double* eta_out, R* st_out, R* W, double dt,
+                              cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_tracer_stage(const DevMesh& m, int TP, const R* U, const R* V, const R* Tn,
-                                const R* Tp, const R* Text, const R* W, R* Tout,
-                                const double* eta_n, const double* eta_np1, double th_p,
-                                double th_s, double alpha, double beta, double dt,
-                                const StageParams& sp, int* err, cudaStream_t st);
+                                const R* Tp, const R* Text, const R* W, R* Tout, const R* st_n,
+                                const R* st_np1, double th_p, double th_s, double alpha,
+                                double beta, double dt, const StageParams& sp, int* err,
+                                cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_rhs3d(const DevMesh& m, int TP, const R* U, const R* V, const R* T,
-                         const R* Text, const double* eta, R* out, cudaStream_t st);
+                         const R* Text, const R* st, R* out, cudaStream_t stm);
 
 template <typename R>
-cudaError_t launch_vertical_solve(const DevMesh& m, int TP, const R* W, const double* eta,
-                                  const R* rhs, R* out, double bdt, const StageParams& sp,
-                                  int* err, cudaStream_t st);
+cudaError_t launch_vertical_solve(const DevMesh& m, int TP, const R* W, const R* st, const R* rhs,
+                                  R* out, double bdt, const StageParams& sp, int* err,
+                                  cudaStream_t st_);
 
 // rhs2d of the tracer scheme: column sums of R_h(q, 1), 3*n_tri doubles
 template <typename R>
 cudaError_t launch_column_divergence(const DevMesh& m, int TP, const R* U, const R* V,
-                                     const double* eta, double* out, cudaStream_t st);
+                                     const R* st_cur, double* out, cudaStream_t st);
 
 // mass: block partials (2 doubles per tile: sum, compensation) then one final block
 template <typename R>

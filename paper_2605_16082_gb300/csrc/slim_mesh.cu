@@ -185,6 +185,9 @@ extern "C" slim_status slim_mesh_create(const double* xy, int n_vert, const int*
     cur += N;
   }
   tile_t0.push_back(nt);
+  int max_tile_tris = 0;
+  for (size_t i = 0; i + 1 < tile_t0.size(); ++i)
+    max_tile_tris = std::max(max_tile_tris, tile_t0[i + 1] - tile_t0[i]);
   std::vector<double> lev;
   if (levels) lev.assign(levels, levels + n_levels);
   std::vector<double> hN(3 * nt), ih(3 * nt);
@@ -203,6 +206,7 @@ extern "C" slim_status slim_mesh_create(const double* xy, int n_vert, const int*
   d.P = P;
   d.n_tiles = (int)tile_t0.size() - 1;
   d.max_layers = max_layers;
+  d.max_tile_tris = max_tile_tris;
   d.n_levels = levels ? n_levels : 0;
   std::vector<float> jhf(jh.begin(), jh.end()), gxf(gx.begin(), gx.end()), gyf(gy.begin(), gy.end()),
       enxf(enx.begin(), enx.end()), enyf(eny.begin(), eny.end()), elenf(elen.begin(), elen.end());

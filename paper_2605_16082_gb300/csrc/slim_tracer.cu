@@ -8,6 +8,16 @@
 // table (no atomics), results staged in shared memory.  Phase 2 is thread-per-
 // vertex-column: the column recursion or the 2x2-block Thomas sweep on shared
 // memory.  Phase 3 writes the six node planes back coalesced.
+//
+// Shared-memory slots of local prism i of local triangle lt are skewed to
+// i + lt, so that the threads of phase 2 (consecutive columns, stride N + 1)
+// and of phase 1 (consecutive layers, stride 1) avoid bank conflicts for even
+// layer counts.
+//
+// The layer geometry enters only through the per-vertex-column stretch
+// 1 + eta/h in the compute type (st arrays), so the mixed form runs no FP64
+// arithmetic in the 3D kernels; the FP64 elevation update stays in the
+// continuity kernel's column epilogue.
 #include <float.h>
 
 #include <algorithm>
@@ -17,6 +27,21 @@
 
 namespace slim {
 
+template <typename R, int TP>
+struct MinBlocks {
+  static constexpr int value = sizeof(R) == 4 ? (1024 / TP > 0 ? 1024 / TP : 1) : (512 / TP > 0 ? 512 / TP : 1);
+};
+
+// ---------------------------------------------------------------------------
+// stretch of every vertex column: st = 1 + eta (1/h)
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_stretch(DevMesh m, const double* __restrict__ eta, R* __restrict__ st) {
+  const int n = 3 * m.n_tri;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    st[i] = (R)(1.0 + eta[i] * m.ih[i]);
+}
+
 // ---------------------------------------------------------------------------
 // continuity: eta' (FP64) and the vertex-weighted vertical flux W
 //   (J_h/6)(eta' - eta)/dt = sum_column R_h(q, 1)                        (Eq. 2)
@@ -24,54 +49,61 @@ namespace slim {
 //   bottom-up D_vd recursion (Eq. 17):  s = 0 at the bed,
 //     W_{k,top} = F_top + F_bot + s,  W_{k,bot} = F_bot - F_top + s,  s = W_{k,top}
 // With DIV_ONLY the kernel writes the column sums (the depth-integrated weak
-// divergence) instead and stops.
+// divergence) to eta_out instead and stops.
 // ---------------------------------------------------------------------------
 template <typename R, int TP, bool DIV_ONLY>
-__global__ void __launch_bounds__(TP) k_continuity(DevMesh m, const R* __restrict__ U,
-                                                   const R* __restrict__ V,
-                                                   const double* __restrict__ eta,
-                                                   double* __restrict__ eta_out,
-                                                   R* __restrict__ W, double dt) {
-  __shared__ int s_off[TP + 1];
-  __shared__ R s_F[6][TP];
+__global__ void __launch_bounds__(TP, (MinBlocks<R, TP>::value))
+    k_continuity(DevMesh m, const R* __restrict__ U, const R* __restrict__ V,
+                 const double* __restrict__ eta, const R* __restrict__ st_cur,
+                 double* __restrict__ eta_out, R* __restrict__ st_out, R* __restrict__ W,
+                 double dt) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int* s_off = reinterpret_cast<int*>(smem);
+  const int TPX = TP + m.max_tile_tris;
+  R* s_F = reinterpret_cast<R*>(smem + ((TP + 1) * sizeof(int) + 15) / 16 * 16);
   const Tile tl = load_tile<TP>(m, s_off);
   const int i = threadIdx.x;
+  int slot = 0;
   if (i < tl.np) {
     const int lt = tile_tri_of(s_off, tl.nt, i);
     const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
+    slot = i + lt;
     R out[2][3];
-    prism_rh<R, true>(m, t, k, tl.p0 + i, N, U, V, nullptr, nullptr, eta, out);
+    prism_rh<R, true>(m, t, k, tl.p0 + i, N, U, V, nullptr, nullptr, st_cur, out);
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
-      for (int a = 0; a < 3; ++a) s_F[c * 3 + a][i] = out[c][a];
+      for (int a = 0; a < 3; ++a) s_F[(c * 3 + a) * TPX + slot] = out[c][a];
   }
   __syncthreads();
   const int nt = m.n_tri;
   for (int j = threadIdx.x; j < 3 * tl.nt; j += TP) {
     const int a = j / tl.nt, lt = j - a * tl.nt;
-    const int t = tl.t0 + lt, base = s_off[lt], N = s_off[lt + 1] - base;
+    const int t = tl.t0 + lt, base = s_off[lt] + lt, N = s_off[lt + 1] - s_off[lt];
+    R* Ft = s_F + a * TPX + base;
+    R* Fb = s_F + (3 + a) * TPX + base;
     double D = 0.0;
-    for (int k = 0; k < N; ++k) D += (double)s_F[a][base + k] + (double)s_F[3 + a][base + k];
+    for (int k = 0; k < N; ++k) D += (double)Ft[k] + (double)Fb[k];
+    const int ia = a * nt + t;
     if (DIV_ONLY) {
-      eta_out[a * nt + t] = D;
+      eta_out[ia] = D;
       continue;
     }
-    const int ia = a * nt + t;
     const double jh = m.jh[t];
     const double e0 = eta[ia];
     const double e1 = e0 + dt * D / (jh / 6.0);
     eta_out[ia] = e1;
+    st_out[ia] = (R)(1.0 + e1 * m.ih[ia]);
     // dz'_k - dz_k = dz_rest_k (e1 - e0) / h
-    const double dm_fac = (jh / 12.0) * (e1 - e0) * m.ih[ia] / dt;
+    const R dm_fac = (R)((jh / 12.0) * (e1 - e0) * m.ih[ia] / dt);
     R s = (R)0;
     for (int k = N - 1; k >= 0; --k) {
-      const R dm = (R)(dm_fac * dz_rest_r<double>(m, ia, k, N));
-      const R ft = s_F[a][base + k] - dm, fb = s_F[3 + a][base + k] - dm;
+      const R dm = dm_fac * dz_rest_r<R>(m, ia, k, N);
+      const R ft = Ft[k] - dm, fb = Fb[k] - dm;
       const R wt = ft + fb + s;
       const R wb = fb - ft + s;
-      s_F[a][base + k] = wt;
-      s_F[3 + a][base + k] = wb;
+      Ft[k] = wt;
+      Fb[k] = wb;
       s = wt;
     }
   }
@@ -79,40 +111,37 @@ __global__ void __launch_bounds__(TP) k_continuity(DevMesh m, const R* __restric
   __syncthreads();
   if (i < tl.np) {
 #pragma unroll
-    for (int r = 0; r < 6; ++r) W[r * m.P + tl.p0 + i] = s_F[r][i];
+    for (int r = 0; r < 6; ++r) W[(size_t)r * m.P + tl.p0 + i] = s_F[r * TPX + slot];
   }
 }
 
 // ---------------------------------------------------------------------------
-// 2x2-block Thomas sweep of one vertex column (vertex a of triangle t) on
-// shared memory.  Wt/Wb: vertex-weighted flux at the top/bottom node of every
-// layer; bt/bb: right-hand side, overwritten by the solution; C: 4 scratch rows
-// holding D'^-1 U of the forward sweep.  Indices are local prisms base + k.
+// 2x2-block Thomas sweep of one vertex column on shared memory.
+// Wt/Wb: vertex-weighted flux at the top/bottom node of every layer; bt/bb:
+// right-hand side, overwritten by the solution; C0..C3: D'^-1 U of the forward
+// sweep.  All indexed by layer k.  st: stretch of the column.
 // ---------------------------------------------------------------------------
 template <typename R>
-__device__ __forceinline__ void column_thomas(const DevMesh& m, int t, int a, int base, int N,
-                                              double eta_s, const R* Wt, const R* Wb, R* bt,
-                                              R* bb, R* C0, R* C1, R* C2, R* C3, R kap, R pen,
-                                              R bdt, R flux_top, R flux_bot) {
-  const int ia = a * m.n_tri + t;
-  const R omega = (R)(m.jh[t] * (1.0 / 6.0));
-  const R st = stretch_r<R>(m, ia, eta_s);
+__device__ __forceinline__ void column_thomas(const DevMesh& m, int t, int ia, int N, R st,
+                                              const R* Wt, const R* Wb, R* bt, R* bb, R* C0, R* C1,
+                                              R* C2, R* C3, R kap, R pen, R bdt, R flux_top,
+                                              R flux_bot) {
+  const R omega = Geo<R>::jh(m, t) * (R)(1.0 / 6.0);
   R z0 = 0, z1 = 0;
   R c00 = 0, c01 = 0, c10 = 0, c11 = 0;
   R dz = dz_rest_r<R>(m, ia, 0, N) * st;
   R idz = (R)1 / dz;
   R idzm = idz;
   for (int k = 0; k < N; ++k) {
-    const int i = base + k;
     R dzp = dz, idzp = idz;
-    if (k + 1 < N) {
+    if (k + 1 < N && m.n_levels != 0) {
       dzp = dz_rest_r<R>(m, ia, k + 1, N) * st;
-      idzp = (m.n_levels == 0) ? idz : (R)1 / dzp;
+      idzp = (R)1 / dzp;
     }
-    const R Wn = (k + 1 < N) ? Wt[i + 1] : (R)0;
+    const R Wn = (k + 1 < N) ? Wt[k + 1] : (R)0;
     Row<R> row;
-    assemble_row<R>(k, N, omega, idzm, dz, idz, idzp, Wt[i], Wb[i], Wn, kap, pen, bdt, row);
-    R b0 = bt[i], b1 = bb[i];
+    assemble_row<R>(k, N, omega, idzm, dz, idz, idzp, Wt[k], Wb[k], Wn, kap, pen, bdt, row);
+    R b0 = bt[k], b1 = bb[k];
     if (k == 0) b0 += bdt * omega * flux_top;
     if (k == N - 1) b1 -= bdt * omega * flux_bot;
     // D' = D - L C_{k-1},  y = b - L z_{k-1}
@@ -131,9 +160,9 @@ __device__ __forceinline__ void column_thomas(const DevMesh& m, int t, int a, in
     c01 = Di[0][0] * row.U[0][1] + Di[0][1] * row.U[1][1];
     c10 = Di[1][0] * row.U[0][0] + Di[1][1] * row.U[1][0];
     c11 = Di[1][0] * row.U[0][1] + Di[1][1] * row.U[1][1];
-    bt[i] = z0;
-    bb[i] = z1;
-    C0[i] = c00; C1[i] = c01; C2[i] = c10; C3[i] = c11;
+    bt[k] = z0;
+    bb[k] = z1;
+    C0[k] = c00; C1[k] = c01; C2[k] = c10; C3[k] = c11;
     idzm = idz;
     dz = dzp;
     idz = idzp;
@@ -141,50 +170,53 @@ __device__ __forceinline__ void column_thomas(const DevMesh& m, int t, int a, in
   // back substitution x_k = z_k - C_k x_{k+1}
   R x0 = z0, x1 = z1;
   for (int k = N - 2; k >= 0; --k) {
-    const int i = base + k;
-    const R n0 = bt[i] - (C0[i] * x0 + C1[i] * x1);
-    const R n1 = bb[i] - (C2[i] * x0 + C3[i] * x1);
-    bt[i] = n0;
-    bb[i] = n1;
+    const R n0 = bt[k] - (C0[k] * x0 + C1[k] * x1);
+    const R n1 = bb[k] - (C2[k] * x0 + C3[k] * x1);
+    bt[k] = n0;
+    bb[k] = n1;
     x0 = n0;
     x1 = n1;
   }
 }
 
-// shared-memory carve-up of the solve kernels
+// shared-memory carve-up of the solve kernels (TPX = TP + most triangles per tile)
 template <typename R, int TP>
 struct SolveSmem {
-  static constexpr size_t off_b = ((TP + 1) * sizeof(int) + 15) / 16 * 16;
-  static constexpr size_t off_W = off_b + 6 * TP * sizeof(R);
-  static constexpr size_t off_C = off_W + 6 * TP * sizeof(R);
-  static constexpr size_t off_eta = off_C + 12 * TP * sizeof(R);
-  static constexpr size_t bytes = off_eta + 3 * TP * sizeof(double);
+  size_t off_b, off_W, off_C, off_st, bytes;
+  __host__ __device__ SolveSmem(int TPX) {
+    off_b = ((TP + 1) * sizeof(int) + 15) / 16 * 16;
+    off_W = off_b + 6 * (size_t)TPX * sizeof(R);
+    off_C = off_W + 6 * (size_t)TPX * sizeof(R);
+    off_st = off_C + 12 * (size_t)TPX * sizeof(R);
+    bytes = off_st + 3 * (size_t)TP * sizeof(R);
+  }
 };
 
 template <typename R, int TP>
 __device__ __forceinline__ void solve_tile_columns(const DevMesh& m, const Tile& tl,
-                                                   const int* s_off, R* s_b, R* s_W, R* s_C,
-                                                   const double* s_eta, const StageParams& sp,
-                                                   double bdt) {
+                                                   const int* s_off, int TPX, R* s_b, R* s_W,
+                                                   R* s_C, const R* s_st, const StageParams& sp,
+                                                   R bdt) {
   for (int j = threadIdx.x; j < 3 * tl.nt; j += TP) {
     const int a = j / tl.nt, lt = j - a * tl.nt;
-    const int t = tl.t0 + lt, base = s_off[lt], N = s_off[lt + 1] - base;
-    R* C = s_C + (size_t)a * 4 * TP;
-    column_thomas<R>(m, t, a, base, N, s_eta[a * TP + lt], s_W + a * TP, s_W + (3 + a) * TP,
-                     s_b + a * TP, s_b + (3 + a) * TP, C, C + TP, C + 2 * TP, C + 3 * TP,
-                     (R)sp.kappa, (R)sp.penalty, (R)bdt, (R)sp.flux_top, (R)sp.flux_bot);
+    const int t = tl.t0 + lt, base = s_off[lt] + lt, N = s_off[lt + 1] - s_off[lt];
+    R* C = s_C + (size_t)a * 4 * TPX + base;
+    column_thomas<R>(m, t, a * m.n_tri + t, N, s_st[a * TP + lt], s_W + a * TPX + base,
+                     s_W + (3 + a) * TPX + base, s_b + a * TPX + base, s_b + (3 + a) * TPX + base,
+                     C, C + TPX, C + 2 * TPX, C + 3 * TPX, (R)sp.kappa, (R)sp.penalty, bdt,
+                     (R)sp.flux_top, (R)sp.flux_bot);
   }
 }
 
-template <typename R, int TP>
-__device__ __forceinline__ void write_tile(const DevMesh& m, const Tile& tl, const R* s_b,
-                                           R* out, int* __restrict__ err) {
+template <typename R>
+__device__ __forceinline__ void write_tile(const DevMesh& m, const Tile& tl, int TPX, int slot,
+                                           const R* s_b, R* out, int* __restrict__ err) {
   const int i = threadIdx.x;
   if (i < tl.np) {
     bool ok = true;
 #pragma unroll
     for (int r = 0; r < 6; ++r) {
-      const R x = s_b[r * TP + i];
+      const R x = s_b[r * TPX + slot];
       ok &= (bool)isfinite(x);
       out[(size_t)r * m.P + tl.p0 + i] = x;
     }
@@ -194,102 +226,105 @@ __device__ __forceinline__ void write_tile(const DevMesh& m, const Tile& tl, con
 
 // ---------------------------------------------------------------------------
 // SSP-RK3 stage (fused): T_out solves, per vertex column,
-//   (M(eta_s) - beta dt A) T_out = alpha M(eta_n) T_n
-//                                  + beta (M(eta_p) T_p + dt R_h(q(eta_n), T_p)) + beta dt b
-// with eta_x = (1 - th_x) eta_n + th_x eta_np1 and M the lumped 2x2 mass.
+//   (M(st_s) - beta dt A) T_out = alpha M(st_n) T_n
+//                                 + beta (M(st_p) T_p + dt R_h(q(st_n), T_p)) + beta dt b
+// with st_x = st_n + th_x (st_np1 - st_n) (the stretch is linear in eta) and M
+// the lumped mass (J_h/12) dz [[2,1],[1,2]]/3 per vertex-layer.
 // ---------------------------------------------------------------------------
 template <typename R, int TP>
-__global__ void __launch_bounds__(TP) k_tracer_stage(
+__global__ void __launch_bounds__(TP, (MinBlocks<R, TP>::value)) k_tracer_stage(
     DevMesh m, const R* __restrict__ U, const R* __restrict__ V, const R* Tn,
-    const R* __restrict__ Tp, const R* __restrict__ Text, const R* __restrict__ W,
-    R* Tout, const double* __restrict__ eta_n, const double* __restrict__ eta_np1,
-    double th_p, double th_s, double alpha, double beta, double dt, StageParams sp,
-    int* __restrict__ err) {
+    const R* __restrict__ Tp, const R* __restrict__ Text, const R* __restrict__ W, R* Tout,
+    const R* __restrict__ st_n, const R* __restrict__ st_np1, R th_p, R th_s, R alpha, R beta,
+    R dt, StageParams sp, int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem[];
-  using L = SolveSmem<R, TP>;
+  const int TPX = TP + m.max_tile_tris;
+  const SolveSmem<R, TP> L(TPX);
   int* s_off = reinterpret_cast<int*>(smem);
-  R* s_b = reinterpret_cast<R*>(smem + L::off_b);
-  R* s_W = reinterpret_cast<R*>(smem + L::off_W);
-  R* s_C = reinterpret_cast<R*>(smem + L::off_C);
-  double* s_eta = reinterpret_cast<double*>(smem + L::off_eta);
+  R* s_b = reinterpret_cast<R*>(smem + L.off_b);
+  R* s_W = reinterpret_cast<R*>(smem + L.off_W);
+  R* s_C = reinterpret_cast<R*>(smem + L.off_C);
+  R* s_st = reinterpret_cast<R*>(smem + L.off_st);
   const Tile tl = load_tile<TP>(m, s_off);
   const int nt = m.n_tri;
   for (int j = threadIdx.x; j < 3 * tl.nt; j += TP) {
-    const int a = j / tl.nt, lt = j - a * tl.nt, t = tl.t0 + lt;
-    const double en = eta_n[a * nt + t];
-    s_eta[a * TP + lt] = en + th_s * (eta_np1[a * nt + t] - en);
+    const int a = j / tl.nt, lt = j - a * tl.nt, ia = a * nt + tl.t0 + lt;
+    const R s0 = st_n[ia];
+    s_st[a * TP + lt] = s0 + th_s * (st_np1[ia] - s0);
   }
   const int i = threadIdx.x;
+  int slot = 0;
   if (i < tl.np) {
     const int lt = tile_tri_of(s_off, tl.nt, i);
     const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
     const int p = tl.p0 + i;
+    slot = i + lt;
     R out[2][3];
-    prism_rh<R, false>(m, t, k, p, N, U, V, Tp, Text, eta_n, out);
+    prism_rh<R, false>(m, t, k, p, N, U, V, Tp, Text, st_n, out);
     const R w12 = Geo<R>::jh(m, t) * (R)(1.0 / 12.0);
     const R G2 = (R)(2.0 / 3.0), G1 = (R)(1.0 / 3.0);
-    const R al = (R)alpha, be = (R)beta, dtr = (R)dt;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const int ia = a * nt + t;
-      const double en = eta_n[ia];
-      const double ep = en + th_p * (eta_np1[ia] - en);
-      const R dr = dz_rest_r<R>(m, ia, k, N);
-      const R mn = w12 * dr * stretch_r<R>(m, ia, en);
-      const R mp = w12 * dr * stretch_r<R>(m, ia, ep);
+      const R sn = st_n[ia];
+      const R sp_ = sn + th_p * (st_np1[ia] - sn);
+      const R dr = w12 * dz_rest_r<R>(m, ia, k, N);
+      const R mn = dr * sn;
+      const R mp = dr * sp_;
       const R tn0 = Tn[(size_t)(0 * 3 + a) * m.P + p], tn1 = Tn[(size_t)(1 * 3 + a) * m.P + p];
       const R tp0 = Tp[(size_t)(0 * 3 + a) * m.P + p], tp1 = Tp[(size_t)(1 * 3 + a) * m.P + p];
-      s_b[a * TP + i] = al * mn * (G2 * tn0 + G1 * tn1) + be * (mp * (G2 * tp0 + G1 * tp1) + dtr * out[0][a]);
-      s_b[(3 + a) * TP + i] = al * mn * (G1 * tn0 + G2 * tn1) + be * (mp * (G1 * tp0 + G2 * tp1) + dtr * out[1][a]);
+      s_b[a * TPX + slot] = alpha * mn * (G2 * tn0 + G1 * tn1) + beta * (mp * (G2 * tp0 + G1 * tp1) + dt * out[0][a]);
+      s_b[(3 + a) * TPX + slot] = alpha * mn * (G1 * tn0 + G2 * tn1) + beta * (mp * (G1 * tp0 + G2 * tp1) + dt * out[1][a]);
     }
 #pragma unroll
-    for (int r = 0; r < 6; ++r) s_W[r * TP + i] = W[(size_t)r * m.P + p];
+    for (int r = 0; r < 6; ++r) s_W[r * TPX + slot] = W[(size_t)r * m.P + p];
   }
   __syncthreads();
-  solve_tile_columns<R, TP>(m, tl, s_off, s_b, s_W, s_C, s_eta, sp, beta * dt);
+  solve_tile_columns<R, TP>(m, tl, s_off, TPX, s_b, s_W, s_C, s_st, sp, beta * dt);
   __syncthreads();
-  write_tile<R, TP>(m, tl, s_b, Tout, err);
+  write_tile<R>(m, tl, TPX, slot, s_b, Tout, err);
 }
 
-// standalone vertical solve: (M(eta) - bdt A) x = rhs + bdt b
+// standalone vertical solve: (M(st) - bdt A) x = rhs + bdt b
 template <typename R, int TP>
-__global__ void __launch_bounds__(TP) k_vertical_solve(DevMesh m, const R* __restrict__ W,
-                                                       const double* __restrict__ eta,
-                                                       const R* rhs, R* out, double bdt,
-                                                       StageParams sp, int* __restrict__ err) {
+__global__ void __launch_bounds__(TP, (MinBlocks<R, TP>::value))
+    k_vertical_solve(DevMesh m, const R* __restrict__ W, const R* __restrict__ st, const R* rhs,
+                     R* out, R bdt, StageParams sp, int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem[];
-  using L = SolveSmem<R, TP>;
+  const int TPX = TP + m.max_tile_tris;
+  const SolveSmem<R, TP> L(TPX);
   int* s_off = reinterpret_cast<int*>(smem);
-  R* s_b = reinterpret_cast<R*>(smem + L::off_b);
-  R* s_W = reinterpret_cast<R*>(smem + L::off_W);
-  R* s_C = reinterpret_cast<R*>(smem + L::off_C);
-  double* s_eta = reinterpret_cast<double*>(smem + L::off_eta);
+  R* s_b = reinterpret_cast<R*>(smem + L.off_b);
+  R* s_W = reinterpret_cast<R*>(smem + L.off_W);
+  R* s_C = reinterpret_cast<R*>(smem + L.off_C);
+  R* s_st = reinterpret_cast<R*>(smem + L.off_st);
   const Tile tl = load_tile<TP>(m, s_off);
   const int nt = m.n_tri;
   for (int j = threadIdx.x; j < 3 * tl.nt; j += TP) {
     const int a = j / tl.nt, lt = j - a * tl.nt;
-    s_eta[a * TP + lt] = eta[a * nt + tl.t0 + lt];
+    s_st[a * TP + lt] = st[a * nt + tl.t0 + lt];
   }
   const int i = threadIdx.x;
+  int slot = 0;
   if (i < tl.np) {
+    slot = i + tile_tri_of(s_off, tl.nt, i);
 #pragma unroll
     for (int r = 0; r < 6; ++r) {
-      s_b[r * TP + i] = rhs[(size_t)r * m.P + tl.p0 + i];
-      s_W[r * TP + i] = W[(size_t)r * m.P + tl.p0 + i];
+      s_b[r * TPX + slot] = rhs[(size_t)r * m.P + tl.p0 + i];
+      s_W[r * TPX + slot] = W[(size_t)r * m.P + tl.p0 + i];
     }
   }
   __syncthreads();
-  solve_tile_columns<R, TP>(m, tl, s_off, s_b, s_W, s_C, s_eta, sp, bdt);
+  solve_tile_columns<R, TP>(m, tl, s_off, TPX, s_b, s_W, s_C, s_st, sp, bdt);
   __syncthreads();
-  write_tile<R, TP>(m, tl, s_b, out, err);
+  write_tile<R>(m, tl, TPX, slot, s_b, out, err);
 }
 
 // standalone horizontal residual
 template <typename R, int TP>
-__global__ void __launch_bounds__(TP) k_rhs3d(DevMesh m, const R* __restrict__ U,
-                                              const R* __restrict__ V, const R* __restrict__ T,
-                                              const R* __restrict__ Text,
-                                              const double* __restrict__ eta, R* __restrict__ out) {
+__global__ void __launch_bounds__(TP, (MinBlocks<R, TP>::value))
+    k_rhs3d(DevMesh m, const R* __restrict__ U, const R* __restrict__ V, const R* __restrict__ T,
+            const R* __restrict__ Text, const R* __restrict__ st, R* __restrict__ out) {
   __shared__ int s_off[TP + 1];
   const Tile tl = load_tile<TP>(m, s_off);
   const int i = threadIdx.x;
@@ -297,7 +332,7 @@ __global__ void __launch_bounds__(TP) k_rhs3d(DevMesh m, const R* __restrict__ U
   const int lt = tile_tri_of(s_off, tl.nt, i);
   const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
   R o[2][3];
-  prism_rh<R, false>(m, t, k, tl.p0 + i, N, U, V, T, Text, eta, o);
+  prism_rh<R, false>(m, t, k, tl.p0 + i, N, U, V, T, Text, st, o);
 #pragma unroll
   for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -306,7 +341,8 @@ __global__ void __launch_bounds__(TP) k_rhs3d(DevMesh m, const R* __restrict__ U
 
 // ---------------------------------------------------------------------------
 // tracer mass sum_nodes (M T) = sum_p sum_a (J_h/12) dz_a (T_top,a + T_bot,a),
-// compensated pairwise (TwoSum) reduction in a fixed order: deterministic.
+// in FP64 with a compensated pairwise (TwoSum) reduction in a fixed order:
+// deterministic for a given mesh.
 // ---------------------------------------------------------------------------
 struct CSum {
   double s, c;
@@ -387,12 +423,12 @@ __global__ void k_f2d(const float* __restrict__ in, double* __restrict__ out, si
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-#define SLIM_TP_SWITCH(TP, ...) \
-  switch (TP) {                  \
-    case 128: { constexpr int TPc = 128; __VA_ARGS__; } break; \
-    case 256: { constexpr int TPc = 256; __VA_ARGS__; } break; \
-    case 512: { constexpr int TPc = 512; __VA_ARGS__; } break; \
-    default: return cudaErrorInvalidValue;              \
+#define SLIM_TP_SWITCH(TP, ...)                                   \
+  switch (TP) {                                                   \
+    case 128: { constexpr int TPc = 128; __VA_ARGS__; } break;    \
+    case 256: { constexpr int TPc = 256; __VA_ARGS__; } break;    \
+    case 512: { constexpr int TPc = 512; __VA_ARGS__; } break;    \
+    default: return cudaErrorInvalidValue;                        \
   }
 
 template <typename KernelT>
@@ -401,94 +437,117 @@ static cudaError_t set_smem(KernelT kern, size_t bytes) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+static size_t cont_smem(const DevMesh& m, int TP, size_t esz) {
+  return ((TP + 1) * sizeof(int) + 15) / 16 * 16 + 6 * (size_t)(TP + m.max_tile_tris) * esz;
+}
+
+template <typename R>
+cudaError_t launch_stretch(const DevMesh& m, const double* eta, R* st, cudaStream_t stm) {
+  const int n = 3 * m.n_tri;
+  k_stretch<R><<<std::min((n + 255) / 256, 2048), 256, 0, stm>>>(m, eta, st);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_continuity(const DevMesh& m, int TP, const R* U, const R* V, const double* eta,
-                              double* eta_out, R* W, double dt, cudaStream_t st) {
-  SLIM_TP_SWITCH(TP, (k_continuity<R, TPc, false><<<m.n_tiles, TPc, 0, st>>>(m, U, V, eta, eta_out, W, dt)));
-  return cudaGetLastError();
-}
-
-template <typename R>
-cudaError_t launch_column_divergence(const DevMesh& m, int TP, const R* U, const R* V,
-                                     const double* eta, double* out, cudaStream_t st) {
-  SLIM_TP_SWITCH(TP, (k_continuity<R, TPc, true><<<m.n_tiles, TPc, 0, st>>>(m, U, V, eta, out, nullptr, 0.0)));
-  return cudaGetLastError();
-}
-
-template <typename R>
-cudaError_t launch_tracer_stage(const DevMesh& m, int TP, const R* U, const R* V, const R* Tn,
-                                const R* Tp, const R* Text, const R* W, R* Tout,
-                                const double* eta_n, const double* eta_np1, double th_p,
-                                double th_s, double alpha, double beta, double dt,
-                                const StageParams& sp, int* err, cudaStream_t st) {
+                              const R* st_cur, double* eta_out, R* st_out, R* W, double dt,
+                              cudaStream_t stm) {
   SLIM_TP_SWITCH(TP, {
-    const size_t sm = SolveSmem<R, TPc>::bytes;
-    cudaError_t e = set_smem(k_tracer_stage<R, TPc>, sm);
+    const size_t sm = cont_smem(m, TPc, sizeof(R));
+    cudaError_t e = set_smem(k_continuity<R, TPc, false>, sm);
     if (e != cudaSuccess) return e;
-    k_tracer_stage<R, TPc><<<m.n_tiles, TPc, sm, st>>>(m, U, V, Tn, Tp, Text, W, Tout, eta_n,
-                                                       eta_np1, th_p, th_s, alpha, beta, dt, sp, err);
+    k_continuity<R, TPc, false><<<m.n_tiles, TPc, sm, stm>>>(m, U, V, eta, st_cur, eta_out, st_out, W, dt);
   });
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_vertical_solve(const DevMesh& m, int TP, const R* W, const double* eta,
-                                  const R* rhs, R* out, double bdt, const StageParams& sp,
-                                  int* err, cudaStream_t st) {
+cudaError_t launch_column_divergence(const DevMesh& m, int TP, const R* U, const R* V,
+                                     const R* st_cur, double* out, cudaStream_t stm) {
   SLIM_TP_SWITCH(TP, {
-    const size_t sm = SolveSmem<R, TPc>::bytes;
+    const size_t sm = cont_smem(m, TPc, sizeof(R));
+    cudaError_t e = set_smem(k_continuity<R, TPc, true>, sm);
+    if (e != cudaSuccess) return e;
+    k_continuity<R, TPc, true><<<m.n_tiles, TPc, sm, stm>>>(m, U, V, nullptr, st_cur, out, nullptr, nullptr, 0.0);
+  });
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_tracer_stage(const DevMesh& m, int TP, const R* U, const R* V, const R* Tn,
+                                const R* Tp, const R* Text, const R* W, R* Tout, const R* st_n,
+                                const R* st_np1, double th_p, double th_s, double alpha,
+                                double beta, double dt, const StageParams& sp, int* err,
+                                cudaStream_t stm) {
+  SLIM_TP_SWITCH(TP, {
+    const size_t sm = SolveSmem<R, TPc>(TPc + m.max_tile_tris).bytes;
+    cudaError_t e = set_smem(k_tracer_stage<R, TPc>, sm);
+    if (e != cudaSuccess) return e;
+    k_tracer_stage<R, TPc><<<m.n_tiles, TPc, sm, stm>>>(m, U, V, Tn, Tp, Text, W, Tout, st_n, st_np1,
+                                                        (R)th_p, (R)th_s, (R)alpha, (R)beta, (R)dt,
+                                                        sp, err);
+  });
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_vertical_solve(const DevMesh& m, int TP, const R* W, const R* st, const R* rhs,
+                                  R* out, double bdt, const StageParams& sp, int* err,
+                                  cudaStream_t stm) {
+  SLIM_TP_SWITCH(TP, {
+    const size_t sm = SolveSmem<R, TPc>(TPc + m.max_tile_tris).bytes;
     cudaError_t e = set_smem(k_vertical_solve<R, TPc>, sm);
     if (e != cudaSuccess) return e;
-    k_vertical_solve<R, TPc><<<m.n_tiles, TPc, sm, st>>>(m, W, eta, rhs, out, bdt, sp, err);
+    k_vertical_solve<R, TPc><<<m.n_tiles, TPc, sm, stm>>>(m, W, st, rhs, out, (R)bdt, sp, err);
   });
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_rhs3d(const DevMesh& m, int TP, const R* U, const R* V, const R* T,
-                         const R* Text, const double* eta, R* out, cudaStream_t st) {
-  SLIM_TP_SWITCH(TP, (k_rhs3d<R, TPc><<<m.n_tiles, TPc, 0, st>>>(m, U, V, T, Text, eta, out)));
+                         const R* Text, const R* st, R* out, cudaStream_t stm) {
+  SLIM_TP_SWITCH(TP, (k_rhs3d<R, TPc><<<m.n_tiles, TPc, 0, stm>>>(m, U, V, T, Text, st, out)));
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_mass(const DevMesh& m, int TP, const R* T, const double* eta, double* partials,
-                        double* result, cudaStream_t st) {
-  SLIM_TP_SWITCH(TP, (k_mass_partial<R, TPc><<<m.n_tiles, TPc, 0, st>>>(m, T, eta, partials)));
+                        double* result, cudaStream_t stm) {
+  SLIM_TP_SWITCH(TP, (k_mass_partial<R, TPc><<<m.n_tiles, TPc, 0, stm>>>(m, T, eta, partials)));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_mass_final<256><<<1, 256, 0, st>>>(partials, m.n_tiles, result);
+  k_mass_final<256><<<1, 256, 0, stm>>>(partials, m.n_tiles, result);
   return cudaGetLastError();
 }
 
-cudaError_t launch_convert_d2f(const double* in, float* out, size_t n, cudaStream_t st) {
+cudaError_t launch_convert_d2f(const double* in, float* out, size_t n, cudaStream_t stm) {
   if (n == 0) return cudaSuccess;
   int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
-  k_d2f<<<blocks, 256, 0, st>>>(in, out, n);
+  k_d2f<<<blocks, 256, 0, stm>>>(in, out, n);
   return cudaGetLastError();
 }
-cudaError_t launch_convert_f2d(const float* in, double* out, size_t n, cudaStream_t st) {
+cudaError_t launch_convert_f2d(const float* in, double* out, size_t n, cudaStream_t stm) {
   if (n == 0) return cudaSuccess;
   int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
-  k_f2d<<<blocks, 256, 0, st>>>(in, out, n);
+  k_f2d<<<blocks, 256, 0, stm>>>(in, out, n);
   return cudaGetLastError();
 }
 
-#define SLIM_INSTANTIATE(R)                                                                        \
-  template cudaError_t launch_continuity<R>(const DevMesh&, int, const R*, const R*, const double*, \
-                                            double*, R*, double, cudaStream_t);                     \
-  template cudaError_t launch_column_divergence<R>(const DevMesh&, int, const R*, const R*,         \
-                                                   const double*, double*, cudaStream_t);           \
-  template cudaError_t launch_tracer_stage<R>(const DevMesh&, int, const R*, const R*, const R*,    \
-                                              const R*, const R*, const R*, R*, const double*,      \
-                                              const double*, double, double, double, double,        \
-                                              double, const StageParams&, int*, cudaStream_t);      \
-  template cudaError_t launch_vertical_solve<R>(const DevMesh&, int, const R*, const double*,       \
-                                                const R*, R*, double, const StageParams&, int*,     \
-                                                cudaStream_t);                                      \
-  template cudaError_t launch_rhs3d<R>(const DevMesh&, int, const R*, const R*, const R*, const R*, \
-                                       const double*, R*, cudaStream_t);                            \
-  template cudaError_t launch_mass<R>(const DevMesh&, int, const R*, const double*, double*,        \
+#define SLIM_INSTANTIATE(R)                                                                         \
+  template cudaError_t launch_stretch<R>(const DevMesh&, const double*, R*, cudaStream_t);          \
+  template cudaError_t launch_continuity<R>(const DevMesh&, int, const R*, const R*, const double*,  \
+                                            const R*, double*, R*, R*, double, cudaStream_t);        \
+  template cudaError_t launch_column_divergence<R>(const DevMesh&, int, const R*, const R*,          \
+                                                   const R*, double*, cudaStream_t);                 \
+  template cudaError_t launch_tracer_stage<R>(const DevMesh&, int, const R*, const R*, const R*,     \
+                                              const R*, const R*, const R*, R*, const R*, const R*,  \
+                                              double, double, double, double, double,                \
+                                              const StageParams&, int*, cudaStream_t);               \
+  template cudaError_t launch_vertical_solve<R>(const DevMesh&, int, const R*, const R*, const R*,   \
+                                                R*, double, const StageParams&, int*, cudaStream_t); \
+  template cudaError_t launch_rhs3d<R>(const DevMesh&, int, const R*, const R*, const R*, const R*,  \
+                                       const R*, R*, cudaStream_t);                                  \
+  template cudaError_t launch_mass<R>(const DevMesh&, int, const R*, const double*, double*,         \
                                       double*, cudaStream_t);
 
 SLIM_INSTANTIATE(double)
