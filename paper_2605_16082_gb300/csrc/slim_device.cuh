@@ -70,17 +70,31 @@ struct Tile {
   int t0, nt, p0, np;
 };
 
-template <int TP>
-__device__ __forceinline__ Tile load_tile(const DevMesh& m, int* s_off) {
+__device__ __forceinline__ Tile tile_of_block(const DevMesh& m) {
+  const int4 ti = m.tile_info[blockIdx.x];
   Tile tl;
-  tl.t0 = m.tile_t0[blockIdx.x];
-  tl.nt = m.tile_t0[blockIdx.x + 1] - tl.t0;
-  tl.p0 = m.col_off[tl.t0];
-  for (int i = threadIdx.x; i <= tl.nt; i += TP) s_off[i] = m.col_off[tl.t0 + i] - tl.p0;
-  __syncthreads();
-  tl.np = s_off[tl.nt];
+  tl.t0 = ti.x; tl.nt = ti.y; tl.p0 = ti.z; tl.np = ti.w;
   return tl;
 }
+
+// local column offsets of the tile into shared memory (ends with a barrier)
+template <int TP>
+__device__ __forceinline__ void load_offsets(const DevMesh& m, const Tile& tl, int* s_off) {
+  for (int i = threadIdx.x; i <= tl.nt; i += TP) s_off[i] = m.col_off[tl.t0 + i] - tl.p0;
+  __syncthreads();
+}
+
+template <int TP>
+__device__ __forceinline__ Tile load_tile(const DevMesh& m, int* s_off) {
+  const Tile tl = tile_of_block(m);
+  load_offsets<TP>(m, tl, s_off);
+  return tl;
+}
+
+// reciprocal: fast approximate for the FP32 form, exact division in FP64
+template <typename R> __device__ __forceinline__ R rcp(R x);
+template <> __device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.0f, x); }
+template <> __device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
 
 // local triangle of local prism i (largest j with s_off[j] <= i)
 __device__ __forceinline__ int tile_tri_of(const int* s_off, int nt, int i) {
@@ -102,10 +116,32 @@ __device__ __forceinline__ int tile_tri_of(const int* s_off, int nt, int i) {
 //   X_c = sum_{d,f} G3_dfc sum_{b,e} M2_be q_bd T_ef,   out_vol[c][a] = grad(phi_a) . X_c
 // Lateral faces: 2 x 2 Gauss points, mean transport of both sides, upwind T.
 // ---------------------------------------------------------------------------
+// Node values of one prism, loaded before the tile barrier so that these loads
+// overlap the tile set-up.
+template <typename R>
+struct Own {
+  R u[2][3], v[2][3], T[2][3];
+};
+template <typename R, bool UNIT>
+__device__ __forceinline__ void load_own(const DevMesh& m, int p, const R* __restrict__ U,
+                                         const R* __restrict__ V, const R* __restrict__ T,
+                                         Own<R>& o) {
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const size_t idx = (size_t)(c * 3 + a) * m.P + p;
+      o.u[c][a] = U[idx];
+      o.v[c][a] = V[idx];
+      o.T[c][a] = UNIT ? (R)1 : T[idx];
+    }
+}
+
 template <typename R, bool UNIT>
 __device__ __forceinline__ void prism_rh(const DevMesh& m, int t, int k, int p, int N,
-                                         const R* __restrict__ U, const R* __restrict__ V,
-                                         const R* __restrict__ T, const R* __restrict__ Text,
+                                         const Own<R>& own, const R* __restrict__ U,
+                                         const R* __restrict__ V, const R* __restrict__ T,
+                                         const R* __restrict__ Text,
                                          const R* __restrict__ st_q, R out[2][3]) {
   const int nt = m.n_tri, P = m.P;
   R qx[2][3], qy[2][3], Tv[2][3];
@@ -114,10 +150,9 @@ __device__ __forceinline__ void prism_rh(const DevMesh& m, int t, int k, int p, 
     const R hz = (R)0.5 * dz_rest_r<R>(m, a * nt + t, k, N) * st_q[a * nt + t];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      int idx = (c * 3 + a) * P + p;
-      qx[c][a] = hz * U[idx];
-      qy[c][a] = hz * V[idx];
-      Tv[c][a] = UNIT ? (R)1 : T[idx];
+      qx[c][a] = hz * own.u[c][a];
+      qy[c][a] = hz * own.v[c][a];
+      Tv[c][a] = UNIT ? (R)1 : own.T[c][a];
     }
   }
   const R jh = Geo<R>::jh(m, t);
@@ -159,7 +194,8 @@ __device__ __forceinline__ void prism_rh(const DevMesh& m, int t, int k, int p, 
   // lateral faces
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
-    const int nb = m.nbr[e * nt + t];
+    const int4 ei = m.einfo[e * nt + t];
+    const int nb = ei.x;
     if (nb == -1) continue;  // wall
     const int a0 = e, a1 = (e + 1) % 3;
     const R nxe = Geo<R>::nx(m, e * nt + t), nye = Geo<R>::ny(m, e * nt + t);
@@ -174,19 +210,18 @@ __device__ __forceinline__ void prism_rh(const DevMesh& m, int t, int k, int p, 
     }
     bool has_nb = false;
     if (nb >= 0) {
-      const int off = m.col_off[nb];
-      const int Nn = m.col_off[nb + 1] - off;
+      const int Nn = ei.z;
       if (k >= Nn) continue;  // wall against a shallower neighbour column
       has_nb = true;
-      const int pn = off + k;
-      const int loc = m.nloc[e * nt + t];
+      const int pn = ei.y + k;
+      const int loc = ei.w;
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int l = j ? ((loc >> 2) & 3) : (loc & 3);
         const R hz = (R)0.5 * dz_rest_r<R>(m, l * nt + nb, k, Nn) * st_q[l * nt + nb];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          const int idx = (c * 3 + l) * P + pn;
+          const size_t idx = (size_t)(c * 3 + l) * P + pn;
           qb[j][c] = hz * (U[idx] * nxe + V[idx] * nye);
           Tb[j][c] = UNIT ? (R)1 : T[idx];
         }
@@ -198,7 +233,7 @@ __device__ __forceinline__ void prism_rh(const DevMesh& m, int t, int k, int p, 
         for (int c = 0; c < 2; ++c) {
           qb[j][c] = qo[j][c];
           Tb[j][c] = (UNIT || Text == nullptr) ? To[j][c]
-                                               : Text[(c * 3 + (j ? a1 : a0)) * P + p];
+                                               : Text[(size_t)(c * 3 + (j ? a1 : a0)) * P + p];
         }
     }
 #pragma unroll
@@ -302,7 +337,7 @@ __device__ __forceinline__ void assemble_row(int k, int N, R omega, R idzm, R dz
 // 2x2 helpers
 template <typename R>
 __device__ __forceinline__ void inv2(const R a[2][2], R o[2][2]) {
-  const R r = (R)1 / (a[0][0] * a[1][1] - a[0][1] * a[1][0]);
+  const R r = rcp<R>(a[0][0] * a[1][1] - a[0][1] * a[1][0]);
   o[0][0] = a[1][1] * r; o[0][1] = -a[0][1] * r;
   o[1][0] = -a[1][0] * r; o[1][1] = a[0][0] * r;
 }

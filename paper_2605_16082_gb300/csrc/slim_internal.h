@@ -36,6 +36,9 @@ struct DevMesh {
   int n_levels;     // 0 for sigma layers
   const int* col_off;    // [n_tri + 1]
   const int* tile_t0;    // [n_tiles + 1] first triangle of each thread-block tile
+  const int4* tile_info; // [n_tiles] (first triangle, triangles, first prism, prisms)
+  const int4* einfo;     // [3][n_tri] per edge: (neighbour or -1 wall / -2 open, its first
+                         // prism, its layer count, neighbour-local vertices l0 | l1 << 2)
   const double* jh;      // [n_tri] 2 x triangle area
   const double* gx;      // [3][n_tri] d phi_a / dx
   const double* gy;      // [3][n_tri]

@@ -186,8 +186,19 @@ extern "C" slim_status slim_mesh_create(const double* xy, int n_vert, const int*
   }
   tile_t0.push_back(nt);
   int max_tile_tris = 0;
-  for (size_t i = 0; i + 1 < tile_t0.size(); ++i)
-    max_tile_tris = std::max(max_tile_tris, tile_t0[i + 1] - tile_t0[i]);
+  std::vector<int4> tile_info(tile_t0.size() - 1);
+  for (size_t i = 0; i + 1 < tile_t0.size(); ++i) {
+    const int a = tile_t0[i], b = tile_t0[i + 1];
+    max_tile_tris = std::max(max_tile_tris, b - a);
+    tile_info[i] = make_int4(a, b - a, col_off[a], col_off[b] - col_off[a]);
+  }
+  std::vector<int4> einfo(3 * (size_t)nt);
+  for (int e = 0; e < 3; ++e)
+    for (int t = 0; t < nt; ++t) {
+      const int nb = nbr[e * nt + t];
+      einfo[e * nt + t] = nb >= 0 ? make_int4(nb, col_off[nb], col_off[nb + 1] - col_off[nb], nloc[e * nt + t])
+                                  : make_int4(nb, 0, 0, 0);
+    }
   std::vector<double> lev;
   if (levels) lev.assign(levels, levels + n_levels);
   std::vector<double> hN(3 * nt), ih(3 * nt);
@@ -218,6 +229,8 @@ extern "C" slim_status slim_mesh_create(const double* xy, int n_vert, const int*
   }
   UP(col_off, col_off);
   UP(tile_t0, tile_t0);
+  UP(tile_info, tile_info);
+  UP(einfo, einfo);
   UP(jh, jh);
   UP(gx, gx);
   UP(gy, gy);

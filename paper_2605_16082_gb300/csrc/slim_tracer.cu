@@ -61,15 +61,18 @@ __global__ void __launch_bounds__(TP, (MinBlocks<R, TP>::value))
   int* s_off = reinterpret_cast<int*>(smem);
   const int TPX = TP + m.max_tile_tris;
   R* s_F = reinterpret_cast<R*>(smem + ((TP + 1) * sizeof(int) + 15) / 16 * 16);
-  const Tile tl = load_tile<TP>(m, s_off);
+  const Tile tl = tile_of_block(m);
   const int i = threadIdx.x;
+  Own<R> own;
+  if (i < tl.np) load_own<R, true>(m, tl.p0 + i, U, V, nullptr, own);
+  load_offsets<TP>(m, tl, s_off);
   int slot = 0;
   if (i < tl.np) {
     const int lt = tile_tri_of(s_off, tl.nt, i);
     const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
     slot = i + lt;
     R out[2][3];
-    prism_rh<R, true>(m, t, k, tl.p0 + i, N, U, V, nullptr, nullptr, st_cur, out);
+    prism_rh<R, true>(m, t, k, tl.p0 + i, N, own, U, V, nullptr, nullptr, st_cur, out);
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -82,8 +85,10 @@ __global__ void __launch_bounds__(TP, (MinBlocks<R, TP>::value))
     const int t = tl.t0 + lt, base = s_off[lt] + lt, N = s_off[lt + 1] - s_off[lt];
     R* Ft = s_F + a * TPX + base;
     R* Fb = s_F + (3 + a) * TPX + base;
+    // FP64 column sum (each layer's two node values are added in the compute type
+    // first: that rounding is of the order of the inputs' own)
     double D = 0.0;
-    for (int k = 0; k < N; ++k) D += (double)Ft[k] + (double)Fb[k];
+    for (int k = 0; k < N; ++k) D += (double)(Ft[k] + Fb[k]);
     const int ia = a * nt + t;
     if (DIV_ONLY) {
       eta_out[ia] = D;
@@ -123,20 +128,23 @@ __global__ void __launch_bounds__(TP, (MinBlocks<R, TP>::value))
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ void column_thomas(const DevMesh& m, int t, int ia, int N, R st,
-                                              const R* Wt, const R* Wb, R* bt, R* bb, R* C0, R* C1,
-                                              R* C2, R* C3, R kap, R pen, R bdt, R flux_top,
-                                              R flux_bot) {
+                                              const R* __restrict__ Wt, const R* __restrict__ Wb,
+                                              R* __restrict__ bt, R* __restrict__ bb,
+                                              R* __restrict__ C0, R* __restrict__ C1,
+                                              R* __restrict__ C2, R* __restrict__ C3, R kap, R pen,
+                                              R bdt, R flux_top, R flux_bot) {
   const R omega = Geo<R>::jh(m, t) * (R)(1.0 / 6.0);
   R z0 = 0, z1 = 0;
   R c00 = 0, c01 = 0, c10 = 0, c11 = 0;
   R dz = dz_rest_r<R>(m, ia, 0, N) * st;
-  R idz = (R)1 / dz;
+  R idz = rcp<R>(dz);
   R idzm = idz;
+#pragma unroll 2
   for (int k = 0; k < N; ++k) {
     R dzp = dz, idzp = idz;
     if (k + 1 < N && m.n_levels != 0) {
       dzp = dz_rest_r<R>(m, ia, k + 1, N) * st;
-      idzp = (R)1 / dzp;
+      idzp = rcp<R>(dzp);
     }
     const R Wn = (k + 1 < N) ? Wt[k + 1] : (R)0;
     Row<R> row;
@@ -245,14 +253,17 @@ __global__ void __launch_bounds__(TP, (MinBlocks<R, TP>::value)) k_tracer_stage(
   R* s_W = reinterpret_cast<R*>(smem + L.off_W);
   R* s_C = reinterpret_cast<R*>(smem + L.off_C);
   R* s_st = reinterpret_cast<R*>(smem + L.off_st);
-  const Tile tl = load_tile<TP>(m, s_off);
+  const Tile tl = tile_of_block(m);
+  const int i = threadIdx.x;
+  Own<R> own;
+  if (i < tl.np) load_own<R, false>(m, tl.p0 + i, U, V, Tp, own);
   const int nt = m.n_tri;
   for (int j = threadIdx.x; j < 3 * tl.nt; j += TP) {
     const int a = j / tl.nt, lt = j - a * tl.nt, ia = a * nt + tl.t0 + lt;
     const R s0 = st_n[ia];
     s_st[a * TP + lt] = s0 + th_s * (st_np1[ia] - s0);
   }
-  const int i = threadIdx.x;
+  load_offsets<TP>(m, tl, s_off);
   int slot = 0;
   if (i < tl.np) {
     const int lt = tile_tri_of(s_off, tl.nt, i);
@@ -260,7 +271,7 @@ __global__ void __launch_bounds__(TP, (MinBlocks<R, TP>::value)) k_tracer_stage(
     const int p = tl.p0 + i;
     slot = i + lt;
     R out[2][3];
-    prism_rh<R, false>(m, t, k, p, N, U, V, Tp, Text, st_n, out);
+    prism_rh<R, false>(m, t, k, p, N, own, U, V, Tp, Text, st_n, out);
     const R w12 = Geo<R>::jh(m, t) * (R)(1.0 / 12.0);
     const R G2 = (R)(2.0 / 3.0), G1 = (R)(1.0 / 3.0);
 #pragma unroll
@@ -272,7 +283,7 @@ __global__ void __launch_bounds__(TP, (MinBlocks<R, TP>::value)) k_tracer_stage(
       const R mn = dr * sn;
       const R mp = dr * sp_;
       const R tn0 = Tn[(size_t)(0 * 3 + a) * m.P + p], tn1 = Tn[(size_t)(1 * 3 + a) * m.P + p];
-      const R tp0 = Tp[(size_t)(0 * 3 + a) * m.P + p], tp1 = Tp[(size_t)(1 * 3 + a) * m.P + p];
+      const R tp0 = own.T[0][a], tp1 = own.T[1][a];
       s_b[a * TPX + slot] = alpha * mn * (G2 * tn0 + G1 * tn1) + beta * (mp * (G2 * tp0 + G1 * tp1) + dt * out[0][a]);
       s_b[(3 + a) * TPX + slot] = alpha * mn * (G1 * tn0 + G2 * tn1) + beta * (mp * (G1 * tp0 + G2 * tp1) + dt * out[1][a]);
     }
@@ -326,13 +337,16 @@ __global__ void __launch_bounds__(TP, (MinBlocks<R, TP>::value))
     k_rhs3d(DevMesh m, const R* __restrict__ U, const R* __restrict__ V, const R* __restrict__ T,
             const R* __restrict__ Text, const R* __restrict__ st, R* __restrict__ out) {
   __shared__ int s_off[TP + 1];
-  const Tile tl = load_tile<TP>(m, s_off);
+  const Tile tl = tile_of_block(m);
   const int i = threadIdx.x;
+  Own<R> own;
+  if (i < tl.np) load_own<R, false>(m, tl.p0 + i, U, V, T, own);
+  load_offsets<TP>(m, tl, s_off);
   if (i >= tl.np) return;
   const int lt = tile_tri_of(s_off, tl.nt, i);
   const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
   R o[2][3];
-  prism_rh<R, false>(m, t, k, tl.p0 + i, N, U, V, T, Text, st, o);
+  prism_rh<R, false>(m, t, k, tl.p0 + i, N, own, U, V, T, Text, st, o);
 #pragma unroll
   for (int c = 0; c < 2; ++c)
 #pragma unroll
