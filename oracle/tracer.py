@@ -43,7 +43,8 @@ def transport(dz: np.ndarray, u: np.ndarray, v: np.ndarray) -> tuple[np.ndarray,
 
 
 def horizontal_residual(om: OMesh, qx: np.ndarray, qy: np.ndarray, T: np.ndarray,
-                        T_ext: np.ndarray | None = None) -> np.ndarray:
+                        T_ext: np.ndarray | None = None,
+                        face_corr: np.ndarray | None = None) -> np.ndarray:
     """R_h(q, T)_{c,a,p} = int_K q T . grad(phi_a) psi_c J_h
                          - sum_lateral faces int phi_a psi_c (q.n)^ T^ dl dzeta
 
@@ -51,6 +52,9 @@ def horizontal_residual(om: OMesh, qx: np.ndarray, qy: np.ndarray, T: np.ndarray
     the mean of both sides {q}.n; T^ is upwind at each face quadrature point.
     Walls carry no flux.  Open boundaries use the interior transport and, for
     inflow, the exterior state ``T_ext`` (same layout as T; zero-gradient when None).
+    ``face_corr`` (P, 3, 2): an additive correction of the normal transport per
+    lateral face and edge quadrature point (the same at both zeta points), used
+    for the transport that matches the averaged 2D face flux.
     All arrays are (2, 3, P)."""
     R = np.zeros_like(T)
     t = om.t_of
@@ -80,7 +84,7 @@ def horizontal_residual(om: OMesh, qx: np.ndarray, qy: np.ndarray, T: np.ndarray
         own = (e, (e + 1) % 3)
         loc = om.nloc[t, e]                               # (P, 2)
         is_open = om.bnd[t, e] == 2
-        for sq, ws in zip(gs, gw):
+        for gi, (sq, ws) in enumerate(zip(gs, gw)):
             lam = 0.5 * (1.0 + sq)
             wv = (1.0 - lam, lam)                         # basis values of the 2 edge vertices
             for zq, wz in zip(GAUSS_Z, GAUSS_W):
@@ -101,6 +105,8 @@ def horizontal_residual(om: OMesh, qx: np.ndarray, qy: np.ndarray, T: np.ndarray
                 else:
                     T_x = T_own
                 qn = np.where(ok, 0.5 * (qn_own + qn_nb), np.where(is_open, qn_own, 0.0))
+                if face_corr is not None:
+                    qn = qn + np.where(ok | is_open, face_corr[:, e, gi], 0.0)
                 T_other = np.where(ok, T_nb, T_x)
                 flux = qn * np.where(qn > 0.0, T_own, T_other)
                 w = 0.5 * L * ws * wz
