@@ -257,10 +257,12 @@ def horizontal_viscosity(om: OMesh, dz: np.ndarray, u: np.ndarray, nu: float, pe
                 flux = 0.5 * nu * ((zz_o * (go * n).sum(-1)) + (zz_n * (gn * n).sum(-1)))
                 jump = u_o - u_n
                 w = np.where(ok, 0.5 * L * ws * wz, 0.0)
-                for j in range(2):
-                    a = own[j]
+                # every test function of the element: phi_a vanishes on the face for
+                # the opposite vertex, but its gradient does not
+                for a in range(3):
+                    va = wv[own.index(a)] if a in own else 0.0
                     for c in range(2):
-                        v = wv[j] * ps[c]
+                        v = va * ps[c]
                         gv = (grad[:, a] * n).sum(-1) * ps[c]     # grad v . n on the own side
                         R[c, a] += w * (flux * v + 0.5 * nu * zz_o * gv * jump
                                         - sig * 0.5 * (zz_o + zz_n) * jump * v)
@@ -306,7 +308,7 @@ def mode2d_residual(om: OMesh, par: Params, eta, U, V, time: float):
     (n_tri, 3, 2) for the state (eta, Q = (U, V)):
       R_eta,a = int Q . grad phi_a - oint phi_a F_eta
       R_Q,a   = int g eta (H grad phi_a + phi_a grad H) - oint phi_a g H^- eta^ n
-    with H = h + eta, c = sqrt(g (H^- + H^+)/2) at each edge point,
+    with H = h + eta, c = sqrt(g (h^- + h^+)/2) (rest depth) at each edge point,
       F_eta = {Q}.n + c/2 (eta^- - eta^+),   eta^ = {eta} + (q^- - q^+)/(2c)
     (upwind flux of the linear wave system).  Walls: eta^+ = eta^-, q^+ = -q^-.
     Open boundary: eta^+ = A cos(2 pi t / T_M2), Q^+ = Q^-."""
@@ -352,8 +354,11 @@ def mode2d_residual(om: OMesh, par: Params, eta, U, V, time: float):
             # exterior states
             e_ext = np.where(ok, en, np.where(is_open, A_tide, eo))
             q_ext = np.where(ok, qn, np.where(is_open, qo, -qo))
-            H_ext = np.where(ok, Hn, Ho)
-            c = np.sqrt(g * 0.5 * (Ho + H_ext))
+            # wave speed of the rest depth (the linear-wave Riemann problem)
+            ho = wv[0] * h[own[0]] + wv[1] * h[own[1]]
+            hn = wv[0] * h[l0, nbs] + wv[1] * h[l1, nbs]
+            h_ext = np.where(ok, hn, ho)
+            c = np.sqrt(g * 0.5 * (ho + h_ext))
             F_eta = 0.5 * (qo + q_ext) + 0.5 * c * (eo - e_ext)
             e_hat = 0.5 * (eo + e_ext) + (qo - q_ext) / (2.0 * c)
             Fe[:, e, gi] = F_eta

@@ -95,16 +95,20 @@ def test_horizontal_viscosity_properties():
     # constant field: no viscous flux
     R0 = bc.horizontal_viscosity(om, dz, np.full((2, 3, om.P), 1.7), nu, pen)
     assert np.abs(R0).max() < 1e-9
-    # the operator is symmetric negative semidefinite (SIPG)
-    rng = np.random.default_rng(0)
-    n = 6 * om.P
-    idx = rng.choice(n, 12, replace=False)
-    cols = []
-    for i in idx:
+    # the whole operator is symmetric negative semidefinite (SIPG); on flat layers
+    # its null space is the constants
+    mf = flat_or_shelf(n=2, N=2, slope=False)
+    of = OMesh(mf)
+    dzf = of.thickness(np.zeros((3, mf.n_tri)))
+    n = 6 * of.P
+    A = np.empty((n, n))
+    for i in range(n):
         e = np.zeros(n); e[i] = 1.0
-        cols.append(bc.horizontal_viscosity(om, dz, e.reshape(2, 3, om.P), nu, pen).ravel())
-    A = np.array(cols)[:, idx]
-    assert np.allclose(A, A.T, rtol=1e-10, atol=1e-10 * np.abs(A).max())
+        A[:, i] = bc.horizontal_viscosity(of, dzf, e.reshape(2, 3, of.P), nu, pen).ravel()
+    assert np.allclose(A, A.T, rtol=0, atol=1e-12 * np.abs(A).max())
+    ev = np.linalg.eigvalsh(0.5 * (A + A.T))
+    assert ev.max() < 1e-12 * np.abs(ev).max()
+    rng = np.random.default_rng(0)
     u = rng.standard_normal((2, 3, om.P))
     Ru = bc.horizontal_viscosity(om, dz, u, nu, pen)
     assert (u * Ru).sum() < 0
