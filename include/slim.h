@@ -83,7 +83,11 @@ enum {
   SLIM_FIELD_QY = 18,
   SLIM_FIELD_ETA_NEXT = 19, /* 2D elevation at the end of the last continuity solve  */
   SLIM_FIELD_QBAR_X = 20,   /* 2D time-averaged transport of the last external run    */
-  SLIM_FIELD_QBAR_Y = 21
+  SLIM_FIELD_QBAR_Y = 21,
+  SLIM_FIELD_S3_X = 22,     /* 2D column sum of the 3D horizontal momentum terms (last stage) */
+  SLIM_FIELD_S3_Y = 23,
+  SLIM_FIELD_F2D_X = 24,    /* 2D momentum forcing F2D of the last stage (Sec. 2.2)          */
+  SLIM_FIELD_F2D_Y = 25
 };
 
 typedef struct slim_params {
@@ -198,9 +202,9 @@ slim_status slim_continuity(slim_state* s, double dt, void* stream);
 
 /* slim_rhs2d: for SLIM_SCHEME_TRACER, the depth-integrated horizontal residual of
  * T = 1 per 2D node (the right-hand side of Eq. 2 in weak form), 3*n_tri doubles.
- * For SLIM_SCHEME_SPLIT, the 2D external-mode residual (mass, then the two
- * momentum components: 9*n_tri doubles) at time t of the state's eta, Qx, Qy
- * with the last 3D source term. */
+ * For SLIM_SCHEME_SPLIT, the 2D external-mode residual of Eqs. 2 and 10 without
+ * the 3D source (mass, then the two momentum components: 9*n_tri doubles) at
+ * time t (open-boundary elevation) of the state's eta, Qx, Qy. */
 slim_status slim_rhs2d(slim_state* s, double t, double* out_dev, void* stream);
 
 /* slim_vertical_solve: one implicit vertical solve per vertex column,
@@ -211,6 +215,15 @@ slim_status slim_rhs2d(slim_state* s, double t, double* out_dev, void* stream);
  * layer).  rhs_dev, out_dev: 6P elements of the compute type; they may alias. */
 slim_status slim_vertical_solve(slim_state* s, int field, double beta_dt, const void* rhs_dev,
                                 void* out_dev, void* stream);
+
+/* slim_hpg: density anomaly rho' = rho0 (-alpha (T - T0) + beta (S - S0)) of the
+ * state's T, S and the horizontal baroclinic pressure gradient r of Eq. 8 at the
+ * state's elevation: per column the system D_vu r = F of Eq. 16 (printed D_vu
+ * pattern with the consistent M_h), solved top-down by Algorithm 1, with
+ * F = int v g grad_h rho' dV in weak form (central density traces on lateral,
+ * top and bottom faces) and the surface value g rho'(eta) grad(eta).  Writes
+ * SLIM_FIELD_R_X and SLIM_FIELD_R_Y.  SLIM_SCHEME_SPLIT only. */
+slim_status slim_hpg(slim_state* s, void* stream);
 
 /* slim_step: one complete internal step t -> t + dt of the state's scheme.
  * SLIM_SCHEME_TRACER: continuity, then three SSP-RK3 stages for T, then eta <-

@@ -73,6 +73,7 @@ slim_status dev_alloc(slim_state* s, void** p, size_t bytes) {
 
 void free_state(slim_state* s) {
   if (!s) return;
+  split_free(s);
   for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
   for (void* p : s->allocs) cudaFree(p);
   delete s;
@@ -102,6 +103,12 @@ bool field_ref(slim_state* s, int field, FieldRef* r) {
     case SLIM_FIELD_ETA_NEXT: *r = {s->eta_next, false, true}; return true;
     case SLIM_FIELD_QBAR_X: *r = {s->Qbx, false, true}; return true;
     case SLIM_FIELD_QBAR_Y: *r = {s->Qby, false, true}; return true;
+    case SLIM_FIELD_S3_X: case SLIM_FIELD_S3_Y: case SLIM_FIELD_F2D_X: case SLIM_FIELD_F2D_Y: {
+      void* p = split_field(s, field);
+      if (!p) return false;
+      *r = {p, false, true};
+      return true;
+    }
   }
   return false;
 }
@@ -208,6 +215,10 @@ extern "C" slim_status slim_state_alloc(const slim_mesh* m, slim_precision prec,
   for (void** f : fs)
     if ((st = dev_alloc(s, f, n2 * s->esz)) != SLIM_OK) { free_state(s); return st; }
   if ((st = refresh_stretch(s, 0)) != SLIM_OK) { free_state(s); return st; }
+  if (par->scheme == SLIM_SCHEME_SPLIT) {
+    if (par->n_sub < 2 || par->n_sub % 2) { free_state(s); set_error("n_sub must be even"); return SLIM_ERR_ARG; }
+    if ((st = split_alloc(s)) != SLIM_OK) { free_state(s); return st; }
+  }
   s->aux2d_len = split_aux2d_len(m->d);
   if ((st = dev_alloc(s, (void**)&s->aux2d, s->aux2d_len * sizeof(double))) != SLIM_OK) { free_state(s); return st; }
   s->red_blocks = m->d.n_tiles;
@@ -368,6 +379,13 @@ extern "C" slim_status slim_vertical_solve(slim_state* s, int field, double beta
                                              (const float*)rhs_dev, (float*)out_dev, beta_dt, sp,
                                              s->err, st));
   return SLIM_OK;
+}
+
+extern "C" slim_status slim_hpg(slim_state* s, void* stream) {
+  clear_error();
+  if (!s) { set_error("state is null"); return SLIM_ERR_ARG; }
+  if (s->par.scheme != SLIM_SCHEME_SPLIT) { set_error("slim_hpg needs SLIM_SCHEME_SPLIT"); return SLIM_ERR_UNSUPPORTED; }
+  return split_hpg(s, (cudaStream_t)stream);
 }
 
 extern "C" slim_status slim_step(slim_state* s, double t, double dt, void* stream) {

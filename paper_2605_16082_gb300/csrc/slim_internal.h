@@ -11,6 +11,7 @@
 struct slim_state;
 
 namespace slim {
+struct SplitBufs;
 
 // thread-local message of the last failing call
 void set_error(const std::string& msg);
@@ -46,6 +47,7 @@ struct DevMesh {
   const double* eny;
   const double* elen;    // [3][n_tri] edge length
   const double* rin;     // [n_tri] inradius
+  const float* rin_f;
   const double* h;       // [3][n_tri] rest depth at the vertices
   const int* nbr;        // [3][n_tri] neighbour triangle, -1 wall, -2 open boundary
   const int* nloc;       // [3][n_tri] neighbour-local vertices of own e, e+1: l0 | l1 << 2
@@ -108,6 +110,8 @@ struct slim_state {
   double* red = nullptr;    // block partials of the mass sum
   int red_blocks = 0;
   double* red_out = nullptr;
+  // split scheme (2D external mode and coupling; allocated for SLIM_SCHEME_SPLIT)
+  slim::SplitBufs* sp = nullptr;
   int* err = nullptr;       // device error flags
   double* stage64 = nullptr;  // 6P doubles: conversion staging of the mixed form
   int steps_since_check = 0;

@@ -219,6 +219,7 @@ extern "C" slim_status slim_mesh_create(const double* xy, int n_vert, const int*
   d.max_layers = max_layers;
   d.max_tile_tris = max_tile_tris;
   d.n_levels = levels ? n_levels : 0;
+  std::vector<float> rinf(rin.begin(), rin.end());
   std::vector<float> jhf(jh.begin(), jh.end()), gxf(gx.begin(), gx.end()), gyf(gy.begin(), gy.end()),
       enxf(enx.begin(), enx.end()), enyf(eny.begin(), eny.end()), elenf(elen.begin(), elen.end());
   slim_status st;
@@ -238,6 +239,7 @@ extern "C" slim_status slim_mesh_create(const double* xy, int n_vert, const int*
   UP(eny, eny);
   UP(elen, elen);
   UP(rin, rin);
+  UP(rinf, rin_f);
   UP(h, h);
   UP(nbr, nbr);
   UP(nloc, nloc);

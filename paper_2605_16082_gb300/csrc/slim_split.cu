@@ -1,15 +1,1040 @@
-// Split-IMEX internal step (not built yet: entry points report unsupported).
+// The split-IMEX internal step (Sec. 2, Eqs. 11-14): per stage
+//   density + horizontal pressure gradient (Eqs. 7-8, Eq. 15-16, Algorithm 1)
+//   -> 3D horizontal momentum prediction F_3D^h and its column sum (Sec. 2.2)
+//   -> subcycled 2D external mode in FP64 with the time-averaged transport (axpy)
+//   -> F2D coupling and the corrected transport (Sec. 2.2, Sec. 2.5)
+//   -> vertical flux from the continuity (Eq. 17)
+//   -> 3D momentum and tracers, vertically implicit (stage 1) or explicit (stage 2).
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "slim_kernels.h"
 #include "slim_split.h"
+#include "slim_split_device.cuh"
 
 namespace slim {
+
+struct SplitBufs {
+  // 2D (double): running external state A and two stage buffers
+  double *Ae, *AU, *AV, *Be, *BU, *BV, *Ce, *CU, *CV;
+  double *S3x, *S3y, *Sqx, *Sqy, *Gb, *F2x, *F2y, *eta_half, *cw;
+  // compute-type copies for the 3D kernels
+  void *F2x_r, *F2y_r, *Dqx_r, *Dqy_r, *gcor_r, *st_half, *st_end;
+  bool has_s3 = false;
+};
+
+namespace {
+
+template <typename R, int TP>
+struct MB {
+  static constexpr int value = sizeof(R) == 4 ? (1024 / TP > 0 ? 1024 / TP : 1) : (512 / TP > 0 ? 512 / TP : 1);
+};
+
+#define SLIM_TP_SWITCH2(TP, ...)                                \
+  switch (TP) {                                                 \
+    case 128: { constexpr int TPc = 128; __VA_ARGS__; } break;  \
+    case 256: { constexpr int TPc = 256; __VA_ARGS__; } break;  \
+    case 512: { constexpr int TPc = 512; __VA_ARGS__; } break;  \
+    default: return cudaErrorInvalidValue;                      \
+  }
+
+template <typename KernelT>
+cudaError_t set_smem2(KernelT kern, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+struct PhysParams {
+  double g, rho0, f, alpha, beta, T0, S0, nu_h, kappa_h, nu_v, kappa_v, cd, pen_v, pen_h;
+};
+
+// rest depth of interface k of vertex column i (0 at the surface)
+template <typename R>
+__device__ __forceinline__ R zhat_r(const DevMesh& m, int i, int k) {
+  if (m.n_levels == 0) return -(R)k * Geo<R>::hN(m, i);
+  return Geo<R>::lev(m, k);
+}
+
+// ---------------------------------------------------------------------------
+// wave speed of the 2D flux at every edge point: c = sqrt(g (h^- + h^+)/2)
+// ---------------------------------------------------------------------------
+__global__ void k_wave_speed(DevMesh m, double g, double* __restrict__ cw) {
+  const int nt = m.n_tri;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    for (int e = 0; e < 3; ++e) {
+      const int4 ei = m.einfo[e * nt + t];
+      const int a0 = e, a1 = (e + 1) % 3;
+      for (int gs = 0; gs < 2; ++gs) {
+        const double b0 = gs ? SLIM_GL2 : SLIM_GL1, b1 = gs ? SLIM_GL1 : SLIM_GL2;
+        const double ho = b0 * m.h[a0 * nt + t] + b1 * m.h[a1 * nt + t];
+        double hn = ho;
+        if (ei.x >= 0) {
+          const int l0 = ei.w & 3, l1 = (ei.w >> 2) & 3;
+          hn = b0 * m.h[l0 * nt + ei.x] + b1 * m.h[l1 * nt + ei.x];
+        }
+        cw[(e * nt + t) * 2 + gs] = sqrt(g * 0.5 * (ho + hn));
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// density + horizontal pressure gradient (one tile per block)
+// ---------------------------------------------------------------------------
+template <typename R, int TP>
+__global__ void __launch_bounds__(TP, (MB<R, TP>::value))
+    k_hpg(DevMesh m, const R* __restrict__ T, const R* __restrict__ S, const R* __restrict__ st,
+          PhysParams pp, R* __restrict__ Rx, R* __restrict__ Ry) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int* s_off = reinterpret_cast<int*>(smem);
+  const int TPX = TP + m.max_tile_tris;
+  R* s_F = reinterpret_cast<R*>(smem + ((TP + 1) * sizeof(int) + 15) / 16 * 16);  // [12][TPX]
+  const Tile tl = tile_of_block(m);
+  const int i = threadIdx.x;
+  const int nt = m.n_tri, P = m.P;
+  const R rho0 = (R)pp.rho0, al = (R)pp.alpha, be = (R)pp.beta, T0 = (R)pp.T0, S0 = (R)pp.S0;
+  const R g = (R)pp.g;
+  auto rho = [&](R Tv, R Sv) { return rho0 * (-al * (Tv - T0) + be * (Sv - S0)); };
+  R r[2][3];
+  if (i < tl.np) {
+    const int p = tl.p0 + i;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) r[c][a] = rho(T[(size_t)(c * 3 + a) * P + p], S[(size_t)(c * 3 + a) * P + p]);
+  }
+  load_offsets<TP>(m, tl, s_off);
+  int slot = 0;
+  if (i < tl.np) {
+    const int lt = tile_tri_of(s_off, tl.nt, i);
+    const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
+    const int p = tl.p0 + i;
+    slot = i + lt;
+    const R jh = Geo<R>::jh(m, t), w24 = jh * (R)(1.0 / 24.0);
+    R gx[3], gy[3], hz[3], zt[3], zb[3], stv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int ia = a * nt + t;
+      gx[a] = Geo<R>::gx(m, ia); gy[a] = Geo<R>::gy(m, ia);
+      stv[a] = st[ia];
+      const R h = Geo<R>::h(m, ia);
+      hz[a] = (R)0.5 * dz_rest_r<R>(m, ia, k, N) * stv[a];
+      zt[a] = stv[a] * (zhat_r<R>(m, ia, k) + h) - h;
+      zb[a] = zt[a] - (R)2 * hz[a];
+    }
+    const R gztx = zt[0] * gx[0] + zt[1] * gx[1] + zt[2] * gx[2];
+    const R gzty = zt[0] * gy[0] + zt[1] * gy[1] + zt[2] * gy[2];
+    const R gzbx = zb[0] * gx[0] + zb[1] * gx[1] + zb[2] * gx[2];
+    const R gzby = zb[0] * gy[0] + zb[1] * gy[1] + zb[2] * gy[2];
+    R Fx[2][3], Fy[2][3];
+    // volume: -g int rho' grad(phi_a) psi_c z_zeta  +  g int rho' phi_a psi_c' grad z
+    {
+      const R shz = hz[0] + hz[1] + hz[2];
+      R A[2], Sr[2];
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        Sr[d] = r[d][0] + r[d][1] + r[d][2];
+        A[d] = w24 * (Sr[d] * shz + r[d][0] * hz[0] + r[d][1] * hz[1] + r[d][2] * hz[2]);
+      }
+      const R G2 = (R)(2.0 / 3.0), G1 = (R)(1.0 / 3.0);
+      const R tA0 = G2 * A[0] + G1 * A[1], tA1 = G1 * A[0] + G2 * A[1];
+      const R Z0x = G2 * gztx + G1 * gzbx, Z0y = G2 * gzty + G1 * gzby;
+      const R Z1x = G1 * gztx + G2 * gzbx, Z1y = G1 * gzty + G2 * gzby;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const R m0 = w24 * (Sr[0] + r[0][a]), m1 = w24 * (Sr[1] + r[1][a]);
+        const R bx = m0 * Z0x + m1 * Z1x, by = m0 * Z0y + m1 * Z1y;
+        Fx[0][a] = g * (-gx[a] * tA0 + (R)0.5 * bx);
+        Fy[0][a] = g * (-gy[a] * tA0 + (R)0.5 * by);
+        Fx[1][a] = g * (-gx[a] * tA1 - (R)0.5 * bx);
+        Fy[1][a] = g * (-gy[a] * tA1 - (R)0.5 * by);
+      }
+    }
+    // lateral faces: + g oint v {rho'} n z_zeta dl dzeta
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const int4 ei = m.einfo[e * nt + t];
+      const int a0 = e, a1 = (e + 1) % 3;
+      const R nxe = Geo<R>::nx(m, e * nt + t), nye = Geo<R>::ny(m, e * nt + t);
+      const R half_len = (R)0.5 * Geo<R>::len(m, e * nt + t);
+      R rb[2][2];
+      bool has_nb = false;
+      if (ei.x >= 0 && k < ei.z) {
+        has_nb = true;
+        const int pn = ei.y + k;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int l = j ? ((ei.w >> 2) & 3) : (ei.w & 3);
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const size_t idx = (size_t)(c * 3 + l) * P + pn;
+            rb[j][c] = rho(T[idx], S[idx]);
+          }
+        }
+      }
+#pragma unroll
+      for (int gs = 0; gs < 2; ++gs) {
+        const R b0 = gs ? (R)SLIM_GL2 : (R)SLIM_GL1, b1 = gs ? (R)SLIM_GL1 : (R)SLIM_GL2;
+        const R zz = b0 * hz[a0] + b1 * hz[a1];
+#pragma unroll
+        for (int gz = 0; gz < 2; ++gz) {
+          const R z0 = gz ? (R)SLIM_GL2 : (R)SLIM_GL1, z1 = gz ? (R)SLIM_GL1 : (R)SLIM_GL2;
+          const R B00 = b0 * z0, B01 = b0 * z1, B10 = b1 * z0, B11 = b1 * z1;
+          R rh = B00 * r[0][a0] + B01 * r[1][a0] + B10 * r[0][a1] + B11 * r[1][a1];
+          if (has_nb) rh = (R)0.5 * (rh + (B00 * rb[0][0] + B01 * rb[0][1] + B10 * rb[1][0] + B11 * rb[1][1]));
+          const R wx = g * half_len * zz * rh * nxe, wy = g * half_len * zz * rh * nye;
+          Fx[0][a0] += wx * B00; Fx[1][a0] += wx * B01; Fx[0][a1] += wx * B10; Fx[1][a1] += wx * B11;
+          Fy[0][a0] += wy * B00; Fy[1][a0] += wy * B01; Fy[0][a1] += wy * B10; Fy[1][a1] += wy * B11;
+        }
+      }
+    }
+    // top / bottom faces: central rho' with the element above / below
+    R rt[3], rbt[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      rt[a] = r[0][a];
+      rbt[a] = r[1][a];
+    }
+    if (k > 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const size_t idx = (size_t)(3 + a) * P + p - 1;
+        rt[a] = (R)0.5 * (rt[a] + rho(T[idx], S[idx]));
+      }
+    }
+    if (k + 1 < N) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const size_t idx = (size_t)a * P + p + 1;
+        rbt[a] = (R)0.5 * (rbt[a] + rho(T[idx], S[idx]));
+      }
+    }
+    {
+      const R srt = rt[0] + rt[1] + rt[2], srb = rbt[0] + rbt[1] + rbt[2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const R mt = w24 * (srt + rt[a]), mb = w24 * (srb + rbt[a]);
+        Fx[0][a] -= g * mt * gztx; Fy[0][a] -= g * mt * gzty;
+        Fx[1][a] += g * mb * gzbx; Fy[1][a] += g * mb * gzby;
+      }
+    }
+    // surface condition r = g rho'(eta) grad(eta): F_top -= M_h r_surface (layer 0)
+    if (k == 0) {
+      R gex = 0, gey = 0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const R eta = (stv[a] - (R)1) * Geo<R>::h(m, a * nt + t);
+        gex += eta * gx[a]; gey += eta * gy[a];
+      }
+      const R sr = r[0][0] + r[0][1] + r[0][2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const R mr = g * w24 * (sr + r[0][a]);
+        Fx[0][a] -= mr * gex;
+        Fy[0][a] -= mr * gey;
+      }
+    }
+    // M_h^-1 per layer: f_a = (6/J_h)(4 F_a - sum F)
+    const R s6 = (R)6 * rcp<R>(jh);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const R sx = Fx[c][0] + Fx[c][1] + Fx[c][2], sy = Fy[c][0] + Fy[c][1] + Fy[c][2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        s_F[(c * 3 + a) * TPX + slot] = s6 * ((R)4 * Fx[c][a] - sx);
+        s_F[(6 + c * 3 + a) * TPX + slot] = s6 * ((R)4 * Fy[c][a] - sy);
+      }
+    }
+  }
+  __syncthreads();
+  // Algorithm 1 per vertex column and component: s += f_t + f_b, r_t = -s + 2 f_b, r_b = -s
+  for (int j = threadIdx.x; j < 6 * tl.nt; j += TP) {
+    const int comp = j / (3 * tl.nt), rem = j - comp * 3 * tl.nt;
+    const int a = rem / tl.nt, lt = rem - a * tl.nt;
+    const int base = s_off[lt] + lt, N = s_off[lt + 1] - s_off[lt];
+    R* ft = s_F + (comp * 6 + a) * TPX + base;
+    R* fb = s_F + (comp * 6 + 3 + a) * TPX + base;
+    R s = 0;
+    for (int k = 0; k < N; ++k) {
+      s += ft[k] + fb[k];
+      const R rtop = -s + (R)2 * fb[k];
+      fb[k] = -s;
+      ft[k] = rtop;
+    }
+  }
+  __syncthreads();
+  if (i < tl.np) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      Rx[(size_t)q * P + tl.p0 + i] = s_F[q * TPX + slot];
+      Ry[(size_t)q * P + tl.p0 + i] = s_F[(6 + q) * TPX + slot];
+    }
+  }
+}
+
+// lumped mass apply: (M f)_c = (J_h/6) hz (G f)_c, G = [[2,1],[1,2]]/3
+template <typename R>
+__device__ __forceinline__ void lumped(R w6hz, R f0, R f1, R& o0, R& o1) {
+  o0 = w6hz * ((R)(2.0 / 3.0) * f0 + (R)(1.0 / 3.0) * f1);
+  o1 = w6hz * ((R)(1.0 / 3.0) * f0 + (R)(2.0 / 3.0) * f1);
+}
+
+// F_3D^h terms beyond advection: horizontal viscosity, Coriolis, -r/rho0, bed drag
+template <typename R>
+__device__ __forceinline__ void momentum_extras(const DevMesh& m, int t, int k, int p, int N,
+                                                const Own2<R>& own, const R* __restrict__ U,
+                                                const R* __restrict__ V, const R* __restrict__ st,
+                                                const R* __restrict__ Rx, const R* __restrict__ Ry,
+                                                const PhysParams& pp, R Fx[2][3], R Fy[2][3]) {
+  const int nt = m.n_tri, P = m.P;
+  if (pp.nu_h > 0.0) {
+    prism_sipg<R>(m, t, k, N, own.u, U, st, (R)pp.nu_h, (R)pp.pen_h, Fx);
+    prism_sipg<R>(m, t, k, N, own.v, V, st, (R)pp.nu_h, (R)pp.pen_h, Fy);
+  }
+  const R f = (R)pp.f, irho = (R)(1.0 / pp.rho0);
+  const R w6 = Geo<R>::jh(m, t) * (R)(1.0 / 6.0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int ia = a * nt + t;
+    const R hz = (R)0.5 * dz_rest_r<R>(m, ia, k, N) * st[ia];
+    R sx[2], sy[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      sx[c] = f * own.v[c][a] - Rx[(size_t)(c * 3 + a) * P + p] * irho;
+      sy[c] = -f * own.u[c][a] - Ry[(size_t)(c * 3 + a) * P + p] * irho;
+    }
+    R ox0, ox1, oy0, oy1;
+    lumped<R>(w6 * hz, sx[0], sx[1], ox0, ox1);
+    lumped<R>(w6 * hz, sy[0], sy[1], oy0, oy1);
+    Fx[0][a] += ox0; Fx[1][a] += ox1;
+    Fy[0][a] += oy0; Fy[1][a] += oy1;
+    if (k == N - 1) {
+      const R ub = own.u[1][a], vb = own.v[1][a];
+      const R sp = sqrt(ub * ub + vb * vb);
+      Fx[1][a] -= (R)pp.cd * w6 * sp * ub;
+      Fy[1][a] -= (R)pp.cd * w6 * sp * vb;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3D horizontal momentum prediction: column sums of F_3D^h and of q (FP64)
+// ---------------------------------------------------------------------------
+template <typename R, int TP>
+__global__ void __launch_bounds__(TP, (MB<R, TP>::value))
+    k_mompred(DevMesh m, AdvIn<R> in, const R* __restrict__ Rx, const R* __restrict__ Ry,
+              PhysParams pp, double* __restrict__ S3x, double* __restrict__ S3y,
+              double* __restrict__ Sqx, double* __restrict__ Sqy) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int* s_off = reinterpret_cast<int*>(smem);
+  const int TPX = TP + m.max_tile_tris;
+  R* s_v = reinterpret_cast<R*>(smem + ((TP + 1) * sizeof(int) + 15) / 16 * 16);  // [4][3][TPX]
+  const Tile tl = tile_of_block(m);
+  const int i = threadIdx.x;
+  Own2<R> own;
+  if (i < tl.np) load_own2<R, true>(m, tl.p0 + i, in, own);
+  load_offsets<TP>(m, tl, s_off);
+  if (i < tl.np) {
+    const int lt = tile_tri_of(s_off, tl.nt, i);
+    const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
+    const int p = tl.p0 + i, slot = i + lt;
+    R Fx[2][3] = {{0, 0, 0}, {0, 0, 0}}, Fy[2][3] = {{0, 0, 0}, {0, 0, 0}}, qx[2][3], qy[2][3];
+    prism_adv<R, false>(m, t, k, p, N, own, in, Fx, Fy, qx, qy);
+    momentum_extras<R>(m, t, k, p, N, own, in.U, in.V, in.st, Rx, Ry, pp, Fx, Fy);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      s_v[(0 * 3 + a) * TPX + slot] = Fx[0][a] + Fx[1][a];
+      s_v[(1 * 3 + a) * TPX + slot] = Fy[0][a] + Fy[1][a];
+      s_v[(2 * 3 + a) * TPX + slot] = qx[0][a] + qx[1][a];
+      s_v[(3 * 3 + a) * TPX + slot] = qy[0][a] + qy[1][a];
+    }
+  }
+  __syncthreads();
+  double* outs[4] = {S3x, S3y, Sqx, Sqy};
+  for (int j = threadIdx.x; j < 12 * tl.nt; j += TP) {
+    const int q = j / (3 * tl.nt), rem = j - q * 3 * tl.nt;
+    const int a = rem / tl.nt, lt = rem - a * tl.nt;
+    const int base = s_off[lt] + lt, N = s_off[lt + 1] - s_off[lt];
+    const R* src = s_v + (q * 3 + a) * TPX + base;
+    double s = 0.0;
+    for (int k = 0; k < N; ++k) s += (double)src[k];
+    outs[q][a * m.n_tri + tl.t0 + lt] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2D external-mode stage (FP64, thread per triangle)
+//   R_eta,a = int Q.grad phi_a - oint phi_a F_eta
+//   R_Q,a   = int g eta (H grad phi_a + phi_a grad H) - oint phi_a g H^- eta^ n
+//   F_eta = {q} + c/2 (eta^- - eta^+),  eta^ = {eta} + (q^- - q^+)/(2c)
+// Shu-Osher update (alpha, beta) from the subcycle start; the stage input is
+// accumulated into Qbar and its eta flux into Gbar with weight bw.
+// MODE 0: update; MODE 1: residual only (out = R_eta, R_U, R_V).
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void k_ext2d(DevMesh m, const double* __restrict__ es, const double* __restrict__ Us,
+                        const double* __restrict__ Vs, const double* __restrict__ en,
+                        const double* __restrict__ Un, const double* __restrict__ Vn,
+                        const double* __restrict__ S3x, const double* __restrict__ S3y,
+                        const double* __restrict__ cw, double g, double tide, double alpha,
+                        double beta, double dt, double bw, double* __restrict__ eo,
+                        double* __restrict__ Uo, double* __restrict__ Vo, double* __restrict__ Qbx,
+                        double* __restrict__ Qby, double* __restrict__ Gb) {
+  const int nt = m.n_tri;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double e[3], U[3], V[3], H[3], gx[3], gy[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int ia = a * nt + t;
+    e[a] = es[ia]; U[a] = Us[ia]; V[a] = Vs[ia];
+    H[a] = m.h[ia] + e[a];
+    gx[a] = m.gx[ia]; gy[a] = m.gy[ia];
+  }
+  const double jh = m.jh[t];
+  const double w6 = jh * (1.0 / 6.0), w24 = jh * (1.0 / 24.0);
+  const double sU = U[0] + U[1] + U[2], sV = V[0] + V[1] + V[2];
+  const double se = e[0] + e[1] + e[2], sH = H[0] + H[1] + H[2];
+  const double eH = w24 * (se * sH + e[0] * H[0] + e[1] * H[1] + e[2] * H[2]);
+  const double gHx = H[0] * gx[0] + H[1] * gx[1] + H[2] * gx[2];
+  const double gHy = H[0] * gy[0] + H[1] * gy[1] + H[2] * gy[2];
+  double Re[3], RU[3], RV[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Re[a] = w6 * (sU * gx[a] + sV * gy[a]);
+    const double ea = w24 * (se + e[a]);
+    RU[a] = g * (eH * gx[a] + ea * gHx);
+    RV[a] = g * (eH * gy[a] + ea * gHy);
+  }
+#pragma unroll
+  for (int ed = 0; ed < 3; ++ed) {
+    const int4 ei = m.einfo[ed * nt + t];
+    const int a0 = ed, a1 = (ed + 1) % 3;
+    const double nx = m.enx[ed * nt + t], ny = m.eny[ed * nt + t];
+    const double hl = 0.5 * m.elen[ed * nt + t];
+    double en0 = 0, en1 = 0, qn0 = 0, qn1 = 0;
+    if (ei.x >= 0) {
+      const int l0 = ei.w & 3, l1 = (ei.w >> 2) & 3;
+      const int i0 = l0 * nt + ei.x, i1 = l1 * nt + ei.x;
+      en0 = es[i0]; en1 = es[i1];
+      qn0 = Us[i0] * nx + Vs[i0] * ny;
+      qn1 = Us[i1] * nx + Vs[i1] * ny;
+    }
+    const double qo0 = U[a0] * nx + V[a0] * ny, qo1 = U[a1] * nx + V[a1] * ny;
+#pragma unroll
+    for (int gs = 0; gs < 2; ++gs) {
+      const double b0 = gs ? SLIM_GL2 : SLIM_GL1, b1 = gs ? SLIM_GL1 : SLIM_GL2;
+      const double eo_ = b0 * e[a0] + b1 * e[a1];
+      const double Ho = b0 * H[a0] + b1 * H[a1];
+      const double qo = b0 * qo0 + b1 * qo1;
+      double ex, qx;
+      if (ei.x >= 0) {
+        ex = b0 * en0 + b1 * en1;
+        qx = b0 * qn0 + b1 * qn1;
+      } else if (ei.x == -2) {
+        ex = tide;
+        qx = qo;
+      } else {
+        ex = eo_;
+        qx = -qo;
+      }
+      const double c = cw[(ed * nt + t) * 2 + gs];
+      const double Fe = 0.5 * (qo + qx) + 0.5 * c * (eo_ - ex);
+      const double eh = 0.5 * (eo_ + ex) + (qo - qx) / (2.0 * c);
+      if (MODE == 0) Gb[(ed * nt + t) * 2 + gs] += bw * Fe;
+      const double gq = g * Ho * eh;
+      Re[a0] -= hl * b0 * Fe; Re[a1] -= hl * b1 * Fe;
+      RU[a0] -= hl * b0 * gq * nx; RU[a1] -= hl * b1 * gq * nx;
+      RV[a0] -= hl * b0 * gq * ny; RV[a1] -= hl * b1 * gq * ny;
+    }
+  }
+  if (MODE == 1) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      eo[a * nt + t] = Re[a];
+      eo[(3 + a) * nt + t] = RU[a];
+      eo[(6 + a) * nt + t] = RV[a];
+    }
+    return;
+  }
+  const double iw = 1.0 / w6;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int ia = a * nt + t;
+    Qbx[ia] += bw * U[a];
+    Qby[ia] += bw * V[a];
+    const double e_new = alpha * en[ia] + beta * (e[a] + dt * Re[a] * iw);
+    const double U_new = alpha * Un[ia] + beta * (U[a] + dt * (RU[a] + S3x[ia]) * iw);
+    const double V_new = alpha * Vn[ia] + beta * (V[a] + dt * (RV[a] + S3y[ia]) * iw);
+    eo[ia] = e_new;
+    Uo[ia] = U_new;
+    Vo[ia] = V_new;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// coupling after the external run (FP64, thread per triangle):
+//   F2D = (Q1 - (Q0 + T S3/w))/T, Dq = Qbar - sum q, st_end = 1 + eta1/h,
+//   gcor = (Gbar - {Qbar}.n) / (paired layer thickness at the edge point)
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_couple2d(DevMesh m, const double* __restrict__ e1, const double* __restrict__ U1,
+                           const double* __restrict__ V1, const double* __restrict__ U0,
+                           const double* __restrict__ V0, const double* __restrict__ S3x,
+                           const double* __restrict__ S3y, const double* __restrict__ Sqx,
+                           const double* __restrict__ Sqy, const double* __restrict__ Qbx,
+                           const double* __restrict__ Qby, const double* __restrict__ Gb,
+                           const R* __restrict__ st_ev, double T, double* __restrict__ F2x,
+                           double* __restrict__ F2y, R* __restrict__ F2x_r, R* __restrict__ F2y_r,
+                           R* __restrict__ Dqx_r, R* __restrict__ Dqy_r, R* __restrict__ gcor_r,
+                           R* __restrict__ st_end) {
+  const int nt = m.n_tri;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const double w6 = m.jh[t] * (1.0 / 6.0);
+  const int N = m.col_off[t + 1] - m.col_off[t];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int ia = a * nt + t;
+    const double fx = (U1[ia] - (U0[ia] + T * S3x[ia] / w6)) / T;
+    const double fy = (V1[ia] - (V0[ia] + T * S3y[ia] / w6)) / T;
+    F2x[ia] = fx; F2y[ia] = fy;
+    F2x_r[ia] = (R)fx; F2y_r[ia] = (R)fy;
+    Dqx_r[ia] = (R)(Qbx[ia] - Sqx[ia]);
+    Dqy_r[ia] = (R)(Qby[ia] - Sqy[ia]);
+    st_end[ia] = (R)(1.0 + e1[ia] * m.ih[ia]);
+  }
+  // paired rest thickness of vertex i of a column of N layers over its first Np layers
+  auto paired = [&](int i, int Nc, int Np) -> double {
+    if (Np >= Nc) return m.h[i];
+    if (m.n_levels == 0) return m.hN[i] * Np;
+    return -m.levels[Np];
+  };
+#pragma unroll
+  for (int ed = 0; ed < 3; ++ed) {
+    const int4 ei = m.einfo[ed * nt + t];
+    const int a0 = ed, a1 = (ed + 1) % 3;
+    const double nx = m.enx[ed * nt + t], ny = m.eny[ed * nt + t];
+    for (int gs = 0; gs < 2; ++gs) {
+      const double b0 = gs ? SLIM_GL2 : SLIM_GL1, b1 = gs ? SLIM_GL1 : SLIM_GL2;
+      double g = 0.0;
+      if (ei.x != -1) {
+        const int i0 = a0 * nt + t, i1 = a1 * nt + t;
+        const double Qo = b0 * (Qbx[i0] * nx + Qby[i0] * ny) + b1 * (Qbx[i1] * nx + Qby[i1] * ny);
+        double Qavg = Qo;
+        const int Np = ei.x >= 0 ? min(N, ei.z) : N;
+        double tot = b0 * paired(i0, N, Np) * (double)st_ev[i0] + b1 * paired(i1, N, Np) * (double)st_ev[i1];
+        if (ei.x >= 0) {
+          const int l0 = ei.w & 3, l1 = (ei.w >> 2) & 3;
+          const int j0 = l0 * nt + ei.x, j1 = l1 * nt + ei.x;
+          const double Qn = b0 * (Qbx[j0] * nx + Qby[j0] * ny) + b1 * (Qbx[j1] * nx + Qby[j1] * ny);
+          Qavg = 0.5 * (Qo + Qn);
+          tot += b0 * paired(j0, ei.z, Np) * (double)st_ev[j0] + b1 * paired(j1, ei.z, Np) * (double)st_ev[j1];
+        }
+        g = (Gb[(ed * nt + t) * 2 + gs] - Qavg) / tot;
+      }
+      gcor_r[(ed * nt + t) * 2 + gs] = (R)g;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// continuity with the corrected transport over [t0, t0 + T] (elevations given)
+// ---------------------------------------------------------------------------
+template <typename R, int TP>
+__global__ void __launch_bounds__(TP, (MB<R, TP>::value))
+    k_cont_split(DevMesh m, AdvIn<R> in, const double* __restrict__ e0, const double* __restrict__ e1,
+                 double T, R* __restrict__ W) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int* s_off = reinterpret_cast<int*>(smem);
+  const int TPX = TP + m.max_tile_tris;
+  R* s_F = reinterpret_cast<R*>(smem + ((TP + 1) * sizeof(int) + 15) / 16 * 16);
+  const Tile tl = tile_of_block(m);
+  const int i = threadIdx.x;
+  Own2<R> own;
+  if (i < tl.np) load_own2<R, true>(m, tl.p0 + i, in, own);
+  load_offsets<TP>(m, tl, s_off);
+  int slot = 0;
+  if (i < tl.np) {
+    const int lt = tile_tri_of(s_off, tl.nt, i);
+    const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
+    slot = i + lt;
+    R o[2][3] = {{0, 0, 0}, {0, 0, 0}}, dummy[2][3], qx[2][3], qy[2][3];
+    prism_adv<R, true>(m, t, k, tl.p0 + i, N, own, in, o, dummy, qx, qy);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) s_F[(c * 3 + a) * TPX + slot] = o[c][a];
+  }
+  __syncthreads();
+  const int nt = m.n_tri;
+  for (int j = threadIdx.x; j < 3 * tl.nt; j += TP) {
+    const int a = j / tl.nt, lt = j - a * tl.nt;
+    const int t = tl.t0 + lt, base = s_off[lt] + lt, N = s_off[lt + 1] - s_off[lt];
+    const int ia = a * nt + t;
+    R* Ft = s_F + a * TPX + base;
+    R* Fb = s_F + (3 + a) * TPX + base;
+    const R dm_fac = (R)((m.jh[t] / 12.0) * (e1[ia] - e0[ia]) * m.ih[ia] / T);
+    R s = (R)0;
+    for (int k = N - 1; k >= 0; --k) {
+      const R dm = dm_fac * dz_rest_r<R>(m, ia, k, N);
+      const R ft = Ft[k] - dm, fb = Fb[k] - dm;
+      const R wt = ft + fb + s;
+      Fb[k] = fb - ft + s;
+      Ft[k] = wt;
+      s = wt;
+    }
+  }
+  __syncthreads();
+  if (i < tl.np) {
+#pragma unroll
+    for (int r = 0; r < 6; ++r) W[(size_t)r * m.P + tl.p0 + i] = s_F[r * TPX + slot];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3D update of a field pair (KIND 0: momentum u, v; KIND 1: tracers T, S)
+//   M1 f1 = M0 f0 + dt (R_h(f_ev; qbar) + extras [+ M1 F2D/H1] [+ A f_ev]),
+// implicit: (M1 - dt A(W, st1)) f1 = ... without A f_ev.
+// ---------------------------------------------------------------------------
+struct UpdArgs {
+  double dt;
+  double kap_v;  // vertical viscosity / diffusivity
+  double kap_h;  // horizontal viscosity / diffusivity
+};
+
+template <typename R, int TP, int KIND, bool IMPL>
+__global__ void __launch_bounds__(TP, (MB<R, TP>::value))
+    k_update(DevMesh m, AdvIn<R> in, const R* __restrict__ G0, const R* __restrict__ G1,
+             const R* __restrict__ W, const R* __restrict__ Rx, const R* __restrict__ Ry,
+             const R* __restrict__ F2x, const R* __restrict__ F2y, const R* __restrict__ st0,
+             const R* __restrict__ st1, PhysParams pp, UpdArgs ua, R* O0, R* O1,
+             int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int* s_off = reinterpret_cast<int*>(smem);
+  const int TPX = TP + m.max_tile_tris;
+  const size_t ob = ((TP + 1) * sizeof(int) + 15) / 16 * 16;
+  R* s_b = reinterpret_cast<R*>(smem + ob);                 // [12][TPX]
+  R* s_W = s_b + 12 * (size_t)TPX;                          // [6][TPX]
+  R* s_C = s_W + 6 * (size_t)TPX;                           // [3][4][TPX]
+  R* s_st = s_C + 12 * (size_t)TPX;                         // [3][TP]
+  const Tile tl = tile_of_block(m);
+  const int i = threadIdx.x;
+  const int nt = m.n_tri, P = m.P;
+  Own2<R> own;
+  if (i < tl.np) load_own2<R, KIND == 0>(m, tl.p0 + i, in, own);
+  if (IMPL) {
+    for (int j = threadIdx.x; j < 3 * tl.nt; j += TP) {
+      const int a = j / tl.nt, lt = j - a * tl.nt;
+      s_st[a * TP + lt] = st1[a * nt + tl.t0 + lt];
+    }
+  }
+  load_offsets<TP>(m, tl, s_off);
+  const R dt = (R)ua.dt;
+  int slot = 0;
+  R o0[2][3], o1[2][3];
+  if (i < tl.np) {
+    const int lt = tile_tri_of(s_off, tl.nt, i);
+    const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
+    const int p = tl.p0 + i;
+    slot = i + lt;
+    R F0[2][3] = {{0, 0, 0}, {0, 0, 0}}, F1[2][3] = {{0, 0, 0}, {0, 0, 0}}, qx[2][3], qy[2][3];
+    prism_adv<R, false>(m, t, k, p, N, own, in, F0, F1, qx, qy);
+    const R w6 = Geo<R>::jh(m, t) * (R)(1.0 / 6.0);
+    if (KIND == 0) {
+      momentum_extras<R>(m, t, k, p, N, own, in.U, in.V, in.st, Rx, Ry, pp, F0, F1);
+    } else if (ua.kap_h > 0.0) {
+      prism_sipg<R>(m, t, k, N, own.f0, in.F0, in.st, (R)ua.kap_h, (R)pp.pen_h, F0);
+      prism_sipg<R>(m, t, k, N, own.f1, in.F1, in.st, (R)ua.kap_h, (R)pp.pen_h, F1);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int ia = a * nt + t;
+      const R dr = dz_rest_r<R>(m, ia, k, N);
+      const R hz0 = (R)0.5 * dr * st0[ia];
+      R b[2][2];
+      const size_t i0 = (size_t)a * P + p, i1 = (size_t)(3 + a) * P + p;
+      lumped<R>(w6 * hz0, G0[i0], G0[i1], b[0][0], b[0][1]);
+      lumped<R>(w6 * hz0, G1[i0], G1[i1], b[1][0], b[1][1]);
+      R add0 = 0, add1 = 0;
+      if (KIND == 0) {  // M1 F2D / H1 = (J_h/12) dz_rest (1/h) F2D
+        const R cfac = Geo<R>::jh(m, t) * (R)(1.0 / 12.0) * dr * Geo<R>::ih(m, ia);
+        add0 = cfac * F2x[ia];
+        add1 = cfac * F2y[ia];
+      }
+      R r00 = b[0][0] + dt * (F0[0][a] + add0), r01 = b[0][1] + dt * (F0[1][a] + add0);
+      R r10 = b[1][0] + dt * (F1[0][a] + add1), r11 = b[1][1] + dt * (F1[1][a] + add1);
+      if (IMPL) {
+        s_b[(0 * 3 + a) * TPX + slot] = r00;
+        s_b[(1 * 3 + a) * TPX + slot] = r01;
+        s_b[(2 * 3 + a) * TPX + slot] = r10;
+        s_b[(3 * 3 + a) * TPX + slot] = r11;
+      } else {
+        // + dt A(W, st_ev) f_ev, A couples the layers above and below
+        const R kap = (R)ua.kap_v, pen = (R)pp.pen_v;
+        const R stv = in.st[ia];
+        const R dz = dr * stv, idz = rcp<R>(dz);
+        R idzm = idz, idzp = idz;
+        if (m.n_levels != 0) {
+          if (k > 0) idzm = rcp<R>(dz_rest_r<R>(m, ia, k - 1, N) * stv);
+          if (k + 1 < N) idzp = rcp<R>(dz_rest_r<R>(m, ia, k + 1, N) * stv);
+        }
+        const R W0 = W[(size_t)a * P + p], W1 = W[(size_t)(3 + a) * P + p];
+        const R Wn = (k + 1 < N) ? W[(size_t)a * P + p + 1] : (R)0;
+        R A[2][2], AL[2][2], AU[2][2];
+        vertical_A<R>(k, N, w6, idzm, idz, idzp, W0, W1, Wn, kap, pen, A, AL, AU);
+        const R* Fs[2] = {in.F0 ? in.F0 : in.U, in.F1 ? in.F1 : in.V};
+        R rr[2][2] = {{r00, r01}, {r10, r11}};
+        const R fk[2][2] = {{own.f0[0][a], own.f0[1][a]}, {own.f1[0][a], own.f1[1][a]}};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          R fm0 = 0, fm1 = 0, fp0 = 0, fp1 = 0;
+          if (k > 0) { fm0 = Fs[q][i0 - 1]; fm1 = Fs[q][i1 - 1]; }
+          if (k + 1 < N) { fp0 = Fs[q][i0 + 1]; fp1 = Fs[q][i1 + 1]; }
+#pragma unroll
+          for (int rw = 0; rw < 2; ++rw)
+            rr[q][rw] += dt * (A[rw][0] * fk[q][0] + A[rw][1] * fk[q][1] + AL[rw][0] * fm0 +
+                               AL[rw][1] * fm1 + AU[rw][0] * fp0 + AU[rw][1] * fp1);
+        }
+        // M1^-1: (6 / (J_h hz1)) [[2,-1],[-1,2]] per vertex-layer
+        const R hz1 = (R)0.5 * dr * st1[ia];
+        const R im = rcp<R>(w6 * hz1);
+        o0[0][a] = im * ((R)2 * rr[0][0] - rr[0][1]);
+        o0[1][a] = im * ((R)2 * rr[0][1] - rr[0][0]);
+        o1[0][a] = im * ((R)2 * rr[1][0] - rr[1][1]);
+        o1[1][a] = im * ((R)2 * rr[1][1] - rr[1][0]);
+      }
+    }
+    if (IMPL) {
+#pragma unroll
+      for (int r = 0; r < 6; ++r) s_W[r * TPX + slot] = W[(size_t)r * P + p];
+    }
+  }
+  if (IMPL) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < 3 * tl.nt; j += TP) {
+      const int a = j / tl.nt, lt = j - a * tl.nt;
+      const int t = tl.t0 + lt, base = s_off[lt] + lt, N = s_off[lt + 1] - s_off[lt];
+      R* C = s_C + (size_t)a * 4 * TPX + base;
+      column_thomas2<R>(m, t, a * nt + t, N, s_st[a * TP + lt], s_W + a * TPX + base,
+                        s_W + (3 + a) * TPX + base, s_b + (0 * 3 + a) * TPX + base,
+                        s_b + (1 * 3 + a) * TPX + base, s_b + (2 * 3 + a) * TPX + base,
+                        s_b + (3 * 3 + a) * TPX + base, C, C + TPX, C + 2 * TPX, C + 3 * TPX,
+                        (R)ua.kap_v, (R)pp.pen_v, dt);
+    }
+    __syncthreads();
+    if (i < tl.np) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          o0[c][a] = s_b[(c * 3 + a) * TPX + slot];
+          o1[c][a] = s_b[((2 + c) * 3 + a) * TPX + slot];
+        }
+    }
+  }
+  if (i < tl.np) {
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const size_t idx = (size_t)(c * 3 + a) * P + tl.p0 + i;
+        O0[idx] = o0[c][a];
+        O1[idx] = o1[c][a];
+        ok &= (bool)isfinite(o0[c][a]) & (bool)isfinite(o1[c][a]);
+      }
+    if (!ok) atomicOr(err, (int)SLIM_ERRBIT_NONFINITE);
+  }
+}
+
+size_t tile_smem(const DevMesh& m, int TP, size_t esz, int rows) {
+  return ((TP + 1) * sizeof(int) + 15) / 16 * 16 + (size_t)rows * (TP + m.max_tile_tris) * esz;
+}
+size_t update_smem(const DevMesh& m, int TP, size_t esz) {
+  return ((TP + 1) * sizeof(int) + 15) / 16 * 16 + (size_t)30 * (TP + m.max_tile_tris) * esz +
+         (size_t)3 * TP * esz;
+}
+
+PhysParams phys(const slim_params& p) {
+  PhysParams q;
+  q.g = p.g; q.rho0 = p.rho0; q.f = p.coriolis_f; q.alpha = p.eos_alpha; q.beta = p.eos_beta;
+  q.T0 = p.eos_T0; q.S0 = p.eos_S0; q.nu_h = p.nu_h; q.kappa_h = p.kappa_h; q.nu_v = p.nu_v;
+  q.kappa_v = p.kappa_v; q.cd = p.drag_cd; q.pen_v = p.penalty_v; q.pen_h = p.penalty_h;
+  return q;
+}
+
+#define SLIM_CU(expr)                                                          \
+  do {                                                                         \
+    cudaError_t _e = (expr);                                                   \
+    if (_e != cudaSuccess) {                                                   \
+      set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));           \
+      return SLIM_ERR_CUDA;                                                    \
+    }                                                                          \
+  } while (0)
+
+template <typename R>
+cudaError_t launch_hpg(const DevMesh& m, int TP, const R* T, const R* S, const R* st,
+                       const PhysParams& pp, R* Rx, R* Ry, cudaStream_t s) {
+  SLIM_TP_SWITCH2(TP, {
+    const size_t sm = tile_smem(m, TPc, sizeof(R), 12);
+    cudaError_t e = set_smem2(k_hpg<R, TPc>, sm);
+    if (e != cudaSuccess) return e;
+    k_hpg<R, TPc><<<m.n_tiles, TPc, sm, s>>>(m, T, S, st, pp, Rx, Ry);
+  });
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_mompred(const DevMesh& m, int TP, const AdvIn<R>& in, const R* Rx, const R* Ry,
+                           const PhysParams& pp, SplitBufs* b, cudaStream_t s) {
+  SLIM_TP_SWITCH2(TP, {
+    const size_t sm = tile_smem(m, TPc, sizeof(R), 12);
+    cudaError_t e = set_smem2(k_mompred<R, TPc>, sm);
+    if (e != cudaSuccess) return e;
+    k_mompred<R, TPc><<<m.n_tiles, TPc, sm, s>>>(m, in, Rx, Ry, pp, b->S3x, b->S3y, b->Sqx, b->Sqy);
+  });
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_cont_split(const DevMesh& m, int TP, const AdvIn<R>& in, const double* e0,
+                              const double* e1, double T, R* W, cudaStream_t s) {
+  SLIM_TP_SWITCH2(TP, {
+    const size_t sm = tile_smem(m, TPc, sizeof(R), 6);
+    cudaError_t e = set_smem2(k_cont_split<R, TPc>, sm);
+    if (e != cudaSuccess) return e;
+    k_cont_split<R, TPc><<<m.n_tiles, TPc, sm, s>>>(m, in, e0, e1, T, W);
+  });
+  return cudaGetLastError();
+}
+
+template <typename R, int KIND, bool IMPL>
+cudaError_t launch_update(const DevMesh& m, int TP, const AdvIn<R>& in, const R* G0, const R* G1,
+                          const R* W, const R* Rx, const R* Ry, const R* F2x, const R* F2y,
+                          const R* st0, const R* st1, const PhysParams& pp, const UpdArgs& ua,
+                          R* O0, R* O1, int* err, cudaStream_t s) {
+  SLIM_TP_SWITCH2(TP, {
+    const size_t sm = update_smem(m, TPc, sizeof(R));
+    cudaError_t e = set_smem2(k_update<R, TPc, KIND, IMPL>, sm);
+    if (e != cudaSuccess) return e;
+    k_update<R, TPc, KIND, IMPL><<<m.n_tiles, TPc, sm, s>>>(m, in, G0, G1, W, Rx, Ry, F2x, F2y, st0,
+                                                            st1, pp, ua, O0, O1, err);
+  });
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// one stage of the split step
+// ---------------------------------------------------------------------------
+template <typename R>
+slim_status stage(slim_state* s, double t0, double dt, int n_sub, bool implicit, const R* u_ev,
+                  const R* v_ev, const R* T_ev, const R* S_ev, const R* st_ev, R* u_out, R* v_out,
+                  R* T_out, R* S_out, cudaStream_t stm) {
+  const DevMesh& m = s->mesh->d;
+  SplitBufs* b = s->sp;
+  const int TP = s->mesh->tile_prisms;
+  const PhysParams pp = phys(s->par);
+  const int nt = m.n_tri;
+  const size_t n2 = (size_t)3 * nt;
+  R* Rx = (R*)s->Rx;
+  R* Ry = (R*)s->Ry;
+  {
+    ProfScope ps(s, SLIM_PHASE_HPG, stm);
+    SLIM_CU(launch_hpg<R>(m, TP, T_ev, S_ev, st_ev, pp, Rx, Ry, stm));
+  }
+  AdvIn<R> pin{u_ev, v_ev, nullptr, nullptr, nullptr, nullptr, st_ev, nullptr, nullptr, nullptr};
+  {
+    ProfScope ps(s, SLIM_PHASE_MOM_PRED, stm);
+    SLIM_CU(launch_mompred<R>(m, TP, pin, Rx, Ry, pp, b, stm));
+  }
+  b->has_s3 = true;
+  // external mode from the state at t0
+  SLIM_CU(cudaMemcpyAsync(b->Ae, s->eta, n2 * 8, cudaMemcpyDeviceToDevice, stm));
+  SLIM_CU(cudaMemcpyAsync(b->AU, s->Qx, n2 * 8, cudaMemcpyDeviceToDevice, stm));
+  SLIM_CU(cudaMemcpyAsync(b->AV, s->Qy, n2 * 8, cudaMemcpyDeviceToDevice, stm));
+  SLIM_CU(cudaMemsetAsync(s->Qbx, 0, n2 * 8, stm));
+  SLIM_CU(cudaMemsetAsync(s->Qby, 0, n2 * 8, stm));
+  SLIM_CU(cudaMemsetAsync(b->Gb, 0, n2 * 2 * 8, stm));
+  const double dts = dt / n_sub;
+  const double A_[3] = {0.0, 0.75, 1.0 / 3.0}, B_[3] = {1.0, 0.25, 2.0 / 3.0};
+  const double bw_[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0}, ts_[3] = {0.0, 1.0, 0.5};
+  const int blk = 256, grd = (nt + blk - 1) / blk;
+  for (int q = 0; q < n_sub; ++q) {
+    double* ins[3][3] = {{b->Ae, b->AU, b->AV}, {b->Be, b->BU, b->BV}, {b->Ce, b->CU, b->CV}};
+    double* outs[3][3] = {{b->Be, b->BU, b->BV}, {b->Ce, b->CU, b->CV}, {b->Ae, b->AU, b->AV}};
+    for (int st = 0; st < 3; ++st) {
+      const double time = t0 + (q + ts_[st]) * dts;
+      const double tide = s->par.tide_amp * std::cos(2.0 * M_PI * time / s->par.tide_period);
+      ProfScope ps(s, SLIM_PHASE_EXT2D, stm);
+      k_ext2d<0><<<grd, blk, 0, stm>>>(m, ins[st][0], ins[st][1], ins[st][2], b->Ae, b->AU, b->AV,
+                                       b->S3x, b->S3y, b->cw, s->par.g, tide, A_[st], B_[st], dts,
+                                       bw_[st] / n_sub, outs[st][0], outs[st][1], outs[st][2],
+                                       s->Qbx, s->Qby, b->Gb);
+      SLIM_CU(cudaGetLastError());
+    }
+  }
+  {
+    ProfScope ps(s, SLIM_PHASE_MISC, stm);
+    k_couple2d<R><<<grd, blk, 0, stm>>>(m, b->Ae, b->AU, b->AV, s->Qx, s->Qy, b->S3x, b->S3y, b->Sqx,
+                                        b->Sqy, s->Qbx, s->Qby, b->Gb, st_ev, dt, b->F2x, b->F2y,
+                                        (R*)b->F2x_r, (R*)b->F2y_r, (R*)b->Dqx_r, (R*)b->Dqy_r,
+                                        (R*)b->gcor_r, (R*)b->st_end);
+    SLIM_CU(cudaGetLastError());
+  }
+  AdvIn<R> cin{u_ev, v_ev, nullptr, nullptr, nullptr, nullptr, st_ev, (const R*)b->Dqx_r,
+               (const R*)b->Dqy_r, (const R*)b->gcor_r};
+  {
+    ProfScope ps(s, SLIM_PHASE_CONTINUITY, stm);
+    SLIM_CU(launch_cont_split<R>(m, TP, cin, s->eta, b->Ae, dt, (R*)s->W, stm));
+  }
+  const R* st0 = (const R*)s->st_cur;
+  const R* st1 = (const R*)b->st_end;
+  UpdArgs um{dt, s->par.nu_v, s->par.nu_h};
+  UpdArgs ut{dt, s->par.kappa_v, s->par.kappa_h};
+  AdvIn<R> tin{u_ev, v_ev, T_ev, S_ev, (const R*)s->Text, (const R*)s->Sext, st_ev,
+               (const R*)b->Dqx_r, (const R*)b->Dqy_r, (const R*)b->gcor_r};
+  const R* U0 = (const R*)s->U;
+  const R* V0 = (const R*)s->V;
+  const R* T0 = (const R*)s->T;
+  const R* S0 = (const R*)s->S;
+  {
+    ProfScope ps(s, SLIM_PHASE_MOMENTUM, stm);
+    if (implicit)
+      SLIM_CU((launch_update<R, 0, true>(m, TP, cin, U0, V0, (const R*)s->W, Rx, Ry, (const R*)b->F2x_r,
+                                         (const R*)b->F2y_r, st0, st1, pp, um, u_out, v_out, s->err, stm)));
+    else
+      SLIM_CU((launch_update<R, 0, false>(m, TP, cin, U0, V0, (const R*)s->W, Rx, Ry, (const R*)b->F2x_r,
+                                          (const R*)b->F2y_r, st0, st1, pp, um, u_out, v_out, s->err, stm)));
+  }
+  {
+    ProfScope ps(s, SLIM_PHASE_TRACERS, stm);
+    if (implicit)
+      SLIM_CU((launch_update<R, 1, true>(m, TP, tin, T0, S0, (const R*)s->W, nullptr, nullptr, nullptr,
+                                         nullptr, st0, st1, pp, ut, T_out, S_out, s->err, stm)));
+    else
+      SLIM_CU((launch_update<R, 1, false>(m, TP, tin, T0, S0, (const R*)s->W, nullptr, nullptr, nullptr,
+                                          nullptr, st0, st1, pp, ut, T_out, S_out, s->err, stm)));
+  }
+  return SLIM_OK;
+}
+
+template <typename R>
+slim_status step_t(slim_state* s, double t, double dt, cudaStream_t stm) {
+  SplitBufs* b = s->sp;
+  const DevMesh& m = s->mesh->d;
+  const size_t n2 = (size_t)3 * m.n_tri;
+  R* U = (R*)s->U; R* V = (R*)s->V; R* T = (R*)s->T; R* S = (R*)s->S;
+  R* hu = (R*)s->tmp[0]; R* hv = (R*)s->tmp[1]; R* hT = (R*)s->tmp[2]; R* hS = (R*)s->tmp[3];
+  // stage 1: t -> t + dt/2, vertically implicit, n_sub/2 external steps
+  slim_status r = stage<R>(s, t, 0.5 * dt, s->par.n_sub / 2, true, U, V, T, S, (const R*)s->st_cur,
+                           hu, hv, hT, hS, stm);
+  if (r != SLIM_OK) return r;
+  SLIM_CU(cudaMemcpyAsync(b->st_half, b->st_end, n2 * sizeof(R), cudaMemcpyDeviceToDevice, stm));
+  SLIM_CU(cudaMemcpyAsync(b->eta_half, b->Ae, n2 * 8, cudaMemcpyDeviceToDevice, stm));
+  // stage 2: t -> t + dt from the same start, horizontal terms at the stage-1 state
+  r = stage<R>(s, t, dt, s->par.n_sub, false, hu, hv, hT, hS, (const R*)b->st_half, U, V, T, S, stm);
+  if (r != SLIM_OK) return r;
+  SLIM_CU(cudaMemcpyAsync(s->eta, b->Ae, n2 * 8, cudaMemcpyDeviceToDevice, stm));
+  SLIM_CU(cudaMemcpyAsync(s->Qx, b->AU, n2 * 8, cudaMemcpyDeviceToDevice, stm));
+  SLIM_CU(cudaMemcpyAsync(s->Qy, b->AV, n2 * 8, cudaMemcpyDeviceToDevice, stm));
+  SLIM_CU(cudaMemcpyAsync(s->st_cur, b->st_end, n2 * sizeof(R), cudaMemcpyDeviceToDevice, stm));
+  SLIM_CU(cudaMemcpyAsync(s->eta_next, b->Ae, n2 * 8, cudaMemcpyDeviceToDevice, stm));
+  return SLIM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// entry points used by the C ABI
+// ---------------------------------------------------------------------------
 size_t split_aux2d_len(const DevMesh& m) { return (size_t)16 * m.n_tri; }
-slim_status split_rhs2d(slim_state*, double, double*, cudaStream_t) {
-  set_error("split scheme not available");
-  return SLIM_ERR_UNSUPPORTED;
+
+slim_status split_alloc(slim_state* s) {
+  if (s->sp) return SLIM_OK;
+  const DevMesh& m = s->mesh->d;
+  const size_t n2 = (size_t)3 * m.n_tri;
+  SplitBufs* b = new SplitBufs();
+  s->sp = b;
+  double** d2[] = {&b->Ae, &b->AU, &b->AV, &b->Be, &b->BU, &b->BV, &b->Ce, &b->CU, &b->CV,
+                   &b->S3x, &b->S3y, &b->Sqx, &b->Sqy, &b->F2x, &b->F2y, &b->eta_half};
+  for (double** p : d2) {
+    SLIM_CU(cudaMalloc((void**)p, n2 * 8));
+    SLIM_CU(cudaMemset(*p, 0, n2 * 8));
+    s->allocs.push_back(*p);
+  }
+  double** d6[] = {&b->Gb, &b->cw};
+  for (double** p : d6) {
+    SLIM_CU(cudaMalloc((void**)p, n2 * 2 * 8));
+    SLIM_CU(cudaMemset(*p, 0, n2 * 2 * 8));
+    s->allocs.push_back(*p);
+  }
+  void** r2[] = {&b->F2x_r, &b->F2y_r, &b->Dqx_r, &b->Dqy_r, &b->st_half, &b->st_end};
+  for (void** p : r2) {
+    SLIM_CU(cudaMalloc(p, n2 * s->esz));
+    SLIM_CU(cudaMemset(*p, 0, n2 * s->esz));
+    s->allocs.push_back(*p);
+  }
+  SLIM_CU(cudaMalloc(&b->gcor_r, n2 * 2 * s->esz));
+  SLIM_CU(cudaMemset(b->gcor_r, 0, n2 * 2 * s->esz));
+  s->allocs.push_back(b->gcor_r);
+  const int grd = (m.n_tri + 255) / 256;
+  k_wave_speed<<<grd, 256>>>(m, s->par.g, b->cw);
+  SLIM_CU(cudaGetLastError());
+  return SLIM_OK;
 }
-slim_status split_step(slim_state*, double, double, cudaStream_t) {
-  set_error("split scheme not available");
-  return SLIM_ERR_UNSUPPORTED;
+
+void split_free(slim_state* s) {
+  delete s->sp;
+  s->sp = nullptr;
 }
-int split_kernel_count(const slim_state*) { return 0; }
+
+void* split_field(slim_state* s, int field) {
+  if (!s->sp) return nullptr;
+  switch (field) {
+    case SLIM_FIELD_S3_X: return s->sp->S3x;
+    case SLIM_FIELD_S3_Y: return s->sp->S3y;
+    case SLIM_FIELD_F2D_X: return s->sp->F2x;
+    case SLIM_FIELD_F2D_Y: return s->sp->F2y;
+  }
+  return nullptr;
+}
+
+slim_status split_hpg(slim_state* s, cudaStream_t st) {
+  const DevMesh& m = s->mesh->d;
+  const PhysParams pp = phys(s->par);
+  if (s->prec == SLIM_FP64)
+    SLIM_CU(launch_hpg<double>(m, s->mesh->tile_prisms, (const double*)s->T, (const double*)s->S,
+                               (const double*)s->st_cur, pp, (double*)s->Rx, (double*)s->Ry, st));
+  else
+    SLIM_CU(launch_hpg<float>(m, s->mesh->tile_prisms, (const float*)s->T, (const float*)s->S,
+                              (const float*)s->st_cur, pp, (float*)s->Rx, (float*)s->Ry, st));
+  return SLIM_OK;
+}
+
+slim_status split_rhs2d(slim_state* s, double t, double* out, cudaStream_t st) {
+  if (!s->sp) { set_error("split buffers missing"); return SLIM_ERR_UNSUPPORTED; }
+  const DevMesh& m = s->mesh->d;
+  SplitBufs* b = s->sp;
+  const double tide = s->par.tide_amp * std::cos(2.0 * M_PI * t / s->par.tide_period);
+  const int grd = (m.n_tri + 255) / 256;
+  k_ext2d<1><<<grd, 256, 0, st>>>(m, s->eta, s->Qx, s->Qy, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                  b->cw, s->par.g, tide, 0.0, 0.0, 0.0, 0.0, out, nullptr, nullptr,
+                                  nullptr, nullptr, nullptr);
+  SLIM_CU(cudaGetLastError());
+  return SLIM_OK;
+}
+
+slim_status split_step(slim_state* s, double t, double dt, cudaStream_t st) {
+  if (!s->sp) { set_error("split buffers missing"); return SLIM_ERR_UNSUPPORTED; }
+  return s->prec == SLIM_FP64 ? step_t<double>(s, t, dt, st) : step_t<float>(s, t, dt, st);
+}
+
+int split_kernel_count(const slim_state* s) {
+  // per stage: hpg, mompred, 3 n_sub_stage external stages, couple, continuity, momentum, tracers
+  const int n = s->par.n_sub;
+  return 2 * 6 + 3 * (n / 2 + n);
+}
+
 }  // namespace slim

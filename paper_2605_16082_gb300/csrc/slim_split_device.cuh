@@ -1,0 +1,397 @@
+// Device building blocks of the baroclinic (split-IMEX) path: advection of two
+// fields by the corrected transport, horizontal SIPG, vertical operator blocks,
+// a 2x2-block Thomas sweep with two right-hand sides.
+#pragma once
+
+#include "slim_device.cuh"
+
+namespace slim {
+
+// Inputs of the horizontal advection residual.
+template <typename R>
+struct AdvIn {
+  const R* U;      // transport velocity of the evaluation state
+  const R* V;
+  const R* F0;     // advected fields (the transport velocity itself for momentum)
+  const R* F1;
+  const R* E0;     // open-boundary exterior profiles (null: zero gradient)
+  const R* E1;
+  const R* st;     // stretch of the evaluation geometry
+  const R* Dqx;    // [3][n_tri] Qbar - column sum of q (null: no correction)
+  const R* Dqy;
+  const R* gcor;   // [(e n_tri + t) 2 + g] face correction delta / tot (null: none)
+};
+
+template <typename R>
+struct Own2 {
+  R u[2][3], v[2][3], f0[2][3], f1[2][3];
+};
+
+// SELF: the advected fields are the transport velocity (momentum)
+template <typename R, bool SELF>
+__device__ __forceinline__ void load_own2(const DevMesh& m, int p, const AdvIn<R>& in, Own2<R>& o) {
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const size_t idx = (size_t)(c * 3 + a) * m.P + p;
+      o.u[c][a] = in.U[idx];
+      o.v[c][a] = in.V[idx];
+      if (SELF) {
+        o.f0[c][a] = o.u[c][a];
+        o.f1[c][a] = o.v[c][a];
+      } else {
+        o.f0[c][a] = in.F0[idx];
+        o.f1[c][a] = in.F1[idx];
+      }
+    }
+}
+
+// Closed-form volume term of -div(q f) tested with phi_a psi_c (see prism_rh).
+template <typename R>
+__device__ __forceinline__ void adv_volume(const DevMesh& m, int t, const R qx[2][3], const R qy[2][3],
+                                           const R f[2][3], R out[2][3]) {
+  const int nt = m.n_tri;
+  const R w24 = Geo<R>::jh(m, t) * (R)(1.0 / 24.0);
+  R Yx[2][2], Yy[2][2];
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    const R sqx = qx[d][0] + qx[d][1] + qx[d][2];
+    const R sqy = qy[d][0] + qy[d][1] + qy[d][2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const R sf = f[e][0] + f[e][1] + f[e][2];
+      const R px = qx[d][0] * f[e][0] + qx[d][1] * f[e][1] + qx[d][2] * f[e][2];
+      const R py = qy[d][0] * f[e][0] + qy[d][1] * f[e][1] + qy[d][2] * f[e][2];
+      Yx[d][e] = w24 * (sqx * sf + px);
+      Yy[d][e] = w24 * (sqy * sf + py);
+    }
+  }
+  const R h2 = (R)0.5, h6 = (R)(1.0 / 6.0);
+  const R Xx0 = h2 * Yx[0][0] + h6 * (Yx[0][1] + Yx[1][0] + Yx[1][1]);
+  const R Xx1 = h2 * Yx[1][1] + h6 * (Yx[0][0] + Yx[0][1] + Yx[1][0]);
+  const R Xy0 = h2 * Yy[0][0] + h6 * (Yy[0][1] + Yy[1][0] + Yy[1][1]);
+  const R Xy1 = h2 * Yy[1][1] + h6 * (Yy[0][0] + Yy[0][1] + Yy[1][0]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const R gxa = Geo<R>::gx(m, a * nt + t), gya = Geo<R>::gy(m, a * nt + t);
+    out[0][a] += gxa * Xx0 + gya * Xy0;
+    out[1][a] += gxa * Xx1 + gya * Xy1;
+  }
+}
+
+// Horizontal advection residual of two fields (NF = 2) or of T = 1 (UNIT) by the
+// transport q = (dz/2) u (+ the node correction (dz_rest/h)(Qbar - sum q)/2), with
+// the lateral normal transport {q}.n + (hz^- + hz^+)(s) gcor(s) on faces where a
+// face correction is given.  Accumulates into out0 / out1 and returns the nodal
+// transport of the prism in qxo / qyo.
+template <typename R, bool UNIT>
+__device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p, int N,
+                                          const Own2<R>& own, const AdvIn<R>& in, R out0[2][3],
+                                          R out1[2][3], R qxo[2][3], R qyo[2][3]) {
+  const int nt = m.n_tri, P = m.P;
+  R hz[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int ia = a * nt + t;
+    const R dr = dz_rest_r<R>(m, ia, k, N);
+    hz[a] = (R)0.5 * dr * in.st[ia];
+    R cx = 0, cy = 0;
+    if (in.Dqx) {
+      const R f = (R)0.5 * dr * Geo<R>::ih(m, ia);
+      cx = f * in.Dqx[ia];
+      cy = f * in.Dqy[ia];
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      qxo[c][a] = hz[a] * own.u[c][a] + cx;
+      qyo[c][a] = hz[a] * own.v[c][a] + cy;
+    }
+  }
+  if (UNIT) {
+    R one[2][3] = {{1, 1, 1}, {1, 1, 1}};
+    adv_volume<R>(m, t, qxo, qyo, one, out0);
+  } else {
+    adv_volume<R>(m, t, qxo, qyo, own.f0, out0);
+    adv_volume<R>(m, t, qxo, qyo, own.f1, out1);
+  }
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int4 ei = m.einfo[e * nt + t];
+    const int nb = ei.x;
+    if (nb == -1) continue;  // wall
+    const int a0 = e, a1 = (e + 1) % 3;
+    const R nxe = Geo<R>::nx(m, e * nt + t), nye = Geo<R>::ny(m, e * nt + t);
+    const R half_len = (R)0.5 * Geo<R>::len(m, e * nt + t);
+    R qo[2][2], qb[2][2], fo0[2][2], fo1[2][2], fb0[2][2], fb1[2][2], hzb[2] = {0, 0};
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      qo[0][c] = qxo[c][a0] * nxe + qyo[c][a0] * nye;
+      qo[1][c] = qxo[c][a1] * nxe + qyo[c][a1] * nye;
+      if (!UNIT) {
+        fo0[0][c] = own.f0[c][a0]; fo0[1][c] = own.f0[c][a1];
+        fo1[0][c] = own.f1[c][a0]; fo1[1][c] = own.f1[c][a1];
+      }
+    }
+    bool has_nb = false;
+    if (nb >= 0) {
+      const int Nn = ei.z;
+      if (k >= Nn) continue;  // wall against a shallower neighbour column
+      has_nb = true;
+      const int pn = ei.y + k;
+      const int loc = ei.w;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int l = j ? ((loc >> 2) & 3) : (loc & 3);
+        const int il = l * nt + nb;
+        const R dr = dz_rest_r<R>(m, il, k, Nn);
+        const R h = (R)0.5 * dr * in.st[il];
+        hzb[j] = h;
+        R cn = 0;
+        if (in.Dqx) cn = (R)0.5 * dr * Geo<R>::ih(m, il) * (in.Dqx[il] * nxe + in.Dqy[il] * nye);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const size_t idx = (size_t)(c * 3 + l) * P + pn;
+          qb[j][c] = h * (in.U[idx] * nxe + in.V[idx] * nye) + cn;
+          if (!UNIT) {
+            fb0[j][c] = in.F0 ? in.F0[idx] : in.U[idx];
+            fb1[j][c] = in.F1 ? in.F1[idx] : in.V[idx];
+          }
+        }
+      }
+    } else {  // open boundary
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          qb[j][c] = qo[j][c];
+          if (!UNIT) {
+            const size_t idx = (size_t)(c * 3 + (j ? a1 : a0)) * P + p;
+            fb0[j][c] = in.E0 ? in.E0[idx] : fo0[j][c];
+            fb1[j][c] = in.E1 ? in.E1[idx] : fo1[j][c];
+          }
+        }
+    }
+    R gc[2] = {0, 0};
+    if (in.gcor) {
+      gc[0] = in.gcor[(e * nt + t) * 2 + 0];
+      gc[1] = in.gcor[(e * nt + t) * 2 + 1];
+    }
+#pragma unroll
+    for (int gs = 0; gs < 2; ++gs) {
+      const R b0 = gs ? (R)SLIM_GL2 : (R)SLIM_GL1;  // basis of vertex a0 at edge point gs
+      const R b1 = gs ? (R)SLIM_GL1 : (R)SLIM_GL2;
+      const R corr = (b0 * (hz[a0] + hzb[0]) + b1 * (hz[a1] + hzb[1])) * gc[gs];
+#pragma unroll
+      for (int gz = 0; gz < 2; ++gz) {
+        const R z0 = gz ? (R)SLIM_GL2 : (R)SLIM_GL1;  // psi_top at the zeta point
+        const R z1 = gz ? (R)SLIM_GL1 : (R)SLIM_GL2;
+        const R B00 = b0 * z0, B01 = b0 * z1, B10 = b1 * z0, B11 = b1 * z1;
+        const R qno = B00 * qo[0][0] + B01 * qo[0][1] + B10 * qo[1][0] + B11 * qo[1][1];
+        R qn = qno;
+        if (has_nb) qn = (R)0.5 * (qno + (B00 * qb[0][0] + B01 * qb[0][1] + B10 * qb[1][0] + B11 * qb[1][1]));
+        qn += corr;
+        if (UNIT) {
+          const R f = half_len * qn;
+          out0[0][a0] -= f * B00; out0[1][a0] -= f * B01;
+          out0[0][a1] -= f * B10; out0[1][a1] -= f * B11;
+        } else {
+          const bool up = qn > (R)0;
+          const R f0 = half_len * qn * (up ? (B00 * fo0[0][0] + B01 * fo0[0][1] + B10 * fo0[1][0] + B11 * fo0[1][1])
+                                           : (B00 * fb0[0][0] + B01 * fb0[0][1] + B10 * fb0[1][0] + B11 * fb0[1][1]));
+          const R f1 = half_len * qn * (up ? (B00 * fo1[0][0] + B01 * fo1[0][1] + B10 * fo1[1][0] + B11 * fo1[1][1])
+                                           : (B00 * fb1[0][0] + B01 * fb1[0][1] + B10 * fb1[1][0] + B11 * fb1[1][1]));
+          out0[0][a0] -= f0 * B00; out0[1][a0] -= f0 * B01;
+          out0[0][a1] -= f0 * B10; out0[1][a1] -= f0 * B11;
+          out1[0][a0] -= f1 * B00; out1[1][a0] -= f1 * B01;
+          out1[0][a1] -= f1 * B10; out1[1][a1] -= f1 * B11;
+        }
+      }
+    }
+  }
+}
+
+// Horizontal SIPG of one field on coordinate surfaces (weight nu z_zeta):
+//   -int nu z_zeta grad f . grad v + oint [{nu z_zeta grad f}.n v
+//                                          + 1/2 nu z_zeta^- grad v.n [f] - sigma {z_zeta}[f] v]
+// sigma = pen nu / min(r_in^-, r_in^+), interior faces only (natural elsewhere).
+template <typename R>
+__device__ __forceinline__ void prism_sipg(const DevMesh& m, int t, int k, int N, const R f[2][3],
+                                           const R* __restrict__ F, const R* __restrict__ st,
+                                           R nu, R pen, R out[2][3]) {
+  const int nt = m.n_tri, P = m.P;
+  R gx[3], gy[3], hz[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    gx[a] = Geo<R>::gx(m, a * nt + t);
+    gy[a] = Geo<R>::gy(m, a * nt + t);
+    hz[a] = (R)0.5 * dz_rest_r<R>(m, a * nt + t, k, N) * st[a * nt + t];
+  }
+  R gux[2], guy[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    gux[c] = f[c][0] * gx[0] + f[c][1] * gx[1] + f[c][2] * gx[2];
+    guy[c] = f[c][0] * gy[0] + f[c][1] * gy[1] + f[c][2] * gy[2];
+  }
+  // volume: -nu (J_h/6)(sum hz) sum_d G_dc grad f_d . grad phi_a
+  {
+    const R w = nu * Geo<R>::jh(m, t) * (R)(1.0 / 6.0) * (hz[0] + hz[1] + hz[2]);
+    const R G2 = (R)(2.0 / 3.0), G1 = (R)(1.0 / 3.0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const R d0 = gux[0] * gx[a] + guy[0] * gy[a];
+      const R d1 = gux[1] * gx[a] + guy[1] * gy[a];
+      out[0][a] -= w * (G2 * d0 + G1 * d1);
+      out[1][a] -= w * (G1 * d0 + G2 * d1);
+    }
+  }
+  const R rin_t = (sizeof(R) == 4) ? (R)m.rin_f[t] : (R)m.rin[t];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int4 ei = m.einfo[e * nt + t];
+    const int nb = ei.x;
+    if (nb < 0) continue;
+    const int Nn = ei.z;
+    if (k >= Nn) continue;
+    const int pn = ei.y + k;
+    const int loc = ei.w;
+    const int l0 = loc & 3, l1 = (loc >> 2) & 3;
+    const int a0 = e, a1 = (e + 1) % 3;
+    const R nxe = Geo<R>::nx(m, e * nt + t), nye = Geo<R>::ny(m, e * nt + t);
+    const R half_len = (R)0.5 * Geo<R>::len(m, e * nt + t);
+    R fn[2][3];
+    R gnx[2] = {0, 0}, gny[2] = {0, 0};
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const R gxb = Geo<R>::gx(m, b * nt + nb), gyb = Geo<R>::gy(m, b * nt + nb);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        fn[c][b] = F[(size_t)(c * 3 + b) * P + pn];
+        gnx[c] += fn[c][b] * gxb;
+        gny[c] += fn[c][b] * gyb;
+      }
+    }
+    const R hzn0 = (R)0.5 * dz_rest_r<R>(m, l0 * nt + nb, k, Nn) * st[l0 * nt + nb];
+    const R hzn1 = (R)0.5 * dz_rest_r<R>(m, l1 * nt + nb, k, Nn) * st[l1 * nt + nb];
+    const R rin_n = (sizeof(R) == 4) ? (R)m.rin_f[nb] : (R)m.rin[nb];
+    const R sig = pen * nu / fmin(rin_t, rin_n);
+    const R gno[2] = {gux[0] * nxe + guy[0] * nye, gux[1] * nxe + guy[1] * nye};
+    const R gnn[2] = {gnx[0] * nxe + gny[0] * nye, gnx[1] * nxe + gny[1] * nye};
+    R gvn[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gvn[a] = gx[a] * nxe + gy[a] * nye;
+#pragma unroll
+    for (int gs = 0; gs < 2; ++gs) {
+      const R b0 = gs ? (R)SLIM_GL2 : (R)SLIM_GL1;
+      const R b1 = gs ? (R)SLIM_GL1 : (R)SLIM_GL2;
+      const R zzo = b0 * hz[a0] + b1 * hz[a1];
+      const R zzn = b0 * hzn0 + b1 * hzn1;
+#pragma unroll
+      for (int gz = 0; gz < 2; ++gz) {
+        const R z0 = gz ? (R)SLIM_GL2 : (R)SLIM_GL1;
+        const R z1 = gz ? (R)SLIM_GL1 : (R)SLIM_GL2;
+        const R fo = b0 * (z0 * f[0][a0] + z1 * f[1][a0]) + b1 * (z0 * f[0][a1] + z1 * f[1][a1]);
+        const R fnb = b0 * (z0 * fn[0][l0] + z1 * fn[1][l0]) + b1 * (z0 * fn[0][l1] + z1 * fn[1][l1]);
+        const R flux = (R)0.5 * nu * (zzo * (z0 * gno[0] + z1 * gno[1]) + zzn * (z0 * gnn[0] + z1 * gnn[1]));
+        const R jump = fo - fnb;
+        const R pj = sig * (R)0.5 * (zzo + zzn) * jump;
+        const R sj = (R)0.5 * nu * zzo * jump;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const R va = (a == a0) ? b0 : ((a == a1) ? b1 : (R)0);
+          out[0][a] += half_len * ((flux - pj) * va * z0 + sj * gvn[a] * z0);
+          out[1][a] += half_len * ((flux - pj) * va * z1 + sj * gvn[a] * z1);
+        }
+      }
+    }
+  }
+}
+
+// Vertical operator A of block row k (advection by W + omega x SIPG diffusion),
+// as in assemble_row but without the mass and the time step.
+template <typename R>
+__device__ __forceinline__ void vertical_A(int k, int N, R omega, R idzm, R idz, R idzp, R W0, R W1,
+                                           R Wn, R kap, R pen, R A[2][2], R AL[2][2], R AU[2][2]) {
+  Row<R> row;
+  // assemble_row computes K = M - bdt A; with bdt = -1 and the mass removed we get A
+  assemble_row<R>(k, N, omega, idzm, (R)0, idz, idzp, W0, W1, Wn, kap, pen, (R)-1, row);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      A[i][j] = row.D[i][j];
+      AL[i][j] = row.L[i][j];
+      AU[i][j] = row.U[i][j];
+    }
+}
+
+// 2x2-block Thomas sweep of one vertex column with two right-hand sides sharing
+// the matrix (M(st) - bdt A).  b?t/b?b: right-hand sides of field ? (top/bottom
+// rows), overwritten by the solution; C0..C3 scratch.
+template <typename R>
+__device__ __forceinline__ void column_thomas2(const DevMesh& m, int t, int ia, int N, R st,
+                                               const R* __restrict__ Wt, const R* __restrict__ Wb,
+                                               R* __restrict__ b0t, R* __restrict__ b0b,
+                                               R* __restrict__ b1t, R* __restrict__ b1b,
+                                               R* __restrict__ C0, R* __restrict__ C1,
+                                               R* __restrict__ C2, R* __restrict__ C3, R kap, R pen,
+                                               R bdt) {
+  const R omega = Geo<R>::jh(m, t) * (R)(1.0 / 6.0);
+  R z[2][2] = {{0, 0}, {0, 0}};
+  R c00 = 0, c01 = 0, c10 = 0, c11 = 0;
+  R dz = dz_rest_r<R>(m, ia, 0, N) * st;
+  R idz = rcp<R>(dz);
+  R idzm = idz;
+  for (int k = 0; k < N; ++k) {
+    R dzp = dz, idzp = idz;
+    if (k + 1 < N && m.n_levels != 0) {
+      dzp = dz_rest_r<R>(m, ia, k + 1, N) * st;
+      idzp = rcp<R>(dzp);
+    }
+    const R Wn = (k + 1 < N) ? Wt[k + 1] : (R)0;
+    Row<R> row;
+    assemble_row<R>(k, N, omega, idzm, dz, idz, idzp, Wt[k], Wb[k], Wn, kap, pen, bdt, row);
+    R Dp[2][2];
+    Dp[0][0] = row.D[0][0] - (row.L[0][0] * c00 + row.L[0][1] * c10);
+    Dp[0][1] = row.D[0][1] - (row.L[0][0] * c01 + row.L[0][1] * c11);
+    Dp[1][0] = row.D[1][0] - (row.L[1][0] * c00 + row.L[1][1] * c10);
+    Dp[1][1] = row.D[1][1] - (row.L[1][0] * c01 + row.L[1][1] * c11);
+    R Di[2][2];
+    inv2<R>(Dp, Di);
+    R* bt[2] = {b0t, b1t};
+    R* bb[2] = {b0b, b1b};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const R y0 = bt[q][k] - (row.L[0][0] * z[q][0] + row.L[0][1] * z[q][1]);
+      const R y1 = bb[q][k] - (row.L[1][0] * z[q][0] + row.L[1][1] * z[q][1]);
+      z[q][0] = Di[0][0] * y0 + Di[0][1] * y1;
+      z[q][1] = Di[1][0] * y0 + Di[1][1] * y1;
+      bt[q][k] = z[q][0];
+      bb[q][k] = z[q][1];
+    }
+    c00 = Di[0][0] * row.U[0][0] + Di[0][1] * row.U[1][0];
+    c01 = Di[0][0] * row.U[0][1] + Di[0][1] * row.U[1][1];
+    c10 = Di[1][0] * row.U[0][0] + Di[1][1] * row.U[1][0];
+    c11 = Di[1][0] * row.U[0][1] + Di[1][1] * row.U[1][1];
+    C0[k] = c00; C1[k] = c01; C2[k] = c10; C3[k] = c11;
+    idzm = idz;
+    dz = dzp;
+    idz = idzp;
+  }
+  R* bt[2] = {b0t, b1t};
+  R* bb[2] = {b0b, b1b};
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    R x0 = z[q][0], x1 = z[q][1];
+    for (int k = N - 2; k >= 0; --k) {
+      const R n0 = bt[q][k] - (C0[k] * x0 + C1[k] * x1);
+      const R n1 = bb[q][k] - (C2[k] * x0 + C3[k] * x1);
+      bt[q][k] = n0;
+      bb[q][k] = n1;
+      x0 = n0;
+      x1 = n1;
+    }
+  }
+}
+
+}  // namespace slim

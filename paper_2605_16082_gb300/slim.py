@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libslim.so")
 SLIM_FP64, SLIM_MIXED = 0, 1
 SLIM_SCHEME_TRACER, SLIM_SCHEME_SPLIT = 0, 1
 FIELD = dict(T=0, S=1, U=2, V=3, W=4, R_X=5, R_Y=6, T_EXT=7, S_EXT=8, ETA=16, QX=17, QY=18, ETA_NEXT=19,
-             QBAR_X=20, QBAR_Y=21)
+             QBAR_X=20, QBAR_Y=21, S3_X=22, S3_Y=23, F2D_X=24, F2D_Y=25)
 FIELD_IS_3D = {f: (v < 16) for f, v in FIELD.items()}
 
 # every symbol declared in include/slim.h
@@ -26,7 +26,7 @@ EXPORTED = ["slim_params_default", "slim_status_string", "slim_last_error", "sli
             "slim_mesh_destroy", "slim_mesh_info", "slim_state_alloc", "slim_state_free",
             "slim_state_set_params", "slim_state_upload", "slim_state_download",
             "slim_state_field_ptr", "slim_state_check", "slim_rhs3d", "slim_continuity",
-            "slim_rhs2d", "slim_vertical_solve", "slim_step", "slim_tracer_mass",
+            "slim_rhs2d", "slim_vertical_solve", "slim_hpg", "slim_step", "slim_tracer_mass",
             "slim_step_kernel_count", "slim_profile_begin", "slim_profile_end",
             "slim_phase_name"]
 PHASES = ["continuity", "tracer_stage", "hpg", "mom_pred", "ext2d", "momentum", "tracers", "misc"]
@@ -75,6 +75,7 @@ def lib() -> C.CDLL:
             "slim_rhs2d": ([_vp, _d, _vp, _vp], _i),
             "slim_vertical_solve": ([_vp, _i, _d, _vp, _vp, _vp], _i),
             "slim_step": ([_vp, _d, _d, _vp], _i),
+            "slim_hpg": ([_vp, _vp], _i),
             "slim_tracer_mass": ([_vp, _i, _dp, _vp], _i),
             "slim_step_kernel_count": ([_vp], _i),
             "slim_profile_begin": ([_vp, _i], _i),
@@ -201,6 +202,10 @@ def slim_rhs2d(state: int, t: float, out_dev: int, stream: int = 0) -> None:
 def slim_vertical_solve(state: int, field: int, beta_dt: float, rhs_dev: int, out_dev: int,
                         stream: int = 0) -> None:
     _check(lib().slim_vertical_solve(state, int(field), float(beta_dt), rhs_dev, out_dev, stream))
+
+
+def slim_hpg(state: int, stream: int = 0) -> None:
+    _check(lib().slim_hpg(state, stream))
 
 
 def slim_step(state: int, t: float, dt: float, stream: int = 0) -> None:

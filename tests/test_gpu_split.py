@@ -1,0 +1,205 @@
+"""GPU parity of the baroclinic split-IMEX path (C ABI) against the FP64 oracle.
+
+FP64 bar: relative L2 <= 1e-12 per field per step (3D u, v, T, S; 2D eta, U, V;
+the stage-2 intermediates r, W, Qbar, S3 and F2D).  Cases: a graded basin with an
+open tidal boundary (several tiles, ragged last tile), a square basin, and a
+z-level basin with uneven columns (1..N layers, walls against shallower
+neighbours)."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def slim():
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2605_16082_gb300 import slim as s
+    torch.cuda.init()
+    return s
+
+
+def case_mesh(name):
+    if name == "basin":
+        return wl.c2_mesh(2500, 5, 0)
+    if name == "square":
+        return wl.meshes.square_mesh(10, 4000.0, 4, lambda x, y: 15.0 + 20.0 * x / 4000.0,
+                                     lambda x, y: x > 4000.0 - 1e-6)
+    if name == "zlevel":
+        return wl.c4_mesh(3000, 0, n_max=12, h_max=60.0)
+    raise KeyError(name)
+
+
+def initial(m, seed=0):
+    rng = np.random.default_rng(seed)
+    x, y, z, s = wl.fields.node_positions_sigma(m)
+    Lx = max(m.xy[:, 0].max(), 1.0)
+    Ly = max(m.xy[:, 1].max(), 1.0)
+    u = 0.2 * np.sin(np.pi * x / Lx) * np.cos(np.pi * y / Ly) * (1.2 - s)
+    v = 0.1 * np.cos(np.pi * x / Lx) * (0.4 + s)
+    T = 15.0 + 10.0 * np.exp(z / 40.0) + 0.5 * np.sin(3 * x / Lx)
+    S = 34.0 - 2.0 * z / 60.0 + 0.3 * np.cos(2 * y / Ly)
+    eta = 0.05 * np.cos(np.pi * m.xy[m.tri][:, :, 0].T / Lx)
+    U = 0.5 * rng.standard_normal((3, m.n_tri)) * 0 + 1.0 * np.sin(np.pi * m.xy[m.tri][:, :, 0].T / Lx)
+    V = np.zeros((3, m.n_tri))
+    return dict(U=u.ravel(), V=v.ravel(), T=T.ravel(), S=S.ravel(), ETA=eta.ravel(), QX=U.ravel(), QY=V.ravel())
+
+
+def params(slim, **kw):
+    base = dict(scheme=slim.SLIM_SCHEME_SPLIT, n_sub=4, nu_h=0.5, kappa_h=0.5, tide_amp=0.4,
+                tide_period=3600.0)
+    base.update(kw)
+    return slim.slim_params_default(**base)
+
+
+def oracle_params(p):
+    from oracle import baroclinic as bc
+    return bc.Params(g=p.g, rho0=p.rho0, f=p.coriolis_f, alpha=p.eos_alpha, beta=p.eos_beta,
+                     T0=p.eos_T0, S0=p.eos_S0, kappa_v=p.kappa_v, nu_v=p.nu_v, kappa_h=p.kappa_h,
+                     nu_h=p.nu_h, cd=p.drag_cd, penalty_v=p.penalty_v, penalty_h=p.penalty_h,
+                     tide_amp=p.tide_amp, tide_period=p.tide_period, n_sub=p.n_sub)
+
+
+def oracle_state(m, om, ini):
+    from oracle import baroclinic as bc
+    from oracle import tracer as tr
+    P, nt = om.P, m.n_tri
+    st = bc.State(u=tr.to3(ini["U"], P), v=tr.to3(ini["V"], P), T=tr.to3(ini["T"], P),
+                  S=tr.to3(ini["S"], P), eta=tr.to2(ini["ETA"], nt), U=tr.to2(ini["QX"], nt),
+                  V=tr.to2(ini["QY"], nt))
+    st.T_ext = st.T.copy()
+    st.S_ext = st.S.copy()
+    return st
+
+
+def model(slim, m, prec, p, ini, tile=256):
+    mod = slim.Model(m, prec, p, tile_prisms=tile)
+    for k, v in ini.items():
+        mod.upload(k, v)
+    return mod
+
+
+@pytest.mark.parametrize("case", ["basin", "square", "zlevel"])
+def test_hpg_parity(slim, case):
+    from oracle import baroclinic as bc
+    from oracle.mesh import OMesh
+    m = case_mesh(case)
+    ini = initial(m)
+    p = params(slim)
+    om = OMesh(m)
+    st = oracle_state(m, om, ini)
+    with model(slim, m, slim.SLIM_FP64, p, ini) as mod:
+        assert mod.info["n_tiles"] > 1
+        slim.slim_hpg(mod.state)
+        rx, ry = mod.download("R_X"), mod.download("R_Y")
+    ox, oy = bc.hpg(om, oracle_params(p), st.T, st.S, st.eta)
+    assert rel_l2(rx, ox) < TOL64
+    assert rel_l2(ry, oy) < TOL64
+
+
+@pytest.mark.parametrize("case", ["basin", "square"])
+def test_rhs2d_parity(slim, case):
+    import torch
+    from oracle import baroclinic as bc
+    from oracle.mesh import OMesh
+    m = case_mesh(case)
+    ini = initial(m)
+    p = params(slim)
+    om = OMesh(m)
+    st = oracle_state(m, om, ini)
+    with model(slim, m, slim.SLIM_FP64, p, ini) as mod:
+        out = torch.zeros(9 * m.n_tri, dtype=torch.float64, device="cuda")
+        slim.slim_rhs2d(mod.state, 1234.5, out.data_ptr())
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().reshape(3, 3, m.n_tri)
+    Re, RU, RV, _ = bc.mode2d_residual(om, oracle_params(p), st.eta, st.U, st.V, 1234.5)
+    assert rel_l2(got[0], Re) < TOL64
+    assert rel_l2(got[1], RU) < TOL64
+    assert rel_l2(got[2], RV) < TOL64
+
+
+FIELDS3 = [("U", "u"), ("V", "v"), ("T", "T"), ("S", "S")]
+FIELDS2 = [("ETA", "eta"), ("QX", "U"), ("QY", "V")]
+
+
+@pytest.mark.parametrize("case", ["basin", "square", "zlevel"])
+def test_split_step_parity_fp64(slim, case):
+    from oracle import baroclinic as bc
+    from oracle.mesh import OMesh
+    m = case_mesh(case)
+    ini = initial(m)
+    p = params(slim)
+    om = OMesh(m)
+    st = oracle_state(m, om, ini)
+    par = oracle_params(p)
+    dt = 10.0 * wl.fields.dt_2d(m)
+    with model(slim, m, slim.SLIM_FP64, p, ini) as mod:
+        for n in range(2):
+            d1, d2 = {}, {}
+            st = bc.split_step(om, par, st, n * dt, dt, d1, d2)
+            slim.slim_step(mod.state, n * dt, dt)
+            slim.slim_state_check(mod.state)
+            for f, o in FIELDS3 + FIELDS2:
+                assert rel_l2(mod.download(f), getattr(st, o)) < TOL64, (n, f)
+            assert rel_l2(mod.download("R_X"), d2["r"][0]) < TOL64, n
+            assert rel_l2(mod.download("W"), d2["W"]) < TOL64, n
+            assert rel_l2(mod.download("QBAR_X"), d2["Qbar"][0]) < TOL64, n
+            assert rel_l2(mod.download("S3_X"), d2["S3"][0]) < TOL64, n
+            assert rel_l2(mod.download("F2D_Y"), d2["F2D"][1]) < TOL64, n
+
+
+def test_split_step_parity_tiles(slim):
+    """Same step with every tile size gives the oracle's result."""
+    from oracle import baroclinic as bc
+    from oracle.mesh import OMesh
+    m = case_mesh("basin")
+    ini = initial(m, 1)
+    p = params(slim)
+    om = OMesh(m)
+    st = bc.split_step(om, oracle_params(p), oracle_state(m, om, ini), 0.0, 30.0)
+    for tile in (128, 512):
+        with model(slim, m, slim.SLIM_FP64, p, ini, tile=tile) as mod:
+            slim.slim_step(mod.state, 0.0, 30.0)
+            for f, o in FIELDS3 + FIELDS2:
+                assert rel_l2(mod.download(f), getattr(st, o)) < TOL64, (tile, f)
+
+
+def test_split_lake_at_rest_gpu(slim):
+    m = case_mesh("basin")
+    x, y, z, s = wl.fields.node_positions_sigma(m)
+    ini = wl.c2_initial_state(m)
+    p = params(slim, tide_amp=0.0, kappa_v=0.0, kappa_h=0.0)
+    for prec, tol in ((slim.SLIM_FP64, 1e-12), (slim.SLIM_MIXED, 1e-5)):
+        up = dict(U=ini["u"], V=ini["v"], T=ini["T"], S=ini["S"], ETA=ini["eta"], QX=ini["U"], QY=ini["V"])
+        with model(slim, m, prec, p, up) as mod:
+            for n in range(3):
+                slim.slim_step(mod.state, n * 40.0, 40.0)
+            assert np.abs(mod.download("ETA")).max() < tol
+            assert np.abs(mod.download("U")).max() < tol
+            assert np.abs(mod.download("T") - ini["T"]).max() < tol * 30
+
+
+def test_split_mixed_precision_error(slim):
+    from oracle import baroclinic as bc
+    from oracle.mesh import OMesh
+    m = case_mesh("basin")
+    ini = initial(m)
+    p = params(slim)
+    om = OMesh(m)
+    st = oracle_state(m, om, ini)
+    par = oracle_params(p)
+    dt = 10.0 * wl.fields.dt_2d(m)
+    with model(slim, m, slim.SLIM_MIXED, p, ini) as mod:
+        for n in range(3):
+            st = bc.split_step(om, par, st, n * dt, dt)
+            slim.slim_step(mod.state, n * dt, dt)
+        errs = {f: rel_l2(mod.download(f), getattr(st, o)) for f, o in FIELDS3 + FIELDS2}
+    for f, e in errs.items():
+        assert e < 2e-5, (f, e)
