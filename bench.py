@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="basin_tracer", choices=sorted(wl.WORKLOADS))
+    ap.add_argument("--workload", default="basin_baroclinic", choices=sorted(wl.WORKLOADS))
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -112,26 +112,46 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-def tracer_inputs(name: str):
+def workload_inputs(name: str):
+    """Mesh, parameter overrides, initial fields, time step and the number of 3D
+    fields a step updates."""
     W = wl.WORKLOADS[name]
     m = W["mesh"]()
-    if name == "square_tracer":
-        u, v = wl.c1_velocity(m)
-        T = wl.c1_tracer(m)
-    else:
-        u, v = wl.basin_velocity(m)
-        T = wl.c2_initial_state(m)["T"]
-    return m, W, dict(U=u, V=v, T=T, ETA=np.zeros(3 * m.n_tri))
+    if W["scheme"] == "tracer":
+        if name == "square_tracer":
+            u, v = wl.c1_velocity(m)
+            T = wl.c1_tracer(m)
+        else:
+            u, v = wl.basin_velocity(m)
+            T = wl.c2_initial_state(m)["T"]
+        return m, dict(kappa_v=W["kappa_v"]), dict(U=u, V=v, T=T, ETA=np.zeros(3 * m.n_tri)), W["dt"], 1
+    ini = wl.c2_initial_state(m) if name == "basin_baroclinic" else wl.c4_initial_state(m)
+    fields = dict(U=ini["u"], V=ini["v"], T=ini["T"], S=ini["S"], ETA=ini["eta"], QX=ini["U"], QY=ini["V"])
+    par = dict(scheme=1, n_sub=W["n_sub"], kappa_v=W["kappa_v"], nu_v=W["nu_v"],
+               kappa_h=W.get("kappa_h", 0.0), nu_h=W.get("nu_h", 0.0))
+    dt = W["n_sub"] * wl.fields.dt_2d(m)
+    return m, par, fields, dt, 4
 
 
-def stage_bytes(m, esz: int) -> float:
-    """Algorithmic bytes of one fused tracer-stage launch (average of the 3 stages):
-    per prism the stage reads T_p and T_n (stage 1: one array), u, v, W and writes T,
-    34 values on average; per triangle the geometry, adjacency and both elevations."""
+def phase_bytes(phase: str, m, esz: int, n_sub: int) -> float:
+    """Algorithmic bytes of one launch of a phase: every input read once and every
+    output written once (neighbour gathers counted once), per prism P and per
+    triangle n_tri; 2D arrays in FP64."""
     P, nt = m.n_prisms, m.n_tri
-    per_prism = 34.0 * esz
-    per_tri = (252.0 if esz == 8 else 172.0)
-    return P * per_prism + nt * per_tri
+    geo = 160.0 if esz == 4 else 240.0          # per-triangle geometry + adjacency
+    if phase == "tracer_stage":                  # T_p, T_n (avg), u, v, W -> T
+        return P * 34.0 * esz + nt * (geo + 2 * 3 * esz)
+    if phase == "continuity":                    # u, v -> W (+ 2D sums)
+        return P * 18.0 * esz + nt * (geo + 9 * 8 + 3 * esz)
+    if phase == "hpg":                           # T, S -> r
+        return P * 24.0 * esz + nt * (geo + 3 * esz)
+    if phase == "mom_pred":                      # u, v, r -> column sums
+        return P * 24.0 * esz + nt * (geo + 3 * esz + 12 * 8)
+    if phase in ("momentum", "tracers"):         # f_ev(2), f_0(2), u_ev(2, tracers), W, r -> f(2)
+        return P * 54.0 * esz + nt * (geo + 3 * 3 * esz + 18 * esz)
+    if phase == "ext2d":                         # stage and start states, source, averages
+        return nt * 8.0 * (9 + 9 + 6 + 6 + 9 + 12 + 12 + 6)
+    return float("nan")
 
 
 def run_ours(args, rank: int, world: int):
@@ -142,9 +162,9 @@ def run_ours(args, rank: int, world: int):
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    m, W, fields = tracer_inputs(args.workload)
-    dt = W["dt"]
-    dofs = 6.0 * m.n_prisms * 1
+    m, over, fields, dt, nf = workload_inputs(args.workload)
+    W = wl.WORKLOADS[args.workload]
+    dofs = 6.0 * m.n_prisms * nf
     precs = {"both": ["mixed", "fp64"], "mixed": ["mixed"], "fp64": ["fp64"]}[args.precision]
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
@@ -152,7 +172,7 @@ def run_ours(args, rank: int, world: int):
     clocks = None
     for pname in precs:
         prec = slim.SLIM_MIXED if pname == "mixed" else slim.SLIM_FP64
-        par = slim.slim_params_default(kappa_v=W["kappa_v"])
+        par = slim.slim_params_default(**over)
         mod = slim.Model(m, prec, par)
         for k, v in fields.items():
             mod.upload(k, v)
@@ -185,14 +205,14 @@ def run_ours(args, rank: int, world: int):
         dom = max(phases, key=lambda k: phases[k][0])
         dom_ms = phases[dom][0] / phases[dom][1]
         esz = 8 if pname == "fp64" else 4
-        ab = stage_bytes(m, esz) if dom == "tracer_stage" else float("nan")
+        ab = phase_bytes(dom, m, esz, W.get("n_sub", 0))
         r = dict(value=world * dofs / (ms_step / 1e3), ms_per_step=ms_step, phases=phases,
                  dominant=dom, dom_ms=dom_ms, alg_bytes=ab, gpu_launches=n_k * args.steps)
         # end to end through the public API with pinned host buffers
         if not args.no_e2e:
             pin = {k: torch.tensor(v, dtype=torch.float64).pin_memory() for k, v in fields.items()}
-            outT = torch.empty(6 * m.n_prisms, dtype=torch.float64).pin_memory()
-            outE = torch.empty(3 * m.n_tri, dtype=torch.float64).pin_memory()
+            outs = {k: torch.empty(b.numel(), dtype=torch.float64).pin_memory() for k, b in pin.items()
+                    if k in ("T", "ETA", "U", "V", "S")}
             ids = {k: slim.FIELD[k] for k in pin}
             torch.cuda.synchronize()
             barrier(world)
@@ -201,14 +221,14 @@ def run_ours(args, rank: int, world: int):
                 for k, buf in pin.items():
                     slim.slim_state_upload_ptr(mod.state, ids[k], buf.data_ptr(), sh)
                 slim.slim_step(mod.state, t, dt, sh); t += dt
-                slim.slim_state_download_ptr(mod.state, slim.FIELD["T"], outT.data_ptr(), sh)
-                slim.slim_state_download_ptr(mod.state, slim.FIELD["ETA"], outE.data_ptr(), sh)
+                for k, buf in outs.items():
+                    slim.slim_state_download_ptr(mod.state, slim.FIELD[k], buf.data_ptr(), sh)
             torch.cuda.synchronize()
             barrier(world)
             e2e_s = allmax(time.perf_counter() - t0, world) / args.steps
             r["e2e"] = dict(value=world * dofs / e2e_s, unit=UNIT,
                             h2d_bytes_per_step=int(sum(b.numel() * 8 for b in pin.values())),
-                            d2h_bytes_per_step=int((outT.numel() + outE.numel()) * 8))
+                            d2h_bytes_per_step=int(sum(b.numel() * 8 for b in outs.values())))
         mod.close()
         res[pname] = r
     return m, res, clocks
@@ -231,13 +251,15 @@ def allmax(x: float, world: int) -> float:
 
 
 # ---------------------------------------------------------------------------
-def oracle_sample(args, m, W, seconds: float):
+def oracle_sample(args, m, seconds: float):
     """The oracle as it stands on a bounded sample of the workload: a compact patch
     of consecutive (Hilbert-ordered) columns, stepped until ``seconds`` elapse."""
     from oracle import tracer as otr
+    from oracle import baroclinic as obc
     from oracle.mesh import OMesh
     from workloads.meshes import Mesh
-    n_patch = min(m.n_tri, 1200)
+    W = wl.WORKLOADS[args.workload]
+    n_patch = min(m.n_tri, 1200 if W["scheme"] == "tracer" else 400)
     idx = np.arange(n_patch)
     bnd = m.bnd[idx].copy()
     sub = Mesh(xy=m.xy, tri=m.tri[idx], h_tri=m.h_tri[idx], n_layers=m.n_layers[idx], bnd=bnd,
@@ -246,23 +268,43 @@ def oracle_sample(args, m, W, seconds: float):
     topo = wl.meshes._tag_boundary(sub.xy, sub.tri, None)
     sub.bnd = np.where((topo == 1) & (bnd == 2), 2, topo).astype(np.int8)
     om = OMesh(sub)
-    if args.workload == "square_tracer":
-        u, v = wl.c1_velocity(sub); T = wl.c1_tracer(sub)
-    else:
-        u, v = wl.basin_velocity(sub); T = wl.c2_initial_state(sub)["T"]
     P = om.P
-    u, v, T = otr.to3(u, P), otr.to3(v, P), otr.to3(T, P)
-    eta = np.zeros((3, sub.n_tri))
     steps = 0
     t0 = time.perf_counter()
-    while True:
-        eta, T, _ = otr.tracer_step(om, eta, T, u, v, W["dt"], W["kappa_v"])
-        steps += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
+    if W["scheme"] == "tracer":
+        if args.workload == "square_tracer":
+            u, v = wl.c1_velocity(sub); T = wl.c1_tracer(sub)
+        else:
+            u, v = wl.basin_velocity(sub); T = wl.c2_initial_state(sub)["T"]
+        u, v, T = otr.to3(u, P), otr.to3(v, P), otr.to3(T, P)
+        eta = np.zeros((3, sub.n_tri))
+        nf = 1
+        while True:
+            eta, T, _ = otr.tracer_step(om, eta, T, u, v, W["dt"], W["kappa_v"])
+            steps += 1
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                break
+    else:
+        ini = wl.c2_initial_state(sub) if args.workload == "basin_baroclinic" else wl.c4_initial_state(sub)
+        st = obc.State(u=otr.to3(ini["u"], P), v=otr.to3(ini["v"], P), T=otr.to3(ini["T"], P),
+                       S=otr.to3(ini["S"], P), eta=otr.to2(ini["eta"], sub.n_tri),
+                       U=otr.to2(ini["U"], sub.n_tri), V=otr.to2(ini["V"], sub.n_tri))
+        st.T_ext, st.S_ext = st.T.copy(), st.S.copy()
+        par = obc.Params(n_sub=W["n_sub"], kappa_v=W["kappa_v"], nu_v=W["nu_v"],
+                         kappa_h=W.get("kappa_h", 0.0), nu_h=W.get("nu_h", 0.0))
+        dt = W["n_sub"] * wl.fields.dt_2d(m)
+        nf = 4
+        tt = 0.0
+        while True:
+            st = obc.split_step(om, par, st, tt, dt)
+            tt += dt
+            steps += 1
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                break
     per_step = el / steps
-    return dict(value=6.0 * P / per_step, unit=UNIT, cores=1, kind="oracle",
+    return dict(value=6.0 * P * nf / per_step, unit=UNIT, cores=1, kind="oracle",
                 sample=f"{sub.n_tri} columns x {int(sub.n_layers.max())} layers ({P} prisms) of "
                        f"{args.workload}, {steps} steps in {el:.1f} s, numpy FP64, 1 thread")
 
@@ -277,16 +319,17 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
     W = wl.WORKLOADS[args.workload]
-    cfg = dict(workload=args.workload, scheme=W["scheme"], dt=W.get("dt"),
+    cfg = dict(workload=args.workload, scheme=W["scheme"], n_sub=W.get("n_sub"),
                l2="working set per step > L2 (no flush needed)")
     if args.impl == "reference":
         if rank != 0:
             return
         m = W["mesh"]()
         cfg.update(n_tri=m.n_tri, n_prisms=m.n_prisms, layers=int(m.n_layers.max()))
-        cb = oracle_sample(args, m, W, max(2.0, args.cpu_seconds * args.steps / 20.0))
+        cb = oracle_sample(args, m, max(2.0, args.cpu_seconds * args.steps / 20.0))
+        nf = 1 if W["scheme"] == "tracer" else 4
         line = dict(impl="reference", metric=METRIC, value=cb["value"], unit=UNIT, n_gpus=args.gpus,
-                    steps=args.steps, warmup=args.warmup, ms_per_step=6.0 * m.n_prisms / cb["value"] * 1e3,
+                    steps=args.steps, warmup=args.warmup, ms_per_step=6.0 * nf * m.n_prisms / cb["value"] * 1e3,
                     higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
                     data="synthetic", config=cfg, cpu_baseline=cb,
                     e2e=dict(value=cb["value"], unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
@@ -319,7 +362,7 @@ def main():
         line["fp64"] = dict(value=f["value"], ms_per_step=f["ms_per_step"], roofline=roof(f),
                             e2e=f.get("e2e"), phases_ms={k: v[0] for k, v in f["phases"].items()})
     if not args.no_cpu:
-        line["cpu_baseline"] = oracle_sample(args, m, W, args.cpu_seconds)
+        line["cpu_baseline"] = oracle_sample(args, m, args.cpu_seconds)
     print(json.dumps(line))
 
 

@@ -140,7 +140,7 @@ WORKLOADS = {
     "square_tracer": dict(mesh=lambda: c1_mesh(32, 10e3, 10), dt=5.0, steps=100,
                           kappa_v=1e-3, scheme="tracer"),
     "basin_baroclinic": dict(mesh=lambda: c2_mesh(200_000, 20, 0), steps=1000, n_sub=20,
-                             kappa_v=1e-3, nu_v=1e-3, scheme="split"),
+                             kappa_v=1e-3, nu_v=1e-3, kappa_h=1.0, nu_h=1.0, scheme="split"),
     "zlevel_baroclinic": dict(mesh=lambda: c4_mesh(500_000, 0), steps=3, n_sub=20,
-                              kappa_v=1e-3, nu_v=1e-3, scheme="split"),
+                              kappa_v=1e-3, nu_v=1e-3, kappa_h=1.0, nu_h=1.0, scheme="split"),
 }

@@ -273,7 +273,7 @@ def c2_mesh(target_tri: int = 200_000, n_layers: int = 20, seed: int = 0,
     Lx, Ly = 200e3, 100e3
     if s_min is None:
         # the triangle count scales like 1/s_min for a linear size ramp
-        s_min = 175.0 * (200_000 / target_tri)
+        s_min = 146.0 * (200_000 / target_tri)
     xy, tri = basin_mesh(Lx, Ly, 20, 10, s_min, 4000.0, seed)
     h_vert = 10.0 + 190.0 * (xy[:, 0] / Lx)
     bnd = _tag_boundary(xy, tri, lambda x, y: x > Lx - 1e-3)
