@@ -18,7 +18,9 @@ namespace slim {
 struct SplitBufs {
   // 2D (double): running external state A and two stage buffers
   double *Ae, *AU, *AV, *Be, *BU, *BV, *Ce, *CU, *CV;
-  double *S3x, *S3y, *Sqx, *Sqy, *Gb, *F2x, *F2y, *eta_half, *cw;
+  double *S3x, *S3y, *Sqx, *Sqy, *Gb, *F2x, *F2y, *eta_half, *cw, *icw, *iw6;
+  float *cw_f, *icw_f;
+  double *Qbx, *Qby;  // the state's time-averaged transport buffers
   // compute-type copies for the 3D kernels
   void *F2x_r, *F2y_r, *Dqx_r, *Dqy_r, *gcor_r, *st_half, *st_end;
   bool has_s3 = false;
@@ -59,9 +61,12 @@ __device__ __forceinline__ R zhat_r(const DevMesh& m, int i, int k) {
 // ---------------------------------------------------------------------------
 // wave speed of the 2D flux at every edge point: c = sqrt(g (h^- + h^+)/2)
 // ---------------------------------------------------------------------------
-__global__ void k_wave_speed(DevMesh m, double g, double* __restrict__ cw) {
+__global__ void k_wave_speed(DevMesh m, double g, double* __restrict__ cw, double* __restrict__ icw,
+                             float* __restrict__ cw_f, float* __restrict__ icw_f,
+                             double* __restrict__ iw6) {
   const int nt = m.n_tri;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    iw6[t] = 6.0 / m.jh[t];
     for (int e = 0; e < 3; ++e) {
       const int4 ei = m.einfo[e * nt + t];
       const int a0 = e, a1 = (e + 1) % 3;
@@ -73,7 +78,12 @@ __global__ void k_wave_speed(DevMesh m, double g, double* __restrict__ cw) {
           const int l0 = ei.w & 3, l1 = (ei.w >> 2) & 3;
           hn = b0 * m.h[l0 * nt + ei.x] + b1 * m.h[l1 * nt + ei.x];
         }
-        cw[(e * nt + t) * 2 + gs] = sqrt(g * 0.5 * (ho + hn));
+        const double c = sqrt(g * 0.5 * (ho + hn));
+        const int ip = (e * nt + t) * 2 + gs;
+        cw[ip] = c;
+        icw[ip] = 1.0 / (2.0 * c);
+        cw_f[ip] = (float)c;
+        icw_f[ip] = (float)(1.0 / (2.0 * c));
       }
     }
   }
@@ -364,7 +374,9 @@ __global__ void __launch_bounds__(TP, (MB<R, TP>::value))
 }
 
 // ---------------------------------------------------------------------------
-// 2D external-mode stage (FP64, thread per triangle)
+// 2D external-mode stage (thread per triangle).  The state, its update and the
+// accumulated averages are FP64 in both forms; the residual is evaluated in RC
+// (double for the FP64 form, float for the mixed form).
 //   R_eta,a = int Q.grad phi_a - oint phi_a F_eta
 //   R_Q,a   = int g eta (H grad phi_a + phi_a grad H) - oint phi_a g H^- eta^ n
 //   F_eta = {q} + c/2 (eta^- - eta^+),  eta^ = {eta} + (q^- - q^+)/(2c)
@@ -372,38 +384,49 @@ __global__ void __launch_bounds__(TP, (MB<R, TP>::value))
 // accumulated into Qbar and its eta flux into Gbar with weight bw.
 // MODE 0: update; MODE 1: residual only (out = R_eta, R_U, R_V).
 // ---------------------------------------------------------------------------
-template <int MODE>
-__global__ void k_ext2d(DevMesh m, const double* __restrict__ es, const double* __restrict__ Us,
-                        const double* __restrict__ Vs, const double* __restrict__ en,
-                        const double* __restrict__ Un, const double* __restrict__ Vn,
-                        const double* __restrict__ S3x, const double* __restrict__ S3y,
-                        const double* __restrict__ cw, double g, double tide, double alpha,
-                        double beta, double dt, double bw, double* __restrict__ eo,
-                        double* __restrict__ Uo, double* __restrict__ Vo, double* __restrict__ Qbx,
-                        double* __restrict__ Qby, double* __restrict__ Gb) {
+template <typename RC> struct Ext2dGeo;
+template <> struct Ext2dGeo<double> {
+  static __device__ __forceinline__ double c(const SplitBufs& b, int i) { return b.cw[i]; }
+  static __device__ __forceinline__ double ic(const SplitBufs& b, int i) { return b.icw[i]; }
+};
+template <> struct Ext2dGeo<float> {
+  static __device__ __forceinline__ float c(const SplitBufs& b, int i) { return b.cw_f[i]; }
+  static __device__ __forceinline__ float ic(const SplitBufs& b, int i) { return b.icw_f[i]; }
+};
+
+template <int MODE, typename RC>
+__global__ void __launch_bounds__(256)
+    k_ext2d(DevMesh m, SplitBufs bf, const double* __restrict__ es, const double* __restrict__ Us,
+            const double* __restrict__ Vs, const double* __restrict__ en, const double* __restrict__ Un,
+            const double* __restrict__ Vn, double g_, double tide_, double alpha, double beta,
+            double dt, double bw, double* __restrict__ eo, double* __restrict__ Uo,
+            double* __restrict__ Vo) {
   const int nt = m.n_tri;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
-  double e[3], U[3], V[3], H[3], gx[3], gy[3];
+  const RC g = (RC)g_, tide = (RC)tide_;
+  RC e[3], U[3], V[3], H[3], gx[3], gy[3];
+  double Ud[3], Vd[3], ed_[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int ia = a * nt + t;
-    e[a] = es[ia]; U[a] = Us[ia]; V[a] = Vs[ia];
-    H[a] = m.h[ia] + e[a];
-    gx[a] = m.gx[ia]; gy[a] = m.gy[ia];
+    ed_[a] = es[ia]; Ud[a] = Us[ia]; Vd[a] = Vs[ia];
+    e[a] = (RC)ed_[a]; U[a] = (RC)Ud[a]; V[a] = (RC)Vd[a];
+    H[a] = Geo<RC>::h(m, ia) + e[a];
+    gx[a] = Geo<RC>::gx(m, ia); gy[a] = Geo<RC>::gy(m, ia);
   }
-  const double jh = m.jh[t];
-  const double w6 = jh * (1.0 / 6.0), w24 = jh * (1.0 / 24.0);
-  const double sU = U[0] + U[1] + U[2], sV = V[0] + V[1] + V[2];
-  const double se = e[0] + e[1] + e[2], sH = H[0] + H[1] + H[2];
-  const double eH = w24 * (se * sH + e[0] * H[0] + e[1] * H[1] + e[2] * H[2]);
-  const double gHx = H[0] * gx[0] + H[1] * gx[1] + H[2] * gx[2];
-  const double gHy = H[0] * gy[0] + H[1] * gy[1] + H[2] * gy[2];
-  double Re[3], RU[3], RV[3];
+  const RC jh = Geo<RC>::jh(m, t);
+  const RC w6 = jh * (RC)(1.0 / 6.0), w24 = jh * (RC)(1.0 / 24.0);
+  const RC sU = U[0] + U[1] + U[2], sV = V[0] + V[1] + V[2];
+  const RC se = e[0] + e[1] + e[2], sH = H[0] + H[1] + H[2];
+  const RC eH = w24 * (se * sH + e[0] * H[0] + e[1] * H[1] + e[2] * H[2]);
+  const RC gHx = H[0] * gx[0] + H[1] * gx[1] + H[2] * gx[2];
+  const RC gHy = H[0] * gy[0] + H[1] * gy[1] + H[2] * gy[2];
+  RC Re[3], RU[3], RV[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     Re[a] = w6 * (sU * gx[a] + sV * gy[a]);
-    const double ea = w24 * (se + e[a]);
+    const RC ea = w24 * (se + e[a]);
     RU[a] = g * (eH * gx[a] + ea * gHx);
     RV[a] = g * (eH * gy[a] + ea * gHy);
   }
@@ -411,24 +434,24 @@ __global__ void k_ext2d(DevMesh m, const double* __restrict__ es, const double* 
   for (int ed = 0; ed < 3; ++ed) {
     const int4 ei = m.einfo[ed * nt + t];
     const int a0 = ed, a1 = (ed + 1) % 3;
-    const double nx = m.enx[ed * nt + t], ny = m.eny[ed * nt + t];
-    const double hl = 0.5 * m.elen[ed * nt + t];
-    double en0 = 0, en1 = 0, qn0 = 0, qn1 = 0;
+    const RC nx = Geo<RC>::nx(m, ed * nt + t), ny = Geo<RC>::ny(m, ed * nt + t);
+    const RC hl = (RC)0.5 * Geo<RC>::len(m, ed * nt + t);
+    RC en0 = 0, en1 = 0, qn0 = 0, qn1 = 0;
     if (ei.x >= 0) {
       const int l0 = ei.w & 3, l1 = (ei.w >> 2) & 3;
       const int i0 = l0 * nt + ei.x, i1 = l1 * nt + ei.x;
-      en0 = es[i0]; en1 = es[i1];
-      qn0 = Us[i0] * nx + Vs[i0] * ny;
-      qn1 = Us[i1] * nx + Vs[i1] * ny;
+      en0 = (RC)es[i0]; en1 = (RC)es[i1];
+      qn0 = (RC)Us[i0] * nx + (RC)Vs[i0] * ny;
+      qn1 = (RC)Us[i1] * nx + (RC)Vs[i1] * ny;
     }
-    const double qo0 = U[a0] * nx + V[a0] * ny, qo1 = U[a1] * nx + V[a1] * ny;
+    const RC qo0 = U[a0] * nx + V[a0] * ny, qo1 = U[a1] * nx + V[a1] * ny;
 #pragma unroll
     for (int gs = 0; gs < 2; ++gs) {
-      const double b0 = gs ? SLIM_GL2 : SLIM_GL1, b1 = gs ? SLIM_GL1 : SLIM_GL2;
-      const double eo_ = b0 * e[a0] + b1 * e[a1];
-      const double Ho = b0 * H[a0] + b1 * H[a1];
-      const double qo = b0 * qo0 + b1 * qo1;
-      double ex, qx;
+      const RC b0 = gs ? (RC)SLIM_GL2 : (RC)SLIM_GL1, b1 = gs ? (RC)SLIM_GL1 : (RC)SLIM_GL2;
+      const RC eo_ = b0 * e[a0] + b1 * e[a1];
+      const RC Ho = b0 * H[a0] + b1 * H[a1];
+      const RC qo = b0 * qo0 + b1 * qo1;
+      RC ex, qx;
       if (ei.x >= 0) {
         ex = b0 * en0 + b1 * en1;
         qx = b0 * qn0 + b1 * qn1;
@@ -439,11 +462,12 @@ __global__ void k_ext2d(DevMesh m, const double* __restrict__ es, const double* 
         ex = eo_;
         qx = -qo;
       }
-      const double c = cw[(ed * nt + t) * 2 + gs];
-      const double Fe = 0.5 * (qo + qx) + 0.5 * c * (eo_ - ex);
-      const double eh = 0.5 * (eo_ + ex) + (qo - qx) / (2.0 * c);
-      if (MODE == 0) Gb[(ed * nt + t) * 2 + gs] += bw * Fe;
-      const double gq = g * Ho * eh;
+      const int ip = (ed * nt + t) * 2 + gs;
+      const RC c = Ext2dGeo<RC>::c(bf, ip);
+      const RC Fe = (RC)0.5 * (qo + qx) + (RC)0.5 * c * (eo_ - ex);
+      const RC eh = (RC)0.5 * (eo_ + ex) + (qo - qx) * Ext2dGeo<RC>::ic(bf, ip);
+      if (MODE == 0) bf.Gb[ip] += bw * (double)Fe;
+      const RC gq = g * Ho * eh;
       Re[a0] -= hl * b0 * Fe; Re[a1] -= hl * b1 * Fe;
       RU[a0] -= hl * b0 * gq * nx; RU[a1] -= hl * b1 * gq * nx;
       RV[a0] -= hl * b0 * gq * ny; RV[a1] -= hl * b1 * gq * ny;
@@ -452,24 +476,21 @@ __global__ void k_ext2d(DevMesh m, const double* __restrict__ es, const double* 
   if (MODE == 1) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      eo[a * nt + t] = Re[a];
-      eo[(3 + a) * nt + t] = RU[a];
-      eo[(6 + a) * nt + t] = RV[a];
+      eo[a * nt + t] = (double)Re[a];
+      eo[(3 + a) * nt + t] = (double)RU[a];
+      eo[(6 + a) * nt + t] = (double)RV[a];
     }
     return;
   }
-  const double iw = 1.0 / w6;
+  const double iw = bf.iw6[t];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int ia = a * nt + t;
-    Qbx[ia] += bw * U[a];
-    Qby[ia] += bw * V[a];
-    const double e_new = alpha * en[ia] + beta * (e[a] + dt * Re[a] * iw);
-    const double U_new = alpha * Un[ia] + beta * (U[a] + dt * (RU[a] + S3x[ia]) * iw);
-    const double V_new = alpha * Vn[ia] + beta * (V[a] + dt * (RV[a] + S3y[ia]) * iw);
-    eo[ia] = e_new;
-    Uo[ia] = U_new;
-    Vo[ia] = V_new;
+    bf.Qbx[ia] += bw * Ud[a];
+    bf.Qby[ia] += bw * Vd[a];
+    eo[ia] = alpha * en[ia] + beta * (ed_[a] + dt * (double)Re[a] * iw);
+    Uo[ia] = alpha * Un[ia] + beta * (Ud[a] + dt * ((double)RU[a] + bf.S3x[ia]) * iw);
+    Vo[ia] = alpha * Vn[ia] + beta * (Vd[a] + dt * ((double)RV[a] + bf.S3y[ia]) * iw);
   }
 }
 
@@ -868,10 +889,14 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, bool implicit,
       const double time = t0 + (q + ts_[st]) * dts;
       const double tide = s->par.tide_amp * std::cos(2.0 * M_PI * time / s->par.tide_period);
       ProfScope ps(s, SLIM_PHASE_EXT2D, stm);
-      k_ext2d<0><<<grd, blk, 0, stm>>>(m, ins[st][0], ins[st][1], ins[st][2], b->Ae, b->AU, b->AV,
-                                       b->S3x, b->S3y, b->cw, s->par.g, tide, A_[st], B_[st], dts,
-                                       bw_[st] / n_sub, outs[st][0], outs[st][1], outs[st][2],
-                                       s->Qbx, s->Qby, b->Gb);
+      if (sizeof(R) == 8)
+        k_ext2d<0, double><<<grd, blk, 0, stm>>>(m, *b, ins[st][0], ins[st][1], ins[st][2], b->Ae, b->AU,
+                                                 b->AV, s->par.g, tide, A_[st], B_[st], dts,
+                                                 bw_[st] / n_sub, outs[st][0], outs[st][1], outs[st][2]);
+      else
+        k_ext2d<0, float><<<grd, blk, 0, stm>>>(m, *b, ins[st][0], ins[st][1], ins[st][2], b->Ae, b->AU,
+                                                b->AV, s->par.g, tide, A_[st], B_[st], dts,
+                                                bw_[st] / n_sub, outs[st][0], outs[st][1], outs[st][2]);
       SLIM_CU(cudaGetLastError());
     }
   }
@@ -964,7 +989,7 @@ slim_status split_alloc(slim_state* s) {
     SLIM_CU(cudaMemset(*p, 0, n2 * 8));
     s->allocs.push_back(*p);
   }
-  double** d6[] = {&b->Gb, &b->cw};
+  double** d6[] = {&b->Gb, &b->cw, &b->icw};
   for (double** p : d6) {
     SLIM_CU(cudaMalloc((void**)p, n2 * 2 * 8));
     SLIM_CU(cudaMemset(*p, 0, n2 * 2 * 8));
@@ -976,11 +1001,20 @@ slim_status split_alloc(slim_state* s) {
     SLIM_CU(cudaMemset(*p, 0, n2 * s->esz));
     s->allocs.push_back(*p);
   }
+  float** f6[] = {&b->cw_f, &b->icw_f};
+  for (float** p : f6) {
+    SLIM_CU(cudaMalloc((void**)p, n2 * 2 * sizeof(float)));
+    s->allocs.push_back(*p);
+  }
+  SLIM_CU(cudaMalloc((void**)&b->iw6, (size_t)m.n_tri * 8));
+  s->allocs.push_back(b->iw6);
+  b->Qbx = s->Qbx;
+  b->Qby = s->Qby;
   SLIM_CU(cudaMalloc(&b->gcor_r, n2 * 2 * s->esz));
   SLIM_CU(cudaMemset(b->gcor_r, 0, n2 * 2 * s->esz));
   s->allocs.push_back(b->gcor_r);
   const int grd = (m.n_tri + 255) / 256;
-  k_wave_speed<<<grd, 256>>>(m, s->par.g, b->cw);
+  k_wave_speed<<<grd, 256>>>(m, s->par.g, b->cw, b->icw, b->cw_f, b->icw_f, b->iw6);
   SLIM_CU(cudaGetLastError());
   return SLIM_OK;
 }
@@ -1019,9 +1053,12 @@ slim_status split_rhs2d(slim_state* s, double t, double* out, cudaStream_t st) {
   SplitBufs* b = s->sp;
   const double tide = s->par.tide_amp * std::cos(2.0 * M_PI * t / s->par.tide_period);
   const int grd = (m.n_tri + 255) / 256;
-  k_ext2d<1><<<grd, 256, 0, st>>>(m, s->eta, s->Qx, s->Qy, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                  b->cw, s->par.g, tide, 0.0, 0.0, 0.0, 0.0, out, nullptr, nullptr,
-                                  nullptr, nullptr, nullptr);
+  if (s->prec == SLIM_FP64)
+    k_ext2d<1, double><<<grd, 256, 0, st>>>(m, *b, s->eta, s->Qx, s->Qy, nullptr, nullptr, nullptr,
+                                            s->par.g, tide, 0.0, 0.0, 0.0, 0.0, out, nullptr, nullptr);
+  else
+    k_ext2d<1, float><<<grd, 256, 0, st>>>(m, *b, s->eta, s->Qx, s->Qy, nullptr, nullptr, nullptr,
+                                           s->par.g, tide, 0.0, 0.0, 0.0, 0.0, out, nullptr, nullptr);
   SLIM_CU(cudaGetLastError());
   return SLIM_OK;
 }

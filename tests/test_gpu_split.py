@@ -155,11 +155,11 @@ def test_split_step_parity_fp64(slim, case):
             slim.slim_state_check(mod.state)
             for f, o in FIELDS3 + FIELDS2:
                 assert rel_l2(mod.download(f), getattr(st, o)) < TOL64, (n, f)
-            assert rel_l2(mod.download("R_X"), d2["r"][0]) < TOL_R, n
-            assert rel_l2(mod.download("W"), d2["W"]) < TOL64, n
-            assert rel_l2(mod.download("QBAR_X"), d2["Qbar"][0]) < TOL64, n
-            assert rel_l2(mod.download("S3_X"), d2["S3"][0]) < TOL64, n
-            assert rel_l2(mod.download("F2D_Y"), d2["F2D"][1]) < TOL64, n
+            assert rel_l2(mod.download("R_X"), d2["r"][0]) < TOL_R, (n, "r")
+            assert rel_l2(mod.download("W"), d2["W"]) < TOL64, (n, "W")
+            assert rel_l2(mod.download("QBAR_X"), d2["Qbar"][0]) < TOL64, (n, "Qbar")
+            assert rel_l2(mod.download("S3_X"), d2["S3"][0]) < TOL64, (n, "S3")
+            assert rel_l2(mod.download("F2D_Y"), d2["F2D"][1]) < TOL64, (n, "F2D")
 
 
 def test_split_step_parity_tiles(slim):
