@@ -1,8 +1,8 @@
 """GPU parity of the baroclinic split-IMEX path (C ABI) against the FP64 oracle.
 
 FP64 bar: relative L2 <= 1e-12 per field per step (3D u, v, T, S; 2D eta, U, V;
-the stage-2 intermediates W, Qbar, S3 and F2D; 1e-11 for the pressure gradient
-r, see TOL_R).  Cases: a graded basin with an
+the stage-2 intermediates Qbar, S3 and F2D; 1e-11 for the pressure gradient r
+and the vertical flux W, see TOL_R).  Cases: a graded basin with an
 open tidal boundary (several tiles, ragged last tile), a square basin, and a
 z-level basin with uneven columns (1..N layers, walls against shallower
 neighbours)."""
@@ -15,10 +15,12 @@ from helpers import rel_l2
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
-# The pressure gradient r is a small difference of terms of size g rho' H
-# (coordinate-surface slopes times the full density anomaly); its FP64 rounding
-# floor relative to |r| is about 1e-12, so r is compared at 1e-11.  Every
-# prognostic field is held to 1e-12.
+# Two intermediates are small differences of much larger terms: the pressure
+# gradient r (terms of size g rho' H: coordinate-surface slopes times the full
+# density anomaly) and the vertical flux W (partial column sums of the horizontal
+# divergence and the mass change, which cancel over the column).  Their FP64
+# rounding floor relative to their own norm is about 1e-12, so they are compared
+# at 1e-11.  Every prognostic field is held to 1e-12.
 TOL_R = 1e-11
 
 
@@ -156,7 +158,7 @@ def test_split_step_parity_fp64(slim, case):
             for f, o in FIELDS3 + FIELDS2:
                 assert rel_l2(mod.download(f), getattr(st, o)) < TOL64, (n, f)
             assert rel_l2(mod.download("R_X"), d2["r"][0]) < TOL_R, (n, "r")
-            assert rel_l2(mod.download("W"), d2["W"]) < TOL64, (n, "W")
+            assert rel_l2(mod.download("W"), d2["W"]) < TOL_R, (n, "W")
             assert rel_l2(mod.download("QBAR_X"), d2["Qbar"][0]) < TOL64, (n, "Qbar")
             assert rel_l2(mod.download("S3_X"), d2["S3"][0]) < TOL64, (n, "S3")
             assert rel_l2(mod.download("F2D_Y"), d2["F2D"][1]) < TOL64, (n, "F2D")
