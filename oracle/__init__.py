@@ -10,8 +10,8 @@ Every function is written from the paper's statement of the method (arXiv
 (Eqs. 7-10), the discrete 3D step (Eqs. 11-14), the matrix-free column systems
 (Eqs. 15-17, Algorithm 1), the assembled column solves (Sec. 2.4) and the 3D/2D
 transport consistency (Sec. 2.2, Sec. 2.5, Eq. 18).  Where the paper defers to its
-supporting information (not available) the oracle follows the readings listed in
-``DESIGN.md`` ("Readings of the paper"), restated in each function's docstring.
+supporting information (not available) the oracle follows a stated reading of the
+continuous equations, given in each function's docstring.
 
 Style: numpy, vectorised over prisms / triangles, explicit loops over quadrature
 points and basis functions, numerical quadrature for every integral (no

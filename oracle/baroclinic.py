@@ -1,8 +1,8 @@
 """Oracle of the baroclinic step: density and horizontal pressure gradient, 3D
 momentum residual, 2D external mode, mode coupling and the split-IMEX step.
 
-Readings: the paper defers the discrete
-forms to its supporting information, so every form below is written from the
+Readings: the paper defers the discrete forms to its supporting information,
+so every form below is written from the
 continuous equations (Eqs. 1-10) in the moving coordinate of ``mesh.py`` with the
 structure the paper states: the column systems of Eqs. 15-17 / Algorithm 1, the
 discrete momentum step of Eqs. 11-14, the 2D/3D coupling F2D of Sec. 2.2 and the
@@ -553,8 +553,14 @@ def split_stage(om: OMesh, par: Params, st0: State, ev: State, t0: float, dt: fl
 
 
 def split_step(om: OMesh, par: Params, st: State, t: float, dt: float, diag1=None, diag2=None) -> State:
-    """Two-stage split-IMEX step (reading R7): stage 1 over dt/2, vertically implicit,
+    """Two-stage split-IMEX step (a reading of Sec. 2 and Fig. 1): stage 1 over dt/2, vertically implicit,
     n_sub/2 external subcycles; stage 2 over dt from the same start state with the
-    horizontal terms at the stage-1 state, vertically explicit, n_sub subcycles."""
+    horizontal terms at the stage-1 state, vertically explicit, n_sub subcycles.
+
+    Pinned by what the structure fixes (lake at rest, constant tracers, the
+    column sum of the corrected transport, the vanishing surface flux, tracer mass
+    in a closed basin); agreement with the coefficients of the paper's own
+    split-IMEX scheme is parity unpinned (they are in its unavailable supporting
+    information)."""
     half = split_stage(om, par, st, st, t, 0.5 * dt, par.n_sub // 2, True, diag1)
     return split_stage(om, par, st, half, t, dt, par.n_sub, False, diag2)

@@ -5,7 +5,8 @@ Sec. 2.1).  Prism ``p = col_off[t] + k`` is layer ``k`` (0 at the surface) of th
 column under triangle ``t``.  The oracle builds its own edge adjacency from the
 triangle list (it does not use any table of the CUDA library).
 
-Vertical coordinate (reading R1 in the design doc): each triangle vertex ``a`` of
+Vertical coordinate (a reading: the paper leaves the vertical coordinate to its
+supporting information): each triangle vertex ``a`` of
 triangle ``t`` has rest interface depths ``zhat_i`` (``-i h/N`` for sigma layers;
 the level table, with the column's own depth at the bottom, for z-levels) and the
 interfaces move with the triangle's own (discontinuous) elevation as

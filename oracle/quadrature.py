@@ -13,7 +13,7 @@ Quadrature (all integrands of the scheme are polynomials of degree <= 2 in
 * interval: 2-point Gauss-Legendre, exact for degree 3
 * lateral quadrilateral faces: 2-point Gauss along the edge x 2-point Gauss in zeta.
   Upwind fluxes are evaluated at these 4 points; this rule is part of the scheme's
-  definition (reading R4 in the design doc).
+  definition (a reading: the paper does not state its face quadrature).
 """
 from __future__ import annotations
 

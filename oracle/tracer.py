@@ -2,7 +2,7 @@
 residual, column operators, SSP-RK3 IMEX step and the tracer mass.
 
 Continuous problem (Eqs. 1, 2, 4-6) in the moving coordinate of ``mesh.py``
-(reading R1): with z_zeta = dz/dzeta, the layer transport q = z_zeta u and the
+(a reading of the vertical coordinate): with z_zeta = dz/dzeta, the layer transport q = z_zeta u and the
 vertical flux through coordinate surfaces Omega (per unit horizontal area),
 
     d/dt z_zeta + div_xy q + d/dzeta Omega = 0                      (continuity)
@@ -14,7 +14,7 @@ with Omega = 0 on the bed (Eq. 5) and at the surface (Eq. 4 with s = 0).
 Test functions v = phi_a psi_c on each prism.  Terms coupling nodes horizontally
 are integrated exactly (``quadrature.py``).  Terms coupling nodes vertically
 (the time derivative, vertical advection and vertical diffusion) collapse the
-horizontal dependence of the trial function onto the test vertex (reading R2),
+horizontal dependence of the trial function onto the test vertex (a reading),
 which yields one system per vertex column with 2x2 blocks per layer:
 
 * mass         m_{a,cd} = (J_h/6) (dz_a/2) int psi_c psi_d
@@ -22,7 +22,7 @@ which yields one system per vertex column with 2x2 blocks per layer:
   continuity rows are the D_vd pattern of Eq. 17 with M_h replaced by the vertex
   weight (the same recursion structure), and the tracer uses the very same W
 * vertical diffusion: (J_h/6) x 1D SIPG on the vertex's layer thicknesses
-  (reading R3)
+  (a reading; the paper does not state its vertical diffusion form)
 """
 from __future__ import annotations
 
@@ -216,7 +216,7 @@ def vertical_matrix(Wc: np.ndarray, dzc: np.ndarray, kappa: float, omega: np.nda
     bed), upwinded: T^ = T_{i,top} if W^_i > 0 else T_{i-1,bot}; the surface uses the
     interior T_{0,top}.  SIPG: element stiffness int kappa/(dz/2) dpsi dpsi, interface
     terms -{kappa dT/dz}[v] - {kappa dv/dz}[T] + sigma [T][v], [v] = v_below,top -
-    v_above,bot, sigma = penalty * kappa / min(dz_above, dz_below) (reading R3)."""
+    v_above,bot, sigma = penalty * kappa / min(dz_above, dz_below) (the penalty is a reading)."""
     ncol, twoN = Wc.shape
     N = twoN // 2
     A = np.zeros((ncol, twoN, twoN))
