@@ -91,6 +91,27 @@ __device__ __forceinline__ Tile load_tile(const DevMesh& m, int* s_off) {
   return tl;
 }
 
+// Column sum returned in FP64.  FP64 form: plain FP64 accumulation.  Mixed form:
+// compensated FP32 accumulation (TwoSum of every addition, the error terms summed
+// separately), whose result carries about 48 bits, converted to FP64 once; this
+// keeps the FP64-accurate depth integration off GB300's narrow FP64 pipe.
+template <typename R> struct ColSum;
+template <> struct ColSum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct ColSum<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = hi + x;
+    const float bp = t - hi;
+    lo += (hi - (t - bp)) + (x - bp);
+    hi = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // reciprocal: fast approximate for the FP32 form, exact division in FP64
 template <typename R> __device__ __forceinline__ R rcp(R x);
 template <> __device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.0f, x); }

@@ -20,6 +20,8 @@ struct SplitBufs {
   double *Ae, *AU, *AV, *Be, *BU, *BV, *Ce, *CU, *CV;
   double *S3x, *S3y, *Sqx, *Sqy, *Gb, *F2x, *F2y, *eta_half, *cw, *icw, *iw6;
   float *cw_f, *icw_f;
+  void *Ae_r, *AU_r, *AV_r, *Be_r, *BU_r, *BV_r, *Ce_r, *CU_r, *CV_r;  // compute-type shadows
+  void *S3x_r, *S3y_r;
   double *Qbx, *Qby;  // the state's time-averaged transport buffers
   // compute-type copies for the 3D kernels
   void *F2x_r, *F2y_r, *Dqx_r, *Dqy_r, *gcor_r, *st_half, *st_end;
@@ -47,8 +49,11 @@ cudaError_t set_smem2(KernelT kern, size_t bytes) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-struct PhysParams {
-  double g, rho0, f, alpha, beta, T0, S0, nu_h, kappa_h, nu_v, kappa_v, cd, pen_v, pen_h;
+// physical parameters converted once on the host to the compute type
+template <typename R>
+struct PP {
+  R g, rho0, irho0, f, alpha, beta, T0, S0, nu_h, kappa_h, nu_v, kappa_v, cd, pen_v, pen_h;
+  double g_d;  // the 2D mode's gravity (FP64 state update)
 };
 
 // rest depth of interface k of vertex column i (0 at the surface)
@@ -95,7 +100,7 @@ __global__ void k_wave_speed(DevMesh m, double g, double* __restrict__ cw, doubl
 template <typename R, int TP>
 __global__ void __launch_bounds__(TP, (MB<R, TP>::value))
     k_hpg(DevMesh m, const R* __restrict__ T, const R* __restrict__ S, const R* __restrict__ st,
-          PhysParams pp, R* __restrict__ Rx, R* __restrict__ Ry) {
+          PP<R> pp, R* __restrict__ Rx, R* __restrict__ Ry) {
   extern __shared__ __align__(16) unsigned char smem[];
   int* s_off = reinterpret_cast<int*>(smem);
   const int TPX = TP + m.max_tile_tris;
@@ -103,8 +108,8 @@ __global__ void __launch_bounds__(TP, (MB<R, TP>::value))
   const Tile tl = tile_of_block(m);
   const int i = threadIdx.x;
   const int nt = m.n_tri, P = m.P;
-  const R rho0 = (R)pp.rho0, al = (R)pp.alpha, be = (R)pp.beta, T0 = (R)pp.T0, S0 = (R)pp.S0;
-  const R g = (R)pp.g;
+  const R rho0 = pp.rho0, al = pp.alpha, be = pp.beta, T0 = pp.T0, S0 = pp.S0;
+  const R g = pp.g;
   auto rho = [&](R Tv, R Sv) { return rho0 * (-al * (Tv - T0) + be * (Sv - S0)); };
   R r[2][3];
   if (i < tl.np) {
@@ -296,13 +301,13 @@ __device__ __forceinline__ void momentum_extras(const DevMesh& m, int t, int k, 
                                                 const Own2<R>& own, const R* __restrict__ U,
                                                 const R* __restrict__ V, const R* __restrict__ st,
                                                 const R* __restrict__ Rx, const R* __restrict__ Ry,
-                                                const PhysParams& pp, R Fx[2][3], R Fy[2][3]) {
+                                                const PP<R>& pp, R Fx[2][3], R Fy[2][3]) {
   const int nt = m.n_tri, P = m.P;
-  if (pp.nu_h > 0.0) {
-    prism_sipg<R>(m, t, k, N, own.u, U, st, (R)pp.nu_h, (R)pp.pen_h, Fx);
-    prism_sipg<R>(m, t, k, N, own.v, V, st, (R)pp.nu_h, (R)pp.pen_h, Fy);
+  if (pp.nu_h > (R)0) {
+    prism_sipg<R>(m, t, k, N, own.u, U, st, pp.nu_h, pp.pen_h, Fx);
+    prism_sipg<R>(m, t, k, N, own.v, V, st, pp.nu_h, pp.pen_h, Fy);
   }
-  const R f = (R)pp.f, irho = (R)(1.0 / pp.rho0);
+  const R f = pp.f, irho = pp.irho0;
   const R w6 = Geo<R>::jh(m, t) * (R)(1.0 / 6.0);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -322,8 +327,8 @@ __device__ __forceinline__ void momentum_extras(const DevMesh& m, int t, int k, 
     if (k == N - 1) {
       const R ub = own.u[1][a], vb = own.v[1][a];
       const R sp = sqrt(ub * ub + vb * vb);
-      Fx[1][a] -= (R)pp.cd * w6 * sp * ub;
-      Fy[1][a] -= (R)pp.cd * w6 * sp * vb;
+      Fx[1][a] -= pp.cd * w6 * sp * ub;
+      Fy[1][a] -= pp.cd * w6 * sp * vb;
     }
   }
 }
@@ -334,8 +339,9 @@ __device__ __forceinline__ void momentum_extras(const DevMesh& m, int t, int k, 
 template <typename R, int TP>
 __global__ void __launch_bounds__(TP, (MB<R, TP>::value))
     k_mompred(DevMesh m, AdvIn<R> in, const R* __restrict__ Rx, const R* __restrict__ Ry,
-              PhysParams pp, double* __restrict__ S3x, double* __restrict__ S3y,
-              double* __restrict__ Sqx, double* __restrict__ Sqy) {
+              PP<R> pp, double* __restrict__ S3x, double* __restrict__ S3y,
+              double* __restrict__ Sqx, double* __restrict__ Sqy, R* __restrict__ S3x_r,
+              R* __restrict__ S3y_r) {
   extern __shared__ __align__(16) unsigned char smem[];
   int* s_off = reinterpret_cast<int*>(smem);
   const int TPX = TP + m.max_tile_tris;
@@ -367,9 +373,13 @@ __global__ void __launch_bounds__(TP, (MB<R, TP>::value))
     const int a = rem / tl.nt, lt = rem - a * tl.nt;
     const int base = s_off[lt] + lt, N = s_off[lt + 1] - s_off[lt];
     const R* src = s_v + (q * 3 + a) * TPX + base;
-    double s = 0.0;
-    for (int k = 0; k < N; ++k) s += (double)src[k];
-    outs[q][a * m.n_tri + tl.t0 + lt] = s;
+    ColSum<R> cs;
+    for (int k = 0; k < N; ++k) cs.add(src[k]);
+    const double v = cs.value();
+    const int ia = a * m.n_tri + tl.t0 + lt;
+    outs[q][ia] = v;
+    if (q == 0) S3x_r[ia] = (R)v;
+    if (q == 1) S3y_r[ia] = (R)v;
   }
 }
 
@@ -394,24 +404,32 @@ template <> struct Ext2dGeo<float> {
   static __device__ __forceinline__ float ic(const SplitBufs& b, int i) { return b.icw_f[i]; }
 };
 
+// Stage buffers: FP64 state for the update plus its compute-type shadow for the
+// residual (the same arrays in the FP64 form).
+struct Ext2dIO {
+  const double *e, *U, *V;      // stage input (FP64)
+  const void *er, *Ur, *Vr;     // stage input shadow (RC)
+  const double *en, *Un, *Vn;   // subcycle start (FP64)
+  double *eo, *Uo, *Vo;         // stage output (FP64)
+  void *eor, *Uor, *Vor;        // stage output shadow (RC); null in the FP64 form
+};
+
 template <int MODE, typename RC>
 __global__ void __launch_bounds__(256)
-    k_ext2d(DevMesh m, SplitBufs bf, const double* __restrict__ es, const double* __restrict__ Us,
-            const double* __restrict__ Vs, const double* __restrict__ en, const double* __restrict__ Un,
-            const double* __restrict__ Vn, double g_, double tide_, double alpha, double beta,
-            double dt, double bw, double* __restrict__ eo, double* __restrict__ Uo,
-            double* __restrict__ Vo) {
+    k_ext2d(DevMesh m, SplitBufs bf, Ext2dIO io, double g_, double tide_, double alpha, double beta,
+            double dt, double bw) {
   const int nt = m.n_tri;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
+  const RC* er = (const RC*)io.er;
+  const RC* Ur = (const RC*)io.Ur;
+  const RC* Vr = (const RC*)io.Vr;
   const RC g = (RC)g_, tide = (RC)tide_;
   RC e[3], U[3], V[3], H[3], gx[3], gy[3];
-  double Ud[3], Vd[3], ed_[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int ia = a * nt + t;
-    ed_[a] = es[ia]; Ud[a] = Us[ia]; Vd[a] = Vs[ia];
-    e[a] = (RC)ed_[a]; U[a] = (RC)Ud[a]; V[a] = (RC)Vd[a];
+    e[a] = er[ia]; U[a] = Ur[ia]; V[a] = Vr[ia];
     H[a] = Geo<RC>::h(m, ia) + e[a];
     gx[a] = Geo<RC>::gx(m, ia); gy[a] = Geo<RC>::gy(m, ia);
   }
@@ -440,9 +458,9 @@ __global__ void __launch_bounds__(256)
     if (ei.x >= 0) {
       const int l0 = ei.w & 3, l1 = (ei.w >> 2) & 3;
       const int i0 = l0 * nt + ei.x, i1 = l1 * nt + ei.x;
-      en0 = (RC)es[i0]; en1 = (RC)es[i1];
-      qn0 = (RC)Us[i0] * nx + (RC)Vs[i0] * ny;
-      qn1 = (RC)Us[i1] * nx + (RC)Vs[i1] * ny;
+      en0 = er[i0]; en1 = er[i1];
+      qn0 = Ur[i0] * nx + Vr[i0] * ny;
+      qn1 = Ur[i1] * nx + Vr[i1] * ny;
     }
     const RC qo0 = U[a0] * nx + V[a0] * ny, qo1 = U[a1] * nx + V[a1] * ny;
 #pragma unroll
@@ -476,21 +494,33 @@ __global__ void __launch_bounds__(256)
   if (MODE == 1) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      eo[a * nt + t] = (double)Re[a];
-      eo[(3 + a) * nt + t] = (double)RU[a];
-      eo[(6 + a) * nt + t] = (double)RV[a];
+      io.eo[a * nt + t] = (double)Re[a];
+      io.eo[(3 + a) * nt + t] = (double)RU[a];
+      io.eo[(6 + a) * nt + t] = (double)RV[a];
     }
     return;
   }
-  const double iw = bf.iw6[t];
+  // new = alpha start + beta stage + (beta dt / w) R, the increment in RC
+  const RC bdw = (RC)(beta * dt) * (RC)bf.iw6[t];
+  const RC* S3x = (const RC*)bf.S3x_r;
+  const RC* S3y = (const RC*)bf.S3y_r;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int ia = a * nt + t;
-    bf.Qbx[ia] += bw * Ud[a];
-    bf.Qby[ia] += bw * Vd[a];
-    eo[ia] = alpha * en[ia] + beta * (ed_[a] + dt * (double)Re[a] * iw);
-    Uo[ia] = alpha * Un[ia] + beta * (Ud[a] + dt * ((double)RU[a] + bf.S3x[ia]) * iw);
-    Vo[ia] = alpha * Vn[ia] + beta * (Vd[a] + dt * ((double)RV[a] + bf.S3y[ia]) * iw);
+    const double es_ = io.e[ia], Us_ = io.U[ia], Vs_ = io.V[ia];
+    bf.Qbx[ia] += bw * Us_;
+    bf.Qby[ia] += bw * Vs_;
+    const double e_new = alpha * io.en[ia] + beta * es_ + (double)(bdw * Re[a]);
+    const double U_new = alpha * io.Un[ia] + beta * Us_ + (double)(bdw * (RU[a] + S3x[ia]));
+    const double V_new = alpha * io.Vn[ia] + beta * Vs_ + (double)(bdw * (RV[a] + S3y[ia]));
+    io.eo[ia] = e_new;
+    io.Uo[ia] = U_new;
+    io.Vo[ia] = V_new;
+    if (io.eor) {
+      ((RC*)io.eor)[ia] = (RC)e_new;
+      ((RC*)io.Uor)[ia] = (RC)U_new;
+      ((RC*)io.Vor)[ia] = (RC)V_new;
+    }
   }
 }
 
@@ -619,10 +649,11 @@ __global__ void __launch_bounds__(TP, (MB<R, TP>::value))
 //   M1 f1 = M0 f0 + dt (R_h(f_ev; qbar) + extras [+ M1 F2D/H1] [+ A f_ev]),
 // implicit: (M1 - dt A(W, st1)) f1 = ... without A f_ev.
 // ---------------------------------------------------------------------------
-struct UpdArgs {
-  double dt;
-  double kap_v;  // vertical viscosity / diffusivity
-  double kap_h;  // horizontal viscosity / diffusivity
+template <typename R>
+struct UA {
+  R dt;
+  R kap_v;  // vertical viscosity / diffusivity
+  R kap_h;  // horizontal viscosity / diffusivity
 };
 
 template <typename R, int TP, int KIND, bool IMPL>
@@ -630,7 +661,7 @@ __global__ void __launch_bounds__(TP, (MB<R, TP>::value))
     k_update(DevMesh m, AdvIn<R> in, const R* __restrict__ G0, const R* __restrict__ G1,
              const R* __restrict__ W, const R* __restrict__ Rx, const R* __restrict__ Ry,
              const R* __restrict__ F2x, const R* __restrict__ F2y, const R* __restrict__ st0,
-             const R* __restrict__ st1, PhysParams pp, UpdArgs ua, R* O0, R* O1,
+             const R* __restrict__ st1, PP<R> pp, UA<R> ua, R* O0, R* O1,
              int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem[];
   int* s_off = reinterpret_cast<int*>(smem);
@@ -652,7 +683,7 @@ __global__ void __launch_bounds__(TP, (MB<R, TP>::value))
     }
   }
   load_offsets<TP>(m, tl, s_off);
-  const R dt = (R)ua.dt;
+  const R dt = ua.dt;
   int slot = 0;
   R o0[2][3], o1[2][3];
   if (i < tl.np) {
@@ -665,9 +696,9 @@ __global__ void __launch_bounds__(TP, (MB<R, TP>::value))
     const R w6 = Geo<R>::jh(m, t) * (R)(1.0 / 6.0);
     if (KIND == 0) {
       momentum_extras<R>(m, t, k, p, N, own, in.U, in.V, in.st, Rx, Ry, pp, F0, F1);
-    } else if (ua.kap_h > 0.0) {
-      prism_sipg<R>(m, t, k, N, own.f0, in.F0, in.st, (R)ua.kap_h, (R)pp.pen_h, F0);
-      prism_sipg<R>(m, t, k, N, own.f1, in.F1, in.st, (R)ua.kap_h, (R)pp.pen_h, F1);
+    } else if (ua.kap_h > (R)0) {
+      prism_sipg<R>(m, t, k, N, own.f0, in.F0, in.st, ua.kap_h, pp.pen_h, F0);
+      prism_sipg<R>(m, t, k, N, own.f1, in.F1, in.st, ua.kap_h, pp.pen_h, F1);
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -693,7 +724,7 @@ __global__ void __launch_bounds__(TP, (MB<R, TP>::value))
         s_b[(3 * 3 + a) * TPX + slot] = r11;
       } else {
         // + dt A(W, st_ev) f_ev, A couples the layers above and below
-        const R kap = (R)ua.kap_v, pen = (R)pp.pen_v;
+        const R kap = ua.kap_v, pen = pp.pen_v;
         const R stv = in.st[ia];
         const R dz = dr * stv, idz = rcp<R>(dz);
         R idzm = idz, idzp = idz;
@@ -742,7 +773,7 @@ __global__ void __launch_bounds__(TP, (MB<R, TP>::value))
                         s_W + (3 + a) * TPX + base, s_b + (0 * 3 + a) * TPX + base,
                         s_b + (1 * 3 + a) * TPX + base, s_b + (2 * 3 + a) * TPX + base,
                         s_b + (3 * 3 + a) * TPX + base, C, C + TPX, C + 2 * TPX, C + 3 * TPX,
-                        (R)ua.kap_v, (R)pp.pen_v, dt);
+                        ua.kap_v, pp.pen_v, dt);
     }
     __syncthreads();
     if (i < tl.np) {
@@ -778,11 +809,13 @@ size_t update_smem(const DevMesh& m, int TP, size_t esz) {
          (size_t)3 * TP * esz;
 }
 
-PhysParams phys(const slim_params& p) {
-  PhysParams q;
-  q.g = p.g; q.rho0 = p.rho0; q.f = p.coriolis_f; q.alpha = p.eos_alpha; q.beta = p.eos_beta;
-  q.T0 = p.eos_T0; q.S0 = p.eos_S0; q.nu_h = p.nu_h; q.kappa_h = p.kappa_h; q.nu_v = p.nu_v;
-  q.kappa_v = p.kappa_v; q.cd = p.drag_cd; q.pen_v = p.penalty_v; q.pen_h = p.penalty_h;
+template <typename R>
+PP<R> phys(const slim_params& p) {
+  PP<R> q;
+  q.g = (R)p.g; q.rho0 = (R)p.rho0; q.irho0 = (R)(1.0 / p.rho0); q.f = (R)p.coriolis_f;
+  q.alpha = (R)p.eos_alpha; q.beta = (R)p.eos_beta; q.T0 = (R)p.eos_T0; q.S0 = (R)p.eos_S0;
+  q.nu_h = (R)p.nu_h; q.kappa_h = (R)p.kappa_h; q.nu_v = (R)p.nu_v; q.kappa_v = (R)p.kappa_v;
+  q.cd = (R)p.drag_cd; q.pen_v = (R)p.penalty_v; q.pen_h = (R)p.penalty_h; q.g_d = p.g;
   return q;
 }
 
@@ -797,7 +830,7 @@ PhysParams phys(const slim_params& p) {
 
 template <typename R>
 cudaError_t launch_hpg(const DevMesh& m, int TP, const R* T, const R* S, const R* st,
-                       const PhysParams& pp, R* Rx, R* Ry, cudaStream_t s) {
+                       const PP<R>& pp, R* Rx, R* Ry, cudaStream_t s) {
   SLIM_TP_SWITCH2(TP, {
     const size_t sm = tile_smem(m, TPc, sizeof(R), 12);
     cudaError_t e = set_smem2(k_hpg<R, TPc>, sm);
@@ -809,12 +842,13 @@ cudaError_t launch_hpg(const DevMesh& m, int TP, const R* T, const R* S, const R
 
 template <typename R>
 cudaError_t launch_mompred(const DevMesh& m, int TP, const AdvIn<R>& in, const R* Rx, const R* Ry,
-                           const PhysParams& pp, SplitBufs* b, cudaStream_t s) {
+                           const PP<R>& pp, SplitBufs* b, cudaStream_t s) {
   SLIM_TP_SWITCH2(TP, {
     const size_t sm = tile_smem(m, TPc, sizeof(R), 12);
     cudaError_t e = set_smem2(k_mompred<R, TPc>, sm);
     if (e != cudaSuccess) return e;
-    k_mompred<R, TPc><<<m.n_tiles, TPc, sm, s>>>(m, in, Rx, Ry, pp, b->S3x, b->S3y, b->Sqx, b->Sqy);
+    k_mompred<R, TPc><<<m.n_tiles, TPc, sm, s>>>(m, in, Rx, Ry, pp, b->S3x, b->S3y, b->Sqx, b->Sqy,
+                                                 (R*)b->S3x_r, (R*)b->S3y_r);
   });
   return cudaGetLastError();
 }
@@ -834,7 +868,7 @@ cudaError_t launch_cont_split(const DevMesh& m, int TP, const AdvIn<R>& in, cons
 template <typename R, int KIND, bool IMPL>
 cudaError_t launch_update(const DevMesh& m, int TP, const AdvIn<R>& in, const R* G0, const R* G1,
                           const R* W, const R* Rx, const R* Ry, const R* F2x, const R* F2y,
-                          const R* st0, const R* st1, const PhysParams& pp, const UpdArgs& ua,
+                          const R* st0, const R* st1, const PP<R>& pp, const UA<R>& ua,
                           R* O0, R* O1, int* err, cudaStream_t s) {
   SLIM_TP_SWITCH2(TP, {
     const size_t sm = update_smem(m, TPc, sizeof(R));
@@ -856,7 +890,7 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, bool implicit,
   const DevMesh& m = s->mesh->d;
   SplitBufs* b = s->sp;
   const int TP = s->mesh->tile_prisms;
-  const PhysParams pp = phys(s->par);
+  const PP<R> pp = phys<R>(s->par);
   const int nt = m.n_tri;
   const size_t n2 = (size_t)3 * nt;
   R* Rx = (R*)s->Rx;
@@ -875,6 +909,12 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, bool implicit,
   SLIM_CU(cudaMemcpyAsync(b->Ae, s->eta, n2 * 8, cudaMemcpyDeviceToDevice, stm));
   SLIM_CU(cudaMemcpyAsync(b->AU, s->Qx, n2 * 8, cudaMemcpyDeviceToDevice, stm));
   SLIM_CU(cudaMemcpyAsync(b->AV, s->Qy, n2 * 8, cudaMemcpyDeviceToDevice, stm));
+  const bool shadow = sizeof(R) != 8;
+  if (shadow) {
+    SLIM_CU(launch_convert_d2f(b->Ae, (float*)b->Ae_r, n2, stm));
+    SLIM_CU(launch_convert_d2f(b->AU, (float*)b->AU_r, n2, stm));
+    SLIM_CU(launch_convert_d2f(b->AV, (float*)b->AV_r, n2, stm));
+  }
   SLIM_CU(cudaMemsetAsync(s->Qbx, 0, n2 * 8, stm));
   SLIM_CU(cudaMemsetAsync(s->Qby, 0, n2 * 8, stm));
   SLIM_CU(cudaMemsetAsync(b->Gb, 0, n2 * 2 * 8, stm));
@@ -882,21 +922,28 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, bool implicit,
   const double A_[3] = {0.0, 0.75, 1.0 / 3.0}, B_[3] = {1.0, 0.25, 2.0 / 3.0};
   const double bw_[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0}, ts_[3] = {0.0, 1.0, 0.5};
   const int blk = 256, grd = (nt + blk - 1) / blk;
+  double* F[3][3] = {{b->Ae, b->AU, b->AV}, {b->Be, b->BU, b->BV}, {b->Ce, b->CU, b->CV}};
+  void* Fr[3][3] = {{b->Ae_r, b->AU_r, b->AV_r}, {b->Be_r, b->BU_r, b->BV_r}, {b->Ce_r, b->CU_r, b->CV_r}};
   for (int q = 0; q < n_sub; ++q) {
-    double* ins[3][3] = {{b->Ae, b->AU, b->AV}, {b->Be, b->BU, b->BV}, {b->Ce, b->CU, b->CV}};
-    double* outs[3][3] = {{b->Be, b->BU, b->BV}, {b->Ce, b->CU, b->CV}, {b->Ae, b->AU, b->AV}};
     for (int st = 0; st < 3; ++st) {
+      const int si = st, so = (st + 1) % 3;  // A -> B -> C -> A
       const double time = t0 + (q + ts_[st]) * dts;
       const double tide = s->par.tide_amp * std::cos(2.0 * M_PI * time / s->par.tide_period);
+      Ext2dIO io;
+      io.e = F[si][0]; io.U = F[si][1]; io.V = F[si][2];
+      io.er = shadow ? Fr[si][0] : F[si][0];
+      io.Ur = shadow ? Fr[si][1] : F[si][1];
+      io.Vr = shadow ? Fr[si][2] : F[si][2];
+      io.en = b->Ae; io.Un = b->AU; io.Vn = b->AV;
+      io.eo = F[so][0]; io.Uo = F[so][1]; io.Vo = F[so][2];
+      io.eor = shadow ? Fr[so][0] : nullptr;
+      io.Uor = shadow ? Fr[so][1] : nullptr;
+      io.Vor = shadow ? Fr[so][2] : nullptr;
       ProfScope ps(s, SLIM_PHASE_EXT2D, stm);
       if (sizeof(R) == 8)
-        k_ext2d<0, double><<<grd, blk, 0, stm>>>(m, *b, ins[st][0], ins[st][1], ins[st][2], b->Ae, b->AU,
-                                                 b->AV, s->par.g, tide, A_[st], B_[st], dts,
-                                                 bw_[st] / n_sub, outs[st][0], outs[st][1], outs[st][2]);
+        k_ext2d<0, double><<<grd, blk, 0, stm>>>(m, *b, io, s->par.g, tide, A_[st], B_[st], dts, bw_[st] / n_sub);
       else
-        k_ext2d<0, float><<<grd, blk, 0, stm>>>(m, *b, ins[st][0], ins[st][1], ins[st][2], b->Ae, b->AU,
-                                                b->AV, s->par.g, tide, A_[st], B_[st], dts,
-                                                bw_[st] / n_sub, outs[st][0], outs[st][1], outs[st][2]);
+        k_ext2d<0, float><<<grd, blk, 0, stm>>>(m, *b, io, s->par.g, tide, A_[st], B_[st], dts, bw_[st] / n_sub);
       SLIM_CU(cudaGetLastError());
     }
   }
@@ -916,8 +963,8 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, bool implicit,
   }
   const R* st0 = (const R*)s->st_cur;
   const R* st1 = (const R*)b->st_end;
-  UpdArgs um{dt, s->par.nu_v, s->par.nu_h};
-  UpdArgs ut{dt, s->par.kappa_v, s->par.kappa_h};
+  UA<R> um{(R)dt, (R)s->par.nu_v, (R)s->par.nu_h};
+  UA<R> ut{(R)dt, (R)s->par.kappa_v, (R)s->par.kappa_h};
   AdvIn<R> tin{u_ev, v_ev, T_ev, S_ev, (const R*)s->Text, (const R*)s->Sext, st_ev,
                (const R*)b->Dqx_r, (const R*)b->Dqy_r, (const R*)b->gcor_r};
   const R* U0 = (const R*)s->U;
@@ -995,7 +1042,9 @@ slim_status split_alloc(slim_state* s) {
     SLIM_CU(cudaMemset(*p, 0, n2 * 2 * 8));
     s->allocs.push_back(*p);
   }
-  void** r2[] = {&b->F2x_r, &b->F2y_r, &b->Dqx_r, &b->Dqy_r, &b->st_half, &b->st_end};
+  void** r2[] = {&b->F2x_r, &b->F2y_r, &b->Dqx_r, &b->Dqy_r, &b->st_half, &b->st_end,
+                 &b->Ae_r, &b->AU_r, &b->AV_r, &b->Be_r, &b->BU_r, &b->BV_r, &b->Ce_r, &b->CU_r,
+                 &b->CV_r, &b->S3x_r, &b->S3y_r};
   for (void** p : r2) {
     SLIM_CU(cudaMalloc(p, n2 * s->esz));
     SLIM_CU(cudaMemset(*p, 0, n2 * s->esz));
@@ -1037,13 +1086,14 @@ void* split_field(slim_state* s, int field) {
 
 slim_status split_hpg(slim_state* s, cudaStream_t st) {
   const DevMesh& m = s->mesh->d;
-  const PhysParams pp = phys(s->par);
   if (s->prec == SLIM_FP64)
     SLIM_CU(launch_hpg<double>(m, s->mesh->tile_prisms, (const double*)s->T, (const double*)s->S,
-                               (const double*)s->st_cur, pp, (double*)s->Rx, (double*)s->Ry, st));
+                               (const double*)s->st_cur, phys<double>(s->par), (double*)s->Rx,
+                               (double*)s->Ry, st));
   else
     SLIM_CU(launch_hpg<float>(m, s->mesh->tile_prisms, (const float*)s->T, (const float*)s->S,
-                              (const float*)s->st_cur, pp, (float*)s->Rx, (float*)s->Ry, st));
+                              (const float*)s->st_cur, phys<float>(s->par), (float*)s->Rx,
+                              (float*)s->Ry, st));
   return SLIM_OK;
 }
 
@@ -1053,12 +1103,20 @@ slim_status split_rhs2d(slim_state* s, double t, double* out, cudaStream_t st) {
   SplitBufs* b = s->sp;
   const double tide = s->par.tide_amp * std::cos(2.0 * M_PI * t / s->par.tide_period);
   const int grd = (m.n_tri + 255) / 256;
-  if (s->prec == SLIM_FP64)
-    k_ext2d<1, double><<<grd, 256, 0, st>>>(m, *b, s->eta, s->Qx, s->Qy, nullptr, nullptr, nullptr,
-                                            s->par.g, tide, 0.0, 0.0, 0.0, 0.0, out, nullptr, nullptr);
-  else
-    k_ext2d<1, float><<<grd, 256, 0, st>>>(m, *b, s->eta, s->Qx, s->Qy, nullptr, nullptr, nullptr,
-                                           s->par.g, tide, 0.0, 0.0, 0.0, 0.0, out, nullptr, nullptr);
+  Ext2dIO io{};
+  io.e = s->eta; io.U = s->Qx; io.V = s->Qy;
+  io.eo = out;
+  if (s->prec == SLIM_FP64) {
+    io.er = s->eta; io.Ur = s->Qx; io.Vr = s->Qy;
+    k_ext2d<1, double><<<grd, 256, 0, st>>>(m, *b, io, s->par.g, tide, 0.0, 0.0, 0.0, 0.0);
+  } else {
+    const size_t n2 = (size_t)3 * m.n_tri;
+    SLIM_CU(launch_convert_d2f(s->eta, (float*)b->Ae_r, n2, st));
+    SLIM_CU(launch_convert_d2f(s->Qx, (float*)b->AU_r, n2, st));
+    SLIM_CU(launch_convert_d2f(s->Qy, (float*)b->AV_r, n2, st));
+    io.er = b->Ae_r; io.Ur = b->AU_r; io.Vr = b->AV_r;
+    k_ext2d<1, float><<<grd, 256, 0, st>>>(m, *b, io, s->par.g, tide, 0.0, 0.0, 0.0, 0.0);
+  }
   SLIM_CU(cudaGetLastError());
   return SLIM_OK;
 }

@@ -85,10 +85,11 @@ __global__ void __launch_bounds__(TP, (MinBlocks<R, TP>::value))
     const int t = tl.t0 + lt, base = s_off[lt] + lt, N = s_off[lt + 1] - s_off[lt];
     R* Ft = s_F + a * TPX + base;
     R* Fb = s_F + (3 + a) * TPX + base;
-    // FP64 column sum (each layer's two node values are added in the compute type
-    // first: that rounding is of the order of the inputs' own)
-    double D = 0.0;
-    for (int k = 0; k < N; ++k) D += (double)(Ft[k] + Fb[k]);
+    // depth integration in FP64 accuracy (each layer's two node values are added
+    // in the compute type first: that rounding is of the order of the inputs' own)
+    ColSum<R> cs;
+    for (int k = 0; k < N; ++k) cs.add(Ft[k] + Fb[k]);
+    const double D = cs.value();
     const int ia = a * nt + t;
     if (DIV_ONLY) {
       eta_out[ia] = D;
