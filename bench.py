@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -170,9 +171,16 @@ def run_ours(args, rank: int, world: int):
     sh = stream.cuda_stream
     res = {}
     clocks = None
+    tuned = {}
     for pname in precs:
         prec = slim.SLIM_MIXED if pname == "mixed" else slim.SLIM_FP64
         par = slim.slim_params_default(**over)
+        if not args.no_tune:
+            from paper_2605_16082_gb300 import autotune
+            tn = autotune.autotune(m, prec, par, fields, dt, use_cache=False)
+            par.tile_prisms = tn["tile_prisms"]
+            par.blocks_per_sm = tn["blocks_per_sm"]
+            tuned[pname] = tn
         mod = slim.Model(m, prec, par)
         for k, v in fields.items():
             mod.upload(k, v)
@@ -185,7 +193,6 @@ def run_ours(args, rank: int, world: int):
         if sampler:
             sampler.start()
         n_k = slim.slim_step_kernel_count(mod.state)
-        slim.slim_profile_begin(mod.state, n_k * args.steps + 8)
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         barrier(world)
@@ -196,6 +203,12 @@ def run_ours(args, rank: int, world: int):
         torch.cuda.synchronize()
         barrier(world)
         ms = e0.elapsed_time(e1)
+        # per-kernel durations: the same K steps again with an event pair around
+        # every kernel (launched individually while profiling)
+        slim.slim_profile_begin(mod.state, n_k * args.steps + 8)
+        for _ in range(args.steps):
+            slim.slim_step(mod.state, t, dt, sh); t += dt
+        torch.cuda.synchronize()
         phases = slim.slim_profile_end(mod.state)
         if sampler:
             clocks = sampler.stop()
@@ -207,7 +220,9 @@ def run_ours(args, rank: int, world: int):
         esz = 8 if pname == "fp64" else 4
         ab = phase_bytes(dom, m, esz, W.get("n_sub", 0))
         r = dict(value=world * dofs / (ms_step / 1e3), ms_per_step=ms_step, phases=phases,
-                 dominant=dom, dom_ms=dom_ms, alg_bytes=ab, gpu_launches=n_k * args.steps)
+                 dominant=dom, dom_ms=dom_ms, alg_bytes=ab, gpu_launches=n_k * args.steps,
+                 tile_prisms=par.tile_prisms, blocks_per_sm=par.blocks_per_sm,
+                 autotune=tuned.get(pname, {}).get("all"))
         # end to end through the public API with pinned host buffers
         if not args.no_e2e:
             pin = {k: torch.tensor(v, dtype=torch.float64).pin_memory() for k, v in fields.items()}
@@ -354,13 +369,16 @@ def main():
                 warmup=args.warmup, ms_per_step=head["ms_per_step"], higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f32+f64" if hname == "mixed" else "f64",
                 data="synthetic", config=cfg, roofline=roof(head), clocks=clocks,
-                gpu_launches=head["gpu_launches"], phases_ms={k: v[0] for k, v in head["phases"].items()})
+                gpu_launches=head["gpu_launches"], phases_ms={k: v[0] for k, v in head["phases"].items()},
+                tiling=dict(prisms_per_block=head["tile_prisms"], blocks_per_sm=head["blocks_per_sm"],
+                            autotune_ms=head["autotune"]), cuda_graph=True)
     if "e2e" in head:
         line["e2e"] = head["e2e"]
     if "fp64" in res and hname != "fp64":
         f = res["fp64"]
         line["fp64"] = dict(value=f["value"], ms_per_step=f["ms_per_step"], roofline=roof(f),
-                            e2e=f.get("e2e"), phases_ms={k: v[0] for k, v in f["phases"].items()})
+                            e2e=f.get("e2e"), phases_ms={k: v[0] for k, v in f["phases"].items()},
+                            tiling=dict(prisms_per_block=f["tile_prisms"], blocks_per_sm=f["blocks_per_sm"]))
     if not args.no_cpu:
         line["cpu_baseline"] = oracle_sample(args, m, args.cpu_seconds)
     print(json.dumps(line))

@@ -112,12 +112,19 @@ typedef struct slim_params {
   int n_sub;           /* external-mode steps per internal step (split)    */
   int tile_prisms;     /* prisms per thread block (0 = default 256)        */
   int check_every;     /* slim_step checks the device error flag every n steps (0 = never) */
+  int blocks_per_sm;   /* register budget of the heavy split kernels: 2 or 4 resident
+                          blocks of 256 threads per SM (0 = default 4)            */
+  int use_graph;       /* 1: slim_step replays one CUDA graph of the whole step (captured
+                          on the first call and again whenever dt changes; only the
+                          step's start time is updated between replays); 0: launches
+                          every kernel.  Profiling (slim_profile_begin) uses launches. */
 } slim_params;
 
 /* Fill *p with the defaults: g 9.81, rho0 1025, f 1e-4, alpha 2e-4, beta 7.6e-4,
    T0 10, S0 35, kappa_v = nu_v = 1e-3, kappa_h = nu_h = 0, Cd 2.5e-3, no boundary
    fluxes, penalty_v 4, penalty_h 6, tide 1 m / 44712 s, SLIM_SCHEME_TRACER,
-   n_sub 20, tile 256, check_every 0.  Returns SLIM_ERR_ARG for a null pointer. */
+   n_sub 20, tile 256, check_every 0, blocks_per_sm 0, use_graph 1.  Returns
+   SLIM_ERR_ARG for a null pointer. */
 slim_status slim_params_default(slim_params* p);
 
 const char* slim_status_string(slim_status s);

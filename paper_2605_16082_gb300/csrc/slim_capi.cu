@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "slim_internal.h"
 #include "slim_kernels.h"
@@ -35,6 +36,8 @@ extern "C" slim_status slim_params_default(slim_params* p) {
   p->n_sub = 20;
   p->tile_prisms = 256;
   p->check_every = 0;
+  p->blocks_per_sm = 0;
+  p->use_graph = 1;
   return SLIM_OK;
 }
 
@@ -71,8 +74,18 @@ slim_status dev_alloc(slim_state* s, void** p, size_t bytes) {
   return SLIM_OK;
 }
 
+void drop_graph(slim_state* s) {
+  if (s->g_exec) cudaGraphExecDestroy(s->g_exec);
+  s->g_exec = nullptr;
+  s->g_time_node = nullptr;
+}
+
 void free_state(slim_state* s) {
   if (!s) return;
+  drop_graph(s);
+  if (s->g_in) cudaEventDestroy(s->g_in);
+  if (s->g_out) cudaEventDestroy(s->g_out);
+  if (s->g_stream) cudaStreamDestroy(s->g_stream);
   split_free(s);
   for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
   for (void* p : s->allocs) cudaFree(p);
@@ -240,7 +253,12 @@ extern "C" slim_status slim_state_set_params(slim_state* s, const slim_params* p
   slim_status st = check_params(par);
   if (st != SLIM_OK) return st;
   if (par->scheme != s->par.scheme) { set_error("scheme cannot change"); return SLIM_ERR_ARG; }
+  if (par->scheme == SLIM_SCHEME_SPLIT && par->n_sub != s->par.n_sub) {
+    set_error("n_sub cannot change");
+    return SLIM_ERR_ARG;
+  }
   s->par = *par;
+  drop_graph(s);
   return SLIM_OK;
 }
 
@@ -388,16 +406,89 @@ extern "C" slim_status slim_hpg(slim_state* s, void* stream) {
   return split_hpg(s, (cudaStream_t)stream);
 }
 
+namespace {
+slim_status step_launches(slim_state* s, double t, double dt, cudaStream_t st) {
+  if (s->par.scheme == SLIM_SCHEME_SPLIT) return split_step(s, t, dt, st);
+  return s->prec == SLIM_FP64 ? tracer_step<double>(s, dt, st) : tracer_step<float>(s, dt, st);
+}
+
+// Capture the whole step once into a graph on the state's own stream, locate the
+// time kernel (first argument = start time) and replay; between replays only the
+// start time of that node changes.
+slim_status step_graph(slim_state* s, double t, double dt, cudaStream_t user) {
+  if (!s->g_stream) {
+    SLIM_CUDA_TRY(cudaStreamCreateWithFlags(&s->g_stream, cudaStreamNonBlocking));
+    SLIM_CUDA_TRY(cudaEventCreateWithFlags(&s->g_in, cudaEventDisableTiming));
+    SLIM_CUDA_TRY(cudaEventCreateWithFlags(&s->g_out, cudaEventDisableTiming));
+  }
+  if (!s->g_exec || s->g_dt != dt) {
+    drop_graph(s);
+    cudaGraph_t g = nullptr;
+    SLIM_CUDA_TRY(cudaStreamBeginCapture(s->g_stream, cudaStreamCaptureModeThreadLocal));
+    slim_status r = step_launches(s, t, dt, s->g_stream);
+    cudaError_t ce = cudaStreamEndCapture(s->g_stream, &g);
+    if (r != SLIM_OK) { if (g) cudaGraphDestroy(g); return r; }
+    if (ce != cudaSuccess) { set_error(std::string("capture: ") + cudaGetErrorString(ce)); return SLIM_ERR_CUDA; }
+    ce = cudaGraphInstantiate(&s->g_exec, g, 0);
+    if (ce == cudaSuccess && s->par.scheme == SLIM_SCHEME_SPLIT) {
+      size_t n = 0;
+      cudaGraphGetNodes(g, nullptr, &n);
+      std::vector<cudaGraphNode_t> nodes(n);
+      cudaGraphGetNodes(g, nodes.data(), &n);
+      for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp{};
+        if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
+        if (kp.func == split_time_kernel()) {
+          s->g_time_node = nd;
+          s->g_time_params = kp;
+          break;
+        }
+      }
+    }
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) { set_error(std::string("instantiate: ") + cudaGetErrorString(ce)); return SLIM_ERR_CUDA; }
+    if (s->par.scheme == SLIM_SCHEME_SPLIT && !s->g_time_node) {
+      drop_graph(s);
+      set_error("time kernel not found in the captured step");
+      return SLIM_ERR_CUDA;
+    }
+    s->g_dt = dt;
+  } else if (s->g_time_node) {
+    // same arguments as captured, new start time
+    s->g_args_t = t;
+    s->g_args_dt = dt;
+    s->g_args_n = s->par.n_sub;
+    s->g_args_amp = s->par.tide_amp;
+    s->g_args_period = s->par.tide_period;
+    s->g_args_out = ((double**)s->g_time_params.kernelParams)[5];
+    void* args[6] = {&s->g_args_t, &s->g_args_dt, &s->g_args_n, &s->g_args_amp, &s->g_args_period,
+                     &s->g_args_out};
+    cudaKernelNodeParams kp = s->g_time_params;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    SLIM_CUDA_TRY(cudaGraphExecKernelNodeSetParams(s->g_exec, s->g_time_node, &kp));
+  }
+  SLIM_CUDA_TRY(cudaEventRecord(s->g_in, user));
+  SLIM_CUDA_TRY(cudaStreamWaitEvent(s->g_stream, s->g_in, 0));
+  SLIM_CUDA_TRY(cudaGraphLaunch(s->g_exec, s->g_stream));
+  SLIM_CUDA_TRY(cudaEventRecord(s->g_out, s->g_stream));
+  SLIM_CUDA_TRY(cudaStreamWaitEvent(user, s->g_out, 0));
+  return SLIM_OK;
+}
+}  // namespace
+
 extern "C" slim_status slim_step(slim_state* s, double t, double dt, void* stream) {
   clear_error();
   if (!s) { set_error("state is null"); return SLIM_ERR_ARG; }
   if (!(dt > 0)) { set_error("dt must be positive"); return SLIM_ERR_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
   slim_status r;
-  if (s->par.scheme == SLIM_SCHEME_SPLIT)
-    r = split_step(s, t, dt, st);
+  if (s->par.use_graph && !s->prof_on)
+    r = step_graph(s, t, dt, st);
   else
-    r = s->prec == SLIM_FP64 ? tracer_step<double>(s, dt, st) : tracer_step<float>(s, dt, st);
+    r = step_launches(s, t, dt, st);
   if (r != SLIM_OK) return r;
   if (s->par.check_every > 0) {
     if (++s->steps_since_check >= s->par.check_every) {

@@ -115,6 +115,17 @@ struct slim_state {
   int* err = nullptr;       // device error flags
   double* stage64 = nullptr;  // 6P doubles: conversion staging of the mixed form
   int steps_since_check = 0;
+  // CUDA graph of the whole step
+  cudaStream_t g_stream = nullptr;
+  cudaGraphExec_t g_exec = nullptr;
+  cudaEvent_t g_in = nullptr, g_out = nullptr;
+  cudaGraphNode_t g_time_node = nullptr;
+  cudaKernelNodeParams g_time_params{};
+  double g_dt = 0.0;
+  double g_args_t = 0.0, g_args_dt = 0.0, g_args_amp = 0.0, g_args_period = 0.0;
+  int g_args_n = 0;
+  double* g_args_out = nullptr;
+  void* g_args[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // phase timing (slim_profile_*)
   bool prof_on = false;
   int prof_max = 0;

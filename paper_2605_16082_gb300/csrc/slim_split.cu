@@ -22,6 +22,7 @@ struct SplitBufs {
   float *cw_f, *icw_f;
   void *Ae_r, *AU_r, *AV_r, *Be_r, *BU_r, *BV_r, *Ce_r, *CU_r, *CV_r;  // compute-type shadows
   void *S3x_r, *S3y_r;
+  double* tide;  // open-boundary elevation per external stage of the step (+1 slot)
   double *Qbx, *Qby;  // the state's time-averaged transport buffers
   // compute-type copies for the 3D kernels
   void *F2x_r, *F2y_r, *Dqx_r, *Dqy_r, *gcor_r, *st_half, *st_end;
@@ -34,6 +35,24 @@ template <typename R, int TP>
 struct MB {
   static constexpr int value = sizeof(R) == 4 ? (1024 / TP > 0 ? 1024 / TP : 1) : (512 / TP > 0 ? 512 / TP : 1);
 };
+// OCC: resident blocks per SM asked of the register allocator at 256 threads
+// per block (scaled with the block size); the FP64 form always uses 2.
+template <typename R, int TP, int OCC>
+struct MBO {
+  static constexpr int occ = sizeof(R) == 4 ? OCC : 2;
+  static constexpr int value = (occ * 256 / TP) > 0 ? (occ * 256 / TP) : 1;
+};
+
+#define SLIM_TPO_SWITCH(TP, OC, ...)                                                   \
+  switch (TP * 10 + OC) {                                                              \
+    case 1282: { constexpr int TPc = 128, OCc = 2; __VA_ARGS__; } break;               \
+    case 1284: { constexpr int TPc = 128, OCc = 4; __VA_ARGS__; } break;               \
+    case 2562: { constexpr int TPc = 256, OCc = 2; __VA_ARGS__; } break;               \
+    case 2564: { constexpr int TPc = 256, OCc = 4; __VA_ARGS__; } break;               \
+    case 5122: { constexpr int TPc = 512, OCc = 2; __VA_ARGS__; } break;               \
+    case 5124: { constexpr int TPc = 512, OCc = 4; __VA_ARGS__; } break;               \
+    default: return cudaErrorInvalidValue;                                             \
+  }
 
 #define SLIM_TP_SWITCH2(TP, ...)                                \
   switch (TP) {                                                 \
@@ -61,6 +80,29 @@ template <typename R>
 __device__ __forceinline__ R zhat_r(const DevMesh& m, int i, int k) {
   if (m.n_levels == 0) return -(R)k * Geo<R>::hN(m, i);
   return Geo<R>::lev(m, k);
+}
+
+// ---------------------------------------------------------------------------
+// open-boundary elevation A cos(2 pi time / T) at every external stage of a step:
+// stage 1 runs n/2 subcycles over dt/2, stage 2 n subcycles over dt, each
+// subcycle's SSP-RK3 stages at times (0, 1, 1/2) x the subcycle length
+// ---------------------------------------------------------------------------
+__global__ void k_tide(double t0, double dt, int n, double amp, double period, double* __restrict__ out) {
+  const int n1 = n / 2;
+  const int total = 3 * (n1 + n);
+  const double off[3] = {0.0, 1.0, 0.5};
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    double time;
+    if (i < 3 * n1) {
+      const double dts = 0.5 * dt / n1;
+      time = t0 + (i / 3 + off[i % 3]) * dts;
+    } else {
+      const int j = i - 3 * n1;
+      const double dts = dt / n;
+      time = t0 + (j / 3 + off[j % 3]) * dts;
+    }
+    out[i] = amp * cos(2.0 * M_PI * time / period);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -97,8 +139,8 @@ __global__ void k_wave_speed(DevMesh m, double g, double* __restrict__ cw, doubl
 // ---------------------------------------------------------------------------
 // density + horizontal pressure gradient (one tile per block)
 // ---------------------------------------------------------------------------
-template <typename R, int TP>
-__global__ void __launch_bounds__(TP, (MB<R, TP>::value))
+template <typename R, int TP, int OCC>
+__global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
     k_hpg(DevMesh m, const R* __restrict__ T, const R* __restrict__ S, const R* __restrict__ st,
           PP<R> pp, R* __restrict__ Rx, R* __restrict__ Ry) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -336,8 +378,8 @@ __device__ __forceinline__ void momentum_extras(const DevMesh& m, int t, int k, 
 // ---------------------------------------------------------------------------
 // 3D horizontal momentum prediction: column sums of F_3D^h and of q (FP64)
 // ---------------------------------------------------------------------------
-template <typename R, int TP>
-__global__ void __launch_bounds__(TP, (MB<R, TP>::value))
+template <typename R, int TP, int OCC>
+__global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
     k_mompred(DevMesh m, AdvIn<R> in, const R* __restrict__ Rx, const R* __restrict__ Ry,
               PP<R> pp, double* __restrict__ S3x, double* __restrict__ S3y,
               double* __restrict__ Sqx, double* __restrict__ Sqy, R* __restrict__ S3x_r,
@@ -416,7 +458,7 @@ struct Ext2dIO {
 
 template <int MODE, typename RC>
 __global__ void __launch_bounds__(256)
-    k_ext2d(DevMesh m, SplitBufs bf, Ext2dIO io, double g_, double tide_, double alpha, double beta,
+    k_ext2d(DevMesh m, SplitBufs bf, Ext2dIO io, double g_, int tide_idx, double alpha, double beta,
             double dt, double bw) {
   const int nt = m.n_tri;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -424,7 +466,7 @@ __global__ void __launch_bounds__(256)
   const RC* er = (const RC*)io.er;
   const RC* Ur = (const RC*)io.Ur;
   const RC* Vr = (const RC*)io.Vr;
-  const RC g = (RC)g_, tide = (RC)tide_;
+  const RC g = (RC)g_, tide = (RC)bf.tide[tide_idx];
   RC e[3], U[3], V[3], H[3], gx[3], gy[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -656,8 +698,8 @@ struct UA {
   R kap_h;  // horizontal viscosity / diffusivity
 };
 
-template <typename R, int TP, int KIND, bool IMPL>
-__global__ void __launch_bounds__(TP, (MB<R, TP>::value))
+template <typename R, int TP, int KIND, bool IMPL, int OCC>
+__global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
     k_update(DevMesh m, AdvIn<R> in, const R* __restrict__ G0, const R* __restrict__ G1,
              const R* __restrict__ W, const R* __restrict__ Rx, const R* __restrict__ Ry,
              const R* __restrict__ F2x, const R* __restrict__ F2y, const R* __restrict__ st0,
@@ -829,25 +871,25 @@ PP<R> phys(const slim_params& p) {
   } while (0)
 
 template <typename R>
-cudaError_t launch_hpg(const DevMesh& m, int TP, const R* T, const R* S, const R* st,
+cudaError_t launch_hpg(const DevMesh& m, int TP, int occ, const R* T, const R* S, const R* st,
                        const PP<R>& pp, R* Rx, R* Ry, cudaStream_t s) {
-  SLIM_TP_SWITCH2(TP, {
+  SLIM_TPO_SWITCH(TP, occ, {
     const size_t sm = tile_smem(m, TPc, sizeof(R), 12);
-    cudaError_t e = set_smem2(k_hpg<R, TPc>, sm);
+    cudaError_t e = set_smem2(k_hpg<R, TPc, OCc>, sm);
     if (e != cudaSuccess) return e;
-    k_hpg<R, TPc><<<m.n_tiles, TPc, sm, s>>>(m, T, S, st, pp, Rx, Ry);
+    k_hpg<R, TPc, OCc><<<m.n_tiles, TPc, sm, s>>>(m, T, S, st, pp, Rx, Ry);
   });
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_mompred(const DevMesh& m, int TP, const AdvIn<R>& in, const R* Rx, const R* Ry,
-                           const PP<R>& pp, SplitBufs* b, cudaStream_t s) {
-  SLIM_TP_SWITCH2(TP, {
+cudaError_t launch_mompred(const DevMesh& m, int TP, int occ, const AdvIn<R>& in, const R* Rx,
+                           const R* Ry, const PP<R>& pp, SplitBufs* b, cudaStream_t s) {
+  SLIM_TPO_SWITCH(TP, occ, {
     const size_t sm = tile_smem(m, TPc, sizeof(R), 12);
-    cudaError_t e = set_smem2(k_mompred<R, TPc>, sm);
+    cudaError_t e = set_smem2(k_mompred<R, TPc, OCc>, sm);
     if (e != cudaSuccess) return e;
-    k_mompred<R, TPc><<<m.n_tiles, TPc, sm, s>>>(m, in, Rx, Ry, pp, b->S3x, b->S3y, b->Sqx, b->Sqy,
+    k_mompred<R, TPc, OCc><<<m.n_tiles, TPc, sm, s>>>(m, in, Rx, Ry, pp, b->S3x, b->S3y, b->Sqx, b->Sqy,
                                                  (R*)b->S3x_r, (R*)b->S3y_r);
   });
   return cudaGetLastError();
@@ -866,15 +908,15 @@ cudaError_t launch_cont_split(const DevMesh& m, int TP, const AdvIn<R>& in, cons
 }
 
 template <typename R, int KIND, bool IMPL>
-cudaError_t launch_update(const DevMesh& m, int TP, const AdvIn<R>& in, const R* G0, const R* G1,
+cudaError_t launch_update(const DevMesh& m, int TP, int occ, const AdvIn<R>& in, const R* G0, const R* G1,
                           const R* W, const R* Rx, const R* Ry, const R* F2x, const R* F2y,
                           const R* st0, const R* st1, const PP<R>& pp, const UA<R>& ua,
                           R* O0, R* O1, int* err, cudaStream_t s) {
-  SLIM_TP_SWITCH2(TP, {
+  SLIM_TPO_SWITCH(TP, occ, {
     const size_t sm = update_smem(m, TPc, sizeof(R));
-    cudaError_t e = set_smem2(k_update<R, TPc, KIND, IMPL>, sm);
+    cudaError_t e = set_smem2(k_update<R, TPc, KIND, IMPL, OCc>, sm);
     if (e != cudaSuccess) return e;
-    k_update<R, TPc, KIND, IMPL><<<m.n_tiles, TPc, sm, s>>>(m, in, G0, G1, W, Rx, Ry, F2x, F2y, st0,
+    k_update<R, TPc, KIND, IMPL, OCc><<<m.n_tiles, TPc, sm, s>>>(m, in, G0, G1, W, Rx, Ry, F2x, F2y, st0,
                                                             st1, pp, ua, O0, O1, err);
   });
   return cudaGetLastError();
@@ -884,12 +926,13 @@ cudaError_t launch_update(const DevMesh& m, int TP, const AdvIn<R>& in, const R*
 // one stage of the split step
 // ---------------------------------------------------------------------------
 template <typename R>
-slim_status stage(slim_state* s, double t0, double dt, int n_sub, bool implicit, const R* u_ev,
+slim_status stage(slim_state* s, double t0, double dt, int n_sub, int tide_base, bool implicit, const R* u_ev,
                   const R* v_ev, const R* T_ev, const R* S_ev, const R* st_ev, R* u_out, R* v_out,
                   R* T_out, R* S_out, cudaStream_t stm) {
   const DevMesh& m = s->mesh->d;
   SplitBufs* b = s->sp;
   const int TP = s->mesh->tile_prisms;
+  const int occ = s->par.blocks_per_sm == 2 ? 2 : 4;
   const PP<R> pp = phys<R>(s->par);
   const int nt = m.n_tri;
   const size_t n2 = (size_t)3 * nt;
@@ -897,12 +940,12 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, bool implicit,
   R* Ry = (R*)s->Ry;
   {
     ProfScope ps(s, SLIM_PHASE_HPG, stm);
-    SLIM_CU(launch_hpg<R>(m, TP, T_ev, S_ev, st_ev, pp, Rx, Ry, stm));
+    SLIM_CU(launch_hpg<R>(m, TP, occ, T_ev, S_ev, st_ev, pp, Rx, Ry, stm));
   }
   AdvIn<R> pin{u_ev, v_ev, nullptr, nullptr, nullptr, nullptr, st_ev, nullptr, nullptr, nullptr};
   {
     ProfScope ps(s, SLIM_PHASE_MOM_PRED, stm);
-    SLIM_CU(launch_mompred<R>(m, TP, pin, Rx, Ry, pp, b, stm));
+    SLIM_CU(launch_mompred<R>(m, TP, occ, pin, Rx, Ry, pp, b, stm));
   }
   b->has_s3 = true;
   // external mode from the state at t0
@@ -920,15 +963,14 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, bool implicit,
   SLIM_CU(cudaMemsetAsync(b->Gb, 0, n2 * 2 * 8, stm));
   const double dts = dt / n_sub;
   const double A_[3] = {0.0, 0.75, 1.0 / 3.0}, B_[3] = {1.0, 0.25, 2.0 / 3.0};
-  const double bw_[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0}, ts_[3] = {0.0, 1.0, 0.5};
+  const double bw_[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
   const int blk = 256, grd = (nt + blk - 1) / blk;
   double* F[3][3] = {{b->Ae, b->AU, b->AV}, {b->Be, b->BU, b->BV}, {b->Ce, b->CU, b->CV}};
   void* Fr[3][3] = {{b->Ae_r, b->AU_r, b->AV_r}, {b->Be_r, b->BU_r, b->BV_r}, {b->Ce_r, b->CU_r, b->CV_r}};
   for (int q = 0; q < n_sub; ++q) {
     for (int st = 0; st < 3; ++st) {
       const int si = st, so = (st + 1) % 3;  // A -> B -> C -> A
-      const double time = t0 + (q + ts_[st]) * dts;
-      const double tide = s->par.tide_amp * std::cos(2.0 * M_PI * time / s->par.tide_period);
+      const int tide_idx = tide_base + 3 * q + st;
       Ext2dIO io;
       io.e = F[si][0]; io.U = F[si][1]; io.V = F[si][2];
       io.er = shadow ? Fr[si][0] : F[si][0];
@@ -941,9 +983,9 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, bool implicit,
       io.Vor = shadow ? Fr[so][2] : nullptr;
       ProfScope ps(s, SLIM_PHASE_EXT2D, stm);
       if (sizeof(R) == 8)
-        k_ext2d<0, double><<<grd, blk, 0, stm>>>(m, *b, io, s->par.g, tide, A_[st], B_[st], dts, bw_[st] / n_sub);
+        k_ext2d<0, double><<<grd, blk, 0, stm>>>(m, *b, io, s->par.g, tide_idx, A_[st], B_[st], dts, bw_[st] / n_sub);
       else
-        k_ext2d<0, float><<<grd, blk, 0, stm>>>(m, *b, io, s->par.g, tide, A_[st], B_[st], dts, bw_[st] / n_sub);
+        k_ext2d<0, float><<<grd, blk, 0, stm>>>(m, *b, io, s->par.g, tide_idx, A_[st], B_[st], dts, bw_[st] / n_sub);
       SLIM_CU(cudaGetLastError());
     }
   }
@@ -974,19 +1016,19 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, bool implicit,
   {
     ProfScope ps(s, SLIM_PHASE_MOMENTUM, stm);
     if (implicit)
-      SLIM_CU((launch_update<R, 0, true>(m, TP, cin, U0, V0, (const R*)s->W, Rx, Ry, (const R*)b->F2x_r,
+      SLIM_CU((launch_update<R, 0, true>(m, TP, occ, cin, U0, V0, (const R*)s->W, Rx, Ry, (const R*)b->F2x_r,
                                          (const R*)b->F2y_r, st0, st1, pp, um, u_out, v_out, s->err, stm)));
     else
-      SLIM_CU((launch_update<R, 0, false>(m, TP, cin, U0, V0, (const R*)s->W, Rx, Ry, (const R*)b->F2x_r,
+      SLIM_CU((launch_update<R, 0, false>(m, TP, occ, cin, U0, V0, (const R*)s->W, Rx, Ry, (const R*)b->F2x_r,
                                           (const R*)b->F2y_r, st0, st1, pp, um, u_out, v_out, s->err, stm)));
   }
   {
     ProfScope ps(s, SLIM_PHASE_TRACERS, stm);
     if (implicit)
-      SLIM_CU((launch_update<R, 1, true>(m, TP, tin, T0, S0, (const R*)s->W, nullptr, nullptr, nullptr,
+      SLIM_CU((launch_update<R, 1, true>(m, TP, occ, tin, T0, S0, (const R*)s->W, nullptr, nullptr, nullptr,
                                          nullptr, st0, st1, pp, ut, T_out, S_out, s->err, stm)));
     else
-      SLIM_CU((launch_update<R, 1, false>(m, TP, tin, T0, S0, (const R*)s->W, nullptr, nullptr, nullptr,
+      SLIM_CU((launch_update<R, 1, false>(m, TP, occ, tin, T0, S0, (const R*)s->W, nullptr, nullptr, nullptr,
                                           nullptr, st0, st1, pp, ut, T_out, S_out, s->err, stm)));
   }
   return SLIM_OK;
@@ -1000,13 +1042,21 @@ slim_status step_t(slim_state* s, double t, double dt, cudaStream_t stm) {
   R* U = (R*)s->U; R* V = (R*)s->V; R* T = (R*)s->T; R* S = (R*)s->S;
   R* hu = (R*)s->tmp[0]; R* hv = (R*)s->tmp[1]; R* hT = (R*)s->tmp[2]; R* hS = (R*)s->tmp[3];
   // stage 1: t -> t + dt/2, vertically implicit, n_sub/2 external steps
-  slim_status r = stage<R>(s, t, 0.5 * dt, s->par.n_sub / 2, true, U, V, T, S, (const R*)s->st_cur,
+  // open-boundary elevation of every external stage of the step (first kernel of the
+  // step: its time argument is the only one that changes between steps)
+  {
+    ProfScope ps(s, SLIM_PHASE_MISC, stm);
+    k_tide<<<1, 128, 0, stm>>>(t, dt, s->par.n_sub, s->par.tide_amp, s->par.tide_period, b->tide);
+    SLIM_CU(cudaGetLastError());
+  }
+  slim_status r = stage<R>(s, t, 0.5 * dt, s->par.n_sub / 2, 0, true, U, V, T, S, (const R*)s->st_cur,
                            hu, hv, hT, hS, stm);
   if (r != SLIM_OK) return r;
   SLIM_CU(cudaMemcpyAsync(b->st_half, b->st_end, n2 * sizeof(R), cudaMemcpyDeviceToDevice, stm));
   SLIM_CU(cudaMemcpyAsync(b->eta_half, b->Ae, n2 * 8, cudaMemcpyDeviceToDevice, stm));
   // stage 2: t -> t + dt from the same start, horizontal terms at the stage-1 state
-  r = stage<R>(s, t, dt, s->par.n_sub, false, hu, hv, hT, hS, (const R*)b->st_half, U, V, T, S, stm);
+  r = stage<R>(s, t, dt, s->par.n_sub, 3 * (s->par.n_sub / 2), false, hu, hv, hT, hS,
+               (const R*)b->st_half, U, V, T, S, stm);
   if (r != SLIM_OK) return r;
   SLIM_CU(cudaMemcpyAsync(s->eta, b->Ae, n2 * 8, cudaMemcpyDeviceToDevice, stm));
   SLIM_CU(cudaMemcpyAsync(s->Qx, b->AU, n2 * 8, cudaMemcpyDeviceToDevice, stm));
@@ -1022,6 +1072,8 @@ slim_status step_t(slim_state* s, double t, double dt, cudaStream_t stm) {
 // entry points used by the C ABI
 // ---------------------------------------------------------------------------
 size_t split_aux2d_len(const DevMesh& m) { return (size_t)16 * m.n_tri; }
+
+const void* split_time_kernel() { return (const void*)k_tide; }
 
 slim_status split_alloc(slim_state* s) {
   if (s->sp) return SLIM_OK;
@@ -1055,6 +1107,8 @@ slim_status split_alloc(slim_state* s) {
     SLIM_CU(cudaMalloc((void**)p, n2 * 2 * sizeof(float)));
     s->allocs.push_back(*p);
   }
+  SLIM_CU(cudaMalloc((void**)&b->tide, (size_t)(3 * (s->par.n_sub / 2 + s->par.n_sub) + 1) * 8));
+  s->allocs.push_back(b->tide);
   SLIM_CU(cudaMalloc((void**)&b->iw6, (size_t)m.n_tri * 8));
   s->allocs.push_back(b->iw6);
   b->Qbx = s->Qbx;
@@ -1087,11 +1141,11 @@ void* split_field(slim_state* s, int field) {
 slim_status split_hpg(slim_state* s, cudaStream_t st) {
   const DevMesh& m = s->mesh->d;
   if (s->prec == SLIM_FP64)
-    SLIM_CU(launch_hpg<double>(m, s->mesh->tile_prisms, (const double*)s->T, (const double*)s->S,
+    SLIM_CU(launch_hpg<double>(m, s->mesh->tile_prisms, 2, (const double*)s->T, (const double*)s->S,
                                (const double*)s->st_cur, phys<double>(s->par), (double*)s->Rx,
                                (double*)s->Ry, st));
   else
-    SLIM_CU(launch_hpg<float>(m, s->mesh->tile_prisms, (const float*)s->T, (const float*)s->S,
+    SLIM_CU(launch_hpg<float>(m, s->mesh->tile_prisms, s->par.blocks_per_sm == 2 ? 2 : 4, (const float*)s->T, (const float*)s->S,
                               (const float*)s->st_cur, phys<float>(s->par), (float*)s->Rx,
                               (float*)s->Ry, st));
   return SLIM_OK;
@@ -1102,20 +1156,23 @@ slim_status split_rhs2d(slim_state* s, double t, double* out, cudaStream_t st) {
   const DevMesh& m = s->mesh->d;
   SplitBufs* b = s->sp;
   const double tide = s->par.tide_amp * std::cos(2.0 * M_PI * t / s->par.tide_period);
+  const int slot = 3 * (s->par.n_sub / 2 + s->par.n_sub);
+  SLIM_CU(cudaMemcpyAsync(b->tide + slot, &tide, sizeof(double), cudaMemcpyHostToDevice, st));
+  SLIM_CU(cudaStreamSynchronize(st));
   const int grd = (m.n_tri + 255) / 256;
   Ext2dIO io{};
   io.e = s->eta; io.U = s->Qx; io.V = s->Qy;
   io.eo = out;
   if (s->prec == SLIM_FP64) {
     io.er = s->eta; io.Ur = s->Qx; io.Vr = s->Qy;
-    k_ext2d<1, double><<<grd, 256, 0, st>>>(m, *b, io, s->par.g, tide, 0.0, 0.0, 0.0, 0.0);
+    k_ext2d<1, double><<<grd, 256, 0, st>>>(m, *b, io, s->par.g, slot, 0.0, 0.0, 0.0, 0.0);
   } else {
     const size_t n2 = (size_t)3 * m.n_tri;
     SLIM_CU(launch_convert_d2f(s->eta, (float*)b->Ae_r, n2, st));
     SLIM_CU(launch_convert_d2f(s->Qx, (float*)b->AU_r, n2, st));
     SLIM_CU(launch_convert_d2f(s->Qy, (float*)b->AV_r, n2, st));
     io.er = b->Ae_r; io.Ur = b->AU_r; io.Vr = b->AV_r;
-    k_ext2d<1, float><<<grd, 256, 0, st>>>(m, *b, io, s->par.g, tide, 0.0, 0.0, 0.0, 0.0);
+    k_ext2d<1, float><<<grd, 256, 0, st>>>(m, *b, io, s->par.g, slot, 0.0, 0.0, 0.0, 0.0);
   }
   SLIM_CU(cudaGetLastError());
   return SLIM_OK;
@@ -1127,9 +1184,10 @@ slim_status split_step(slim_state* s, double t, double dt, cudaStream_t st) {
 }
 
 int split_kernel_count(const slim_state* s) {
-  // per stage: hpg, mompred, 3 n_sub_stage external stages, couple, continuity, momentum, tracers
+  // time kernel; per stage: hpg, mompred, 3 n_sub_stage external stages, couple,
+  // continuity, momentum, tracers; the mixed form's 2D shadow conversions (3 per stage)
   const int n = s->par.n_sub;
-  return 2 * 6 + 3 * (n / 2 + n);
+  return 1 + 2 * 6 + 3 * (n / 2 + n) + (s->prec == SLIM_MIXED ? 6 : 0);
 }
 
 }  // namespace slim

@@ -13,4 +13,6 @@ slim_status split_hpg(slim_state* s, cudaStream_t st);
 slim_status split_rhs2d(slim_state* s, double t, double* out, cudaStream_t st);
 slim_status split_step(slim_state* s, double t, double dt, cudaStream_t st);
 int split_kernel_count(const slim_state* s);
+// the step's time kernel (its first argument is the step's start time)
+const void* split_time_kernel();
 }  // namespace slim

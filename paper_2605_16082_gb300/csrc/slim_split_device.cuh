@@ -277,32 +277,41 @@ __device__ __forceinline__ void prism_sipg(const DevMesh& m, int t, int k, int N
     const R sig = pen * nu / fmin(rin_t, rin_n);
     const R gno[2] = {gux[0] * nxe + guy[0] * nye, gux[1] * nxe + guy[1] * nye};
     const R gnn[2] = {gnx[0] * nxe + gny[0] * nye, gnx[1] * nxe + gny[1] * nye};
-    R gvn[3];
+    // The face integrals are polynomials of degree <= 3 per direction, integrated
+    // exactly in closed form: with the edge basis b_i and psi_c,
+    //   int b_i b_j = E2_ij (2/3, 1/3), int b_i b_j b_k = 1/2 (all equal) or 1/6,
+    //   int psi_d psi_c = G_dc (2/3, 1/3).
+    const R t3 = (R)(1.0 / 3.0), t6 = (R)(1.0 / 6.0);
+    const R hzo[2] = {hz[a0], hz[a1]}, hzn[2] = {hzn0, hzn1};
+    const R Zo[2] = {t3 * ((R)2 * hzo[0] + hzo[1]), t3 * ((R)2 * hzo[1] + hzo[0])};
+    const R Zn[2] = {t3 * ((R)2 * hzn[0] + hzn[1]), t3 * ((R)2 * hzn[1] + hzn[0])};
+    const R Go[2] = {t3 * ((R)2 * gno[0] + gno[1]), t3 * ((R)2 * gno[1] + gno[0])};
+    const R Gn[2] = {t3 * ((R)2 * gnn[0] + gnn[1]), t3 * ((R)2 * gnn[1] + gnn[0])};
+    // jumps at the face nodes (own vertex j <-> neighbour vertex l_j), G-weighted in zeta
+    R J[2][2], gJ[2][2];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) gvn[a] = gx[a] * nxe + gy[a] * nye;
+    for (int c = 0; c < 2; ++c) {
+      J[0][c] = f[c][a0] - fn[c][l0];
+      J[1][c] = f[c][a1] - fn[c][l1];
+    }
 #pragma unroll
-    for (int gs = 0; gs < 2; ++gs) {
-      const R b0 = gs ? (R)SLIM_GL2 : (R)SLIM_GL1;
-      const R b1 = gs ? (R)SLIM_GL1 : (R)SLIM_GL2;
-      const R zzo = b0 * hz[a0] + b1 * hz[a1];
-      const R zzn = b0 * hzn0 + b1 * hzn1;
+    for (int i = 0; i < 2; ++i) {
+      gJ[i][0] = t3 * ((R)2 * J[i][0] + J[i][1]);
+      gJ[i][1] = t3 * ((R)2 * J[i][1] + J[i][0]);
+    }
+    const R hs0 = hzo[0] + hzn[0], hs1 = hzo[1] + hzn[1];
+    const R M00 = (R)0.5 * hs0 + t6 * hs1, M11 = (R)0.5 * hs1 + t6 * hs0, M01 = t6 * (hs0 + hs1);
+    const R hnu = half_len * (R)0.5 * nu;
+    const R hsig = half_len * (R)0.5 * sig;
 #pragma unroll
-      for (int gz = 0; gz < 2; ++gz) {
-        const R z0 = gz ? (R)SLIM_GL2 : (R)SLIM_GL1;
-        const R z1 = gz ? (R)SLIM_GL1 : (R)SLIM_GL2;
-        const R fo = b0 * (z0 * f[0][a0] + z1 * f[1][a0]) + b1 * (z0 * f[0][a1] + z1 * f[1][a1]);
-        const R fnb = b0 * (z0 * fn[0][l0] + z1 * fn[1][l0]) + b1 * (z0 * fn[0][l1] + z1 * fn[1][l1]);
-        const R flux = (R)0.5 * nu * (zzo * (z0 * gno[0] + z1 * gno[1]) + zzn * (z0 * gnn[0] + z1 * gnn[1]));
-        const R jump = fo - fnb;
-        const R pj = sig * (R)0.5 * (zzo + zzn) * jump;
-        const R sj = (R)0.5 * nu * zzo * jump;
+    for (int c = 0; c < 2; ++c) {
+      const R zj = Zo[0] * gJ[0][c] + Zo[1] * gJ[1][c];
+      // flux {nu z_zeta grad f}.n tested with the edge functions, minus the penalty
+      out[c][a0] += hnu * (Zo[0] * Go[c] + Zn[0] * Gn[c]) - hsig * (M00 * gJ[0][c] + M01 * gJ[1][c]);
+      out[c][a1] += hnu * (Zo[1] * Go[c] + Zn[1] * Gn[c]) - hsig * (M01 * gJ[0][c] + M11 * gJ[1][c]);
+      // symmetry term 1/2 nu z_zeta grad v.n [f] for every own test function
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const R va = (a == a0) ? b0 : ((a == a1) ? b1 : (R)0);
-          out[0][a] += half_len * ((flux - pj) * va * z0 + sj * gvn[a] * z0);
-          out[1][a] += half_len * ((flux - pj) * va * z1 + sj * gvn[a] * z1);
-        }
-      }
+      for (int a = 0; a < 3; ++a) out[c][a] += hnu * (gx[a] * nxe + gy[a] * nye) * zj;
     }
   }
 }

@@ -37,7 +37,7 @@ class SlimParams(C.Structure):
         "g", "rho0", "coriolis_f", "eos_alpha", "eos_beta", "eos_T0", "eos_S0", "kappa_v",
         "nu_v", "kappa_h", "nu_h", "drag_cd", "flux_top", "flux_bot", "penalty_v", "penalty_h",
         "tide_amp", "tide_period")] + [(n, C.c_int) for n in (
-        "scheme", "n_sub", "tile_prisms", "check_every")]
+        "scheme", "n_sub", "tile_prisms", "check_every", "blocks_per_sm", "use_graph")]
 
 
 class SlimError(RuntimeError):

@@ -216,3 +216,32 @@ def test_split_mixed_precision_error(slim):
         assert errs[f] < 1e-6, (f, errs[f])
     for f in ("U", "V", "ETA", "QX", "QY"):
         assert errs[f] < 1e-3, (f, errs[f])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_graph_replay_matches_launches(slim, prec):
+    """The captured whole-step graph reproduces the launched step bit for bit,
+    including the start time that changes between replays."""
+    m = case_mesh("basin")
+    ini = initial(m)
+    pr = slim.SLIM_FP64 if prec == "fp64" else slim.SLIM_MIXED
+    out = []
+    for use_graph in (0, 1):
+        p = params(slim, use_graph=use_graph)
+        with model(slim, m, pr, p, ini) as mod:
+            for n in range(3):
+                slim.slim_step(mod.state, 100.0 + n * 25.0, 25.0)
+            out.append({f: mod.download(f) for f, _ in FIELDS3 + FIELDS2})
+    for f in out[0]:
+        assert np.array_equal(out[0][f], out[1][f]), f
+
+
+def test_autotune_returns_a_measured_configuration(slim):
+    from paper_2605_16082_gb300 import autotune
+    m = case_mesh("basin")
+    ini = initial(m)
+    p = params(slim)
+    res = autotune.autotune(m, slim.SLIM_MIXED, p, ini, 20.0, use_cache=False)
+    assert res["tile_prisms"] in autotune.TILES and res["blocks_per_sm"] in autotune.OCCS
+    assert len(res["all"]) == len(autotune.TILES) * len(autotune.OCCS)
+    assert res["ms_per_step"] == min(res["all"].values()) > 0

@@ -275,3 +275,16 @@ def test_sampled_parity_at_basin_size(slim):
     # the per-field bar over the sampled outputs
     assert rel_l2(np.concatenate(gT), np.concatenate(rT)) < TOL64
     assert rel_l2(np.concatenate(ge), np.concatenate(re)) < TOL64
+
+
+def test_tracer_graph_replay_matches_launches(slim):
+    m, L = CASES["uneven"]()
+    u, v = sheared_velocity(m, L)
+    T = wl.c1_tracer(m, L, 0.2 * L)
+    res = []
+    for g in (0, 1):
+        with _setup(slim, m, u, v, T, slim.SLIM_MIXED, kappa_v=1e-2, use_graph=g) as mod:
+            for n in range(3):
+                slim.slim_step(mod.state, n * 20.0, 20.0)
+            res.append(mod.download("T"))
+    assert np.array_equal(res[0], res[1])
