@@ -76,7 +76,9 @@ slim_status dev_alloc(slim_state* s, void** p, size_t bytes) {
 
 void drop_graph(slim_state* s) {
   if (s->g_exec) cudaGraphExecDestroy(s->g_exec);
+  if (s->g_graph) cudaGraphDestroy(s->g_graph);
   s->g_exec = nullptr;
+  s->g_graph = nullptr;
   s->g_time_node = nullptr;
 }
 
@@ -447,8 +449,12 @@ slim_status step_graph(slim_state* s, double t, double dt, cudaStream_t user) {
         }
       }
     }
-    cudaGraphDestroy(g);
-    if (ce != cudaSuccess) { set_error(std::string("instantiate: ") + cudaGetErrorString(ce)); return SLIM_ERR_CUDA; }
+    s->g_graph = g;
+    if (ce != cudaSuccess) {
+      drop_graph(s);
+      set_error(std::string("instantiate: ") + cudaGetErrorString(ce));
+      return SLIM_ERR_CUDA;
+    }
     if (s->par.scheme == SLIM_SCHEME_SPLIT && !s->g_time_node) {
       drop_graph(s);
       set_error("time kernel not found in the captured step");
@@ -462,7 +468,7 @@ slim_status step_graph(slim_state* s, double t, double dt, cudaStream_t user) {
     s->g_args_n = s->par.n_sub;
     s->g_args_amp = s->par.tide_amp;
     s->g_args_period = s->par.tide_period;
-    s->g_args_out = ((double**)s->g_time_params.kernelParams)[5];
+    s->g_args_out = split_tide_ptr(s);
     void* args[6] = {&s->g_args_t, &s->g_args_dt, &s->g_args_n, &s->g_args_amp, &s->g_args_period,
                      &s->g_args_out};
     cudaKernelNodeParams kp = s->g_time_params;

@@ -117,6 +117,7 @@ struct slim_state {
   int steps_since_check = 0;
   // CUDA graph of the whole step
   cudaStream_t g_stream = nullptr;
+  cudaGraph_t g_graph = nullptr;      // kept alive: its node handles address the exec
   cudaGraphExec_t g_exec = nullptr;
   cudaEvent_t g_in = nullptr, g_out = nullptr;
   cudaGraphNode_t g_time_node = nullptr;

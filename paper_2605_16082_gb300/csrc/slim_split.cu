@@ -1074,6 +1074,7 @@ slim_status step_t(slim_state* s, double t, double dt, cudaStream_t stm) {
 size_t split_aux2d_len(const DevMesh& m) { return (size_t)16 * m.n_tri; }
 
 const void* split_time_kernel() { return (const void*)k_tide; }
+double* split_tide_ptr(slim_state* s) { return s->sp ? s->sp->tide : nullptr; }
 
 slim_status split_alloc(slim_state* s) {
   if (s->sp) return SLIM_OK;

@@ -259,6 +259,8 @@ class Model:
             self.state = slim_state_alloc(self.mesh_h, precision, self.params)
         except Exception:
             slim_mesh_destroy(self.mesh_h)
+            self.mesh_h = None
+            self.state = None
             raise
 
     def n(self, field: str) -> int:
