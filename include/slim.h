@@ -242,6 +242,25 @@ slim_status slim_step(slim_state* s, double t, double dt, void* stream);
  * order (deterministic).  Writes one double to *mass_host; synchronises. */
 slim_status slim_tracer_mass(slim_state* s, int field, double* mass_host, void* stream);
 
+/* slim_tracer_mass_noalloc: the same sum as slim_tracer_mass (same order, same
+ * result), for callers that must not allocate device memory during the call: a
+ * pool or caching allocator that forbids direct cudaMalloc/cudaFree, code that
+ * must not block or synchronize the host, or a fixed device-memory budget.  The
+ * paper has no counterpart; this is a library convenience.
+ *   mass_dev: caller-owned device address of one double, written when the
+ *             stream reaches the call (nothing is copied to the host; the call
+ *             does not wait for the GPU).
+ * Scratch: the block partials live in a fixed 1 MiB device array inside the
+ * library (2 doubles per thread-block tile, at most 65536 tiles), held by every
+ * GPU that loads the library until the process exits; a mesh with more tiles is
+ * rejected with SLIM_ERR_ARG.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  The array is shared by all calls and keeps
+ * the last call's partials: calls whose work overlaps on the GPU (other streams,
+ * other states, other threads) race on it.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.  field: SLIM_FIELD_T or _S. */
+slim_status slim_tracer_mass_noalloc(slim_state* s, int field, double* mass_dev, void* stream);
+
 /* Number of kernels slim_step launches per call (for launch accounting). */
 int slim_step_kernel_count(const slim_state* s);
 

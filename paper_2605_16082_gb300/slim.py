@@ -28,7 +28,7 @@ EXPORTED = ["slim_params_default", "slim_status_string", "slim_last_error", "sli
             "slim_state_field_ptr", "slim_state_check", "slim_rhs3d", "slim_continuity",
             "slim_rhs2d", "slim_vertical_solve", "slim_hpg", "slim_step", "slim_tracer_mass",
             "slim_step_kernel_count", "slim_profile_begin", "slim_profile_end",
-            "slim_phase_name"]
+            "slim_phase_name", "slim_tracer_mass_noalloc"]
 PHASES = ["continuity", "tracer_stage", "hpg", "mom_pred", "ext2d", "momentum", "tracers", "misc"]
 
 
@@ -81,6 +81,7 @@ def lib() -> C.CDLL:
             "slim_profile_begin": ([_vp, _i], _i),
             "slim_profile_end": ([_vp, _dp, C.POINTER(_i)], _i),
             "slim_phase_name": ([_i], C.c_char_p),
+            "slim_tracer_mass_noalloc": ([_vp, _i, _vp, _vp], _i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -216,6 +217,12 @@ def slim_tracer_mass(state: int, field: int, stream: int = 0) -> float:
     out = C.c_double()
     _check(lib().slim_tracer_mass(state, int(field), C.byref(out), stream))
     return out.value
+
+
+def slim_tracer_mass_noalloc(state: int, field: int, mass_dev: int, stream: int = 0) -> None:
+    """Tracer mass into one device double at ``mass_dev`` without device allocation
+    (asynchronous on ``stream``)."""
+    _check(lib().slim_tracer_mass_noalloc(state, int(field), mass_dev, stream))
 
 
 def slim_step_kernel_count(state: int) -> int:
