@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--tile", type=int, default=0, help="prisms per block without the autotuner")
+    ap.add_argument("--occ", type=int, default=0, help="blocks per SM without the autotuner")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -137,7 +139,10 @@ def workload_inputs(name: str):
 def phase_bytes(phase: str, m, esz: int, n_sub: int) -> float:
     """Algorithmic bytes of one launch of a phase: every input read once and every
     output written once (neighbour gathers counted once), per prism P and per
-    triangle n_tri; 2D arrays in FP64."""
+    triangle n_tri.  The 2D kernel of the FP64 form moves 736 B per triangle per
+    RK stage (FP64 state, geometry, averages); the mixed form's three stage
+    kernels move 332, 452 and 692 B (FP32 stage values and increment sums, FP64
+    state and averages only in the last stage), 492 B on average."""
     P, nt = m.n_prisms, m.n_tri
     geo = 160.0 if esz == 4 else 240.0          # per-triangle geometry + adjacency
     if phase == "tracer_stage":                  # T_p, T_n (avg), u, v, W -> T
@@ -150,9 +155,64 @@ def phase_bytes(phase: str, m, esz: int, n_sub: int) -> float:
         return P * 24.0 * esz + nt * (geo + 3 * esz + 12 * 8)
     if phase in ("momentum", "tracers"):         # f_ev(2), f_0(2), u_ev(2, tracers), W, r -> f(2)
         return P * 54.0 * esz + nt * (geo + 3 * 3 * esz + 18 * esz)
-    if phase == "ext2d":                         # stage and start states, source, averages
-        return nt * 8.0 * (9 + 9 + 6 + 6 + 9 + 12 + 12 + 6)
+    if phase == "ext2d":
+        return nt * (492.0 if esz == 4 else 736.0)
     return float("nan")
+
+
+# phase -> kernel function that runs it (the momentum and tracer updates are two
+# instances of one kernel)
+KERNEL_OF = {"split": {"continuity": "k_cont_split", "hpg": "k_hpg", "mom_pred": "k_mompred",
+                       "ext2d": "k_ext2d", "momentum": "k_update", "tracers": "k_update",
+                       "misc": "k_couple2d"},
+             "tracer": {"continuity": "k_continuity", "tracer_stage": "k_tracer_stage",
+                        "misc": "k_stretch"}}
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
+# capture, valid only while the kernel sources hash to ``src``; see profiles/.
+TRAFFIC = {}
+KSRC = ["paper_2605_16082_gb300/csrc/slim_split.cu", "paper_2605_16082_gb300/csrc/slim_split_device.cuh",
+        "paper_2605_16082_gb300/csrc/slim_device.cuh", "paper_2605_16082_gb300/csrc/slim_tracer.cu",
+        "paper_2605_16082_gb300/csrc/slim_internal.h"]
+
+
+def kernel_src_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KSRC:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def rooflines(r: dict, m, scheme: str, pname: str, workload: str, hbm: float, peak_src: str):
+    """Achieved GB/s of every kernel function over its launches in the profiled
+    steps, and the dominant one (largest share of the step)."""
+    esz = 8 if pname == "fp64" else 4
+    groups = {}
+    for ph, (ms, n) in r["phases"].items():
+        k = KERNEL_OF[scheme].get(ph, ph)
+        g = groups.setdefault(k, dict(ms=0.0, launches=0, bytes=0.0))
+        g["ms"] += ms
+        g["launches"] += n
+        g["bytes"] += phase_bytes(ph, m, esz, 0) * n
+    out = {}
+    for k, g in groups.items():
+        if not g["launches"] or not np.isfinite(g["bytes"]):
+            continue
+        ach = g["bytes"] / (g["ms"] / 1e3) / 1e9
+        out[k] = dict(achieved=ach, frac=ach / hbm, launch_ms=g["ms"] / g["launches"],
+                      launches=g["launches"], alg_bytes_per_launch=g["bytes"] / g["launches"])
+    dom = max(out, key=lambda k: out[k]["launch_ms"] * out[k]["launches"])
+    d = out[dom]
+    tr = TRAFFIC.get((dom, pname, workload))
+    traffic = tr["bytes"] if tr and tr["src"] == kernel_src_hash() else None
+    head = dict(kernel=dom, bound="hbm", achieved=d["achieved"], peak=hbm, unit="GB/s",
+                frac=d["frac"], traffic=traffic, peak_src=peak_src, launch_ms=d["launch_ms"],
+                alg_bytes_per_launch=d["alg_bytes_per_launch"])
+    return head, {k: dict(achieved=round(v["achieved"], 1), frac=round(v["frac"], 4),
+                          launch_ms=round(v["launch_ms"], 5), launches=v["launches"])
+                  for k, v in out.items()}
 
 
 def run_ours(args, rank: int, world: int):
@@ -181,7 +241,16 @@ def run_ours(args, rank: int, world: int):
             par.tile_prisms = tn["tile_prisms"]
             par.blocks_per_sm = tn["blocks_per_sm"]
             tuned[pname] = tn
+        else:
+            if args.tile:
+                par.tile_prisms = args.tile
+            if args.occ:
+                par.blocks_per_sm = args.occ
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         mod = slim.Model(m, prec, par)
+        torch.cuda.synchronize()
+        dev_bytes = free0 - torch.cuda.mem_get_info()[0]
         for k, v in fields.items():
             mod.upload(k, v)
         t = 0.0
@@ -215,13 +284,9 @@ def run_ours(args, rank: int, world: int):
         slim.slim_state_check(mod.state, sh)
         ms = allmax(ms, world)
         ms_step = ms / args.steps
-        dom = max(phases, key=lambda k: phases[k][0])
-        dom_ms = phases[dom][0] / phases[dom][1]
-        esz = 8 if pname == "fp64" else 4
-        ab = phase_bytes(dom, m, esz, W.get("n_sub", 0))
         r = dict(value=world * dofs / (ms_step / 1e3), ms_per_step=ms_step, phases=phases,
-                 dominant=dom, dom_ms=dom_ms, alg_bytes=ab, gpu_launches=n_k * args.steps,
-                 tile_prisms=par.tile_prisms, blocks_per_sm=par.blocks_per_sm,
+                 gpu_launches=n_k * args.steps,
+                 tile_prisms=par.tile_prisms, blocks_per_sm=par.blocks_per_sm, device_bytes=dev_bytes,
                  autotune=tuned.get(pname, {}).get("all"))
         # end to end through the public API with pinned host buffers
         if not args.no_e2e:
@@ -359,25 +424,26 @@ def main():
     head = res.get("mixed") or res["fp64"]
     hname = "mixed" if "mixed" in res else "fp64"
 
-    def roof(r):
-        ach = r["alg_bytes"] / (r["dom_ms"] / 1e3) / 1e9
-        return dict(kernel=r["dominant"], bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s",
-                    frac=ach / pk["hbm_gbs"], traffic=None, peak_src=pk["src"],
-                    launch_ms=r["dom_ms"])
+    def roof(r, pname):
+        return rooflines(r, m, W["scheme"], pname, args.workload, pk["hbm_gbs"], pk["src"])
 
     line = dict(metric=METRIC, value=head["value"], unit=UNIT, n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=head["ms_per_step"], higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f32+f64" if hname == "mixed" else "f64",
-                data="synthetic", config=cfg, roofline=roof(head), clocks=clocks,
+                data="synthetic", config=cfg, roofline=roof(head, hname)[0],
+                roofline_all=roof(head, hname)[1], clocks=clocks,
                 gpu_launches=head["gpu_launches"], phases_ms={k: v[0] for k, v in head["phases"].items()},
+                device_bytes=head["device_bytes"],
                 tiling=dict(prisms_per_block=head["tile_prisms"], blocks_per_sm=head["blocks_per_sm"],
                             autotune_ms=head["autotune"]), cuda_graph=True)
     if "e2e" in head:
         line["e2e"] = head["e2e"]
     if "fp64" in res and hname != "fp64":
         f = res["fp64"]
-        line["fp64"] = dict(value=f["value"], ms_per_step=f["ms_per_step"], roofline=roof(f),
+        line["fp64"] = dict(value=f["value"], ms_per_step=f["ms_per_step"], roofline=roof(f, "fp64")[0],
+                            roofline_all=roof(f, "fp64")[1],
                             e2e=f.get("e2e"), phases_ms={k: v[0] for k, v in f["phases"].items()},
+                            device_bytes=f["device_bytes"],
                             tiling=dict(prisms_per_block=f["tile_prisms"], blocks_per_sm=f["blocks_per_sm"]))
     if not args.no_cpu:
         line["cpu_baseline"] = oracle_sample(args, m, args.cpu_seconds)

@@ -23,6 +23,9 @@ struct SplitBufs {
   void *Ae_r, *AU_r, *AV_r, *Be_r, *BU_r, *BV_r, *Ce_r, *CU_r, *CV_r;  // compute-type shadows
   void *S3x_r, *S3y_r;
   double* tide;  // open-boundary elevation per external stage of the step (+1 slot)
+  float* tide_f;  // the same stage values in FP32 (after the doubles in the same buffer)
+  // mixed form: FP32 stage-increment sums of the 2D subcycle and FP32 1/(w/6)
+  float *Dacc, *Eacc, *Gacc, *iw6_f;
   double *Qbx, *Qby;  // the state's time-averaged transport buffers
   // compute-type copies for the 3D kernels
   void *F2x_r, *F2y_r, *Dqx_r, *Dqy_r, *gcor_r, *st_half, *st_end;
@@ -91,6 +94,7 @@ __global__ void k_tide(double t0, double dt, int n, double amp, double period, d
   const int n1 = n / 2;
   const int total = 3 * (n1 + n);
   const double off[3] = {0.0, 1.0, 0.5};
+  float* out_f = reinterpret_cast<float*>(out + total + 1);  // FP32 copies after the doubles
   for (int i = threadIdx.x; i < total; i += blockDim.x) {
     double time;
     if (i < 3 * n1) {
@@ -102,6 +106,7 @@ __global__ void k_tide(double t0, double dt, int n, double amp, double period, d
       time = t0 + (j / 3 + off[j % 3]) * dts;
     }
     out[i] = amp * cos(2.0 * M_PI * time / period);
+    out_f[i] = (float)out[i];
   }
 }
 
@@ -110,10 +115,11 @@ __global__ void k_tide(double t0, double dt, int n, double amp, double period, d
 // ---------------------------------------------------------------------------
 __global__ void k_wave_speed(DevMesh m, double g, double* __restrict__ cw, double* __restrict__ icw,
                              float* __restrict__ cw_f, float* __restrict__ icw_f,
-                             double* __restrict__ iw6) {
+                             double* __restrict__ iw6, float* __restrict__ iw6_f) {
   const int nt = m.n_tri;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
     iw6[t] = 6.0 / m.jh[t];
+    iw6_f[t] = (float)iw6[t];
     for (int e = 0; e < 3; ++e) {
       const int4 ei = m.einfo[e * nt + t];
       const int a0 = e, a1 = (e + 1) % 3;
@@ -456,17 +462,13 @@ struct Ext2dIO {
   void *eor, *Uor, *Vor;        // stage output shadow (RC); null in the FP64 form
 };
 
-template <int MODE, typename RC>
-__global__ void __launch_bounds__(256)
-    k_ext2d(DevMesh m, SplitBufs bf, Ext2dIO io, double g_, int tide_idx, double alpha, double beta,
-            double dt, double bw) {
+// Residual of the 2D stage at the RC state (er, Ur, Vr) of triangle t; Fe
+// receives the eta flux at the 6 edge points (edge-major, 2 points per edge).
+template <typename RC>
+__device__ __forceinline__ void ext2d_residual(const DevMesh& m, const SplitBufs& bf, const RC* er,
+                                               const RC* Ur, const RC* Vr, RC g, RC tide, int t,
+                                               RC Re[3], RC RU[3], RC RV[3], RC Fe[6]) {
   const int nt = m.n_tri;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nt) return;
-  const RC* er = (const RC*)io.er;
-  const RC* Ur = (const RC*)io.Ur;
-  const RC* Vr = (const RC*)io.Vr;
-  const RC g = (RC)g_, tide = (RC)bf.tide[tide_idx];
   RC e[3], U[3], V[3], H[3], gx[3], gy[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -482,7 +484,6 @@ __global__ void __launch_bounds__(256)
   const RC eH = w24 * (se * sH + e[0] * H[0] + e[1] * H[1] + e[2] * H[2]);
   const RC gHx = H[0] * gx[0] + H[1] * gx[1] + H[2] * gx[2];
   const RC gHy = H[0] * gy[0] + H[1] * gy[1] + H[2] * gy[2];
-  RC Re[3], RU[3], RV[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     Re[a] = w6 * (sU * gx[a] + sV * gy[a]);
@@ -524,15 +525,27 @@ __global__ void __launch_bounds__(256)
       }
       const int ip = (ed * nt + t) * 2 + gs;
       const RC c = Ext2dGeo<RC>::c(bf, ip);
-      const RC Fe = (RC)0.5 * (qo + qx) + (RC)0.5 * c * (eo_ - ex);
+      const RC fe = (RC)0.5 * (qo + qx) + (RC)0.5 * c * (eo_ - ex);
       const RC eh = (RC)0.5 * (eo_ + ex) + (qo - qx) * Ext2dGeo<RC>::ic(bf, ip);
-      if (MODE == 0) bf.Gb[ip] += bw * (double)Fe;
+      Fe[ed * 2 + gs] = fe;
       const RC gq = g * Ho * eh;
-      Re[a0] -= hl * b0 * Fe; Re[a1] -= hl * b1 * Fe;
+      Re[a0] -= hl * b0 * fe; Re[a1] -= hl * b1 * fe;
       RU[a0] -= hl * b0 * gq * nx; RU[a1] -= hl * b1 * gq * nx;
       RV[a0] -= hl * b0 * gq * ny; RV[a1] -= hl * b1 * gq * ny;
     }
   }
+}
+
+template <int MODE, typename RC>
+__global__ void __launch_bounds__(256)
+    k_ext2d(DevMesh m, SplitBufs bf, Ext2dIO io, double g_, int tide_idx, double alpha, double beta,
+            double dt, double bw) {
+  const int nt = m.n_tri;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  RC Re[3], RU[3], RV[3], Fe[6];
+  ext2d_residual<RC>(m, bf, (const RC*)io.er, (const RC*)io.Ur, (const RC*)io.Vr, (RC)g_,
+                     (RC)bf.tide[tide_idx], t, Re, RU, RV, Fe);
   if (MODE == 1) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -541,6 +554,11 @@ __global__ void __launch_bounds__(256)
       io.eo[(6 + a) * nt + t] = (double)RV[a];
     }
     return;
+  }
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const int ip = ((j >> 1) * nt + t) * 2 + (j & 1);
+    bf.Gb[ip] += bw * (double)Fe[j];
   }
   // new = alpha start + beta stage + (beta dt / w) R, the increment in RC
   const RC bdw = (RC)(beta * dt) * (RC)bf.iw6[t];
@@ -562,6 +580,90 @@ __global__ void __launch_bounds__(256)
       ((RC*)io.eor)[ia] = (RC)e_new;
       ((RC*)io.Uor)[ia] = (RC)U_new;
       ((RC*)io.Vor)[ia] = (RC)V_new;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-form 2D subcycle (thread per triangle), SSP-RK3 written with the stage
+// increments D_s = dt M^-1 R(Q_s) evaluated in FP32 at FP32 stage values:
+//   Q_2 = Q^n + D_1,  Q_3 = Q^n + (D_1 + D_2)/4,
+//   Q^{n+1} = Q^n + (D_1 + D_2)/6 + 2 D_3/3,
+// which is the Shu-Osher form of the FP64 kernel rearranged exactly.  The stage
+// values only feed the FP32 residual, so they are kept in FP32; the FP64 state
+// Q^n is touched once per subcycle, by the last stage.  The Butcher-weighted
+// averages of the subcycle, (Q_1 + Q_2 + 4 Q_3)/6 = Q^n + (2 D_1 + D_2)/6 and
+// (F_1 + F_2 + 4 F_3)/6 for the edge eta flux, are added to the FP64 sums Qbar
+// and Gbar by the last stage as well.
+//   KIND 0: residual at Q^n (shadow), Dacc = D_1, out = Q_2, Gacc = F_1
+//   KIND 1: residual at Q_2, Dacc = D_1 + D_2, Eacc = (2 D_1 + D_2)/6 (U, V),
+//           out = Q_3, Gacc = F_1 + F_2
+//   KIND 2: residual at Q_3; FP64 Q^n += Dacc/6 + 2 D_3/3, out = shadow of it;
+//           Qbar += wn (Q^n + Eacc), Gbar += (Gacc + 4 F_3) wq
+// ---------------------------------------------------------------------------
+struct Mx2dIO {
+  const float *er, *Ur, *Vr;     // stage value
+  const float *en, *Un, *Vn;     // subcycle start (FP32 shadow)
+  float *eo, *Uo, *Vo;           // next stage value / new shadow
+  double *e, *U, *V;             // FP64 subcycle start, updated in place by KIND 2
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(256)
+    k_ext2d_mx(DevMesh m, SplitBufs bf, Mx2dIO io, float g, int tide_idx, float dt, float wq,
+               double wn) {
+  const int nt = m.n_tri;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  float Re[3], RU[3], RV[3], Fe[6];
+  ext2d_residual<float>(m, bf, io.er, io.Ur, io.Vr, g, bf.tide_f[tide_idx], t, Re, RU, RV, Fe);
+  const float bdw = dt * bf.iw6_f[t];
+  const float* S3x = (const float*)bf.S3x_r;
+  const float* S3y = (const float*)bf.S3y_r;
+  const size_t n2 = (size_t)3 * nt;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const int ip = ((j >> 1) * nt + t) * 2 + (j & 1);
+    if (KIND == 0) bf.Gacc[ip] = Fe[j];
+    if (KIND == 1) bf.Gacc[ip] += Fe[j];
+    if (KIND == 2) bf.Gb[ip] += (double)((bf.Gacc[ip] + 4.0f * Fe[j]) * wq);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int ia = a * nt + t;
+    const float d[3] = {bdw * Re[a], bdw * (RU[a] + S3x[ia]), bdw * (RV[a] + S3y[ia])};
+    if (KIND == 0) {
+      const float q[3] = {io.en[ia], io.Un[ia], io.Vn[ia]};
+      float* o[3] = {io.eo, io.Uo, io.Vo};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        bf.Dacc[c * n2 + ia] = d[c];
+        o[c][ia] = q[c] + d[c];
+      }
+    } else if (KIND == 1) {
+      const float q[3] = {io.en[ia], io.Un[ia], io.Vn[ia]};
+      float* o[3] = {io.eo, io.Uo, io.Vo};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float d1 = bf.Dacc[c * n2 + ia];
+        const float s12 = d1 + d[c];
+        bf.Dacc[c * n2 + ia] = s12;
+        if (c > 0) bf.Eacc[(c - 1) * n2 + ia] = (d1 + s12) * (1.0f / 6.0f);
+        o[c][ia] = q[c] + 0.25f * s12;
+      }
+    } else {
+      double* x[3] = {io.e, io.U, io.V};
+      float* o[3] = {io.eo, io.Uo, io.Vo};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double qn = x[c][ia];
+        if (c == 1) bf.Qbx[ia] += wn * (qn + (double)bf.Eacc[ia]);
+        if (c == 2) bf.Qby[ia] += wn * (qn + (double)bf.Eacc[n2 + ia]);
+        const float inc = bf.Dacc[c * n2 + ia] * (1.0f / 6.0f) + d[c] * (2.0f / 3.0f);
+        const double qnew = qn + (double)inc;
+        x[c][ia] = qnew;
+        o[c][ia] = (float)qnew;
+      }
     }
   }
 }
@@ -967,26 +1069,43 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, int tide_base,
   const int blk = 256, grd = (nt + blk - 1) / blk;
   double* F[3][3] = {{b->Ae, b->AU, b->AV}, {b->Be, b->BU, b->BV}, {b->Ce, b->CU, b->CV}};
   void* Fr[3][3] = {{b->Ae_r, b->AU_r, b->AV_r}, {b->Be_r, b->BU_r, b->BV_r}, {b->Ce_r, b->CU_r, b->CV_r}};
-  for (int q = 0; q < n_sub; ++q) {
-    for (int st = 0; st < 3; ++st) {
-      const int si = st, so = (st + 1) % 3;  // A -> B -> C -> A
-      const int tide_idx = tide_base + 3 * q + st;
-      Ext2dIO io;
-      io.e = F[si][0]; io.U = F[si][1]; io.V = F[si][2];
-      io.er = shadow ? Fr[si][0] : F[si][0];
-      io.Ur = shadow ? Fr[si][1] : F[si][1];
-      io.Vr = shadow ? Fr[si][2] : F[si][2];
-      io.en = b->Ae; io.Un = b->AU; io.Vn = b->AV;
-      io.eo = F[so][0]; io.Uo = F[so][1]; io.Vo = F[so][2];
-      io.eor = shadow ? Fr[so][0] : nullptr;
-      io.Uor = shadow ? Fr[so][1] : nullptr;
-      io.Vor = shadow ? Fr[so][2] : nullptr;
-      ProfScope ps(s, SLIM_PHASE_EXT2D, stm);
-      if (sizeof(R) == 8)
-        k_ext2d<0, double><<<grd, blk, 0, stm>>>(m, *b, io, s->par.g, tide_idx, A_[st], B_[st], dts, bw_[st] / n_sub);
-      else
-        k_ext2d<0, float><<<grd, blk, 0, stm>>>(m, *b, io, s->par.g, tide_idx, A_[st], B_[st], dts, bw_[st] / n_sub);
-      SLIM_CU(cudaGetLastError());
+  if (!shadow) {
+    for (int q = 0; q < n_sub; ++q) {
+      for (int st = 0; st < 3; ++st) {
+        const int si = st, so = (st + 1) % 3;  // A -> B -> C -> A
+        const int tide_idx = tide_base + 3 * q + st;
+        Ext2dIO io;
+        io.e = F[si][0]; io.U = F[si][1]; io.V = F[si][2];
+        io.er = F[si][0]; io.Ur = F[si][1]; io.Vr = F[si][2];
+        io.en = b->Ae; io.Un = b->AU; io.Vn = b->AV;
+        io.eo = F[so][0]; io.Uo = F[so][1]; io.Vo = F[so][2];
+        io.eor = io.Uor = io.Vor = nullptr;
+        ProfScope ps(s, SLIM_PHASE_EXT2D, stm);
+        k_ext2d<0, double><<<grd, blk, 0, stm>>>(m, *b, io, s->par.g, tide_idx, A_[st], B_[st], dts,
+                                                 bw_[st] / n_sub);
+        SLIM_CU(cudaGetLastError());
+      }
+    }
+  } else {
+    // FP32 stage values in the B and C shadows, FP64 state in A (updated by KIND 2)
+    const float gf = (float)s->par.g, dtf = (float)dts, wq = (float)(1.0 / (6.0 * n_sub));
+    const double wn = 1.0 / n_sub;
+    const float* A3[3] = {(const float*)b->Ae_r, (const float*)b->AU_r, (const float*)b->AV_r};
+    for (int q = 0; q < n_sub; ++q) {
+      for (int st = 0; st < 3; ++st) {
+        const int tide_idx = tide_base + 3 * q + st;
+        Mx2dIO io;
+        io.en = A3[0]; io.Un = A3[1]; io.Vn = A3[2];
+        io.e = b->Ae; io.U = b->AU; io.V = b->AV;
+        const int so = (st + 1) % 3;  // A -> B -> C -> A
+        io.er = (const float*)Fr[st][0]; io.Ur = (const float*)Fr[st][1]; io.Vr = (const float*)Fr[st][2];
+        io.eo = (float*)Fr[so][0]; io.Uo = (float*)Fr[so][1]; io.Vo = (float*)Fr[so][2];
+        ProfScope ps(s, SLIM_PHASE_EXT2D, stm);
+        if (st == 0) k_ext2d_mx<0><<<grd, blk, 0, stm>>>(m, *b, io, gf, tide_idx, dtf, wq, wn);
+        if (st == 1) k_ext2d_mx<1><<<grd, blk, 0, stm>>>(m, *b, io, gf, tide_idx, dtf, wq, wn);
+        if (st == 2) k_ext2d_mx<2><<<grd, blk, 0, stm>>>(m, *b, io, gf, tide_idx, dtf, wq, wn);
+        SLIM_CU(cudaGetLastError());
+      }
     }
   }
   {
@@ -1108,17 +1227,32 @@ slim_status split_alloc(slim_state* s) {
     SLIM_CU(cudaMalloc((void**)p, n2 * 2 * sizeof(float)));
     s->allocs.push_back(*p);
   }
-  SLIM_CU(cudaMalloc((void**)&b->tide, (size_t)(3 * (s->par.n_sub / 2 + s->par.n_sub) + 1) * 8));
+  const size_t n_tide = (size_t)3 * (s->par.n_sub / 2 + s->par.n_sub);
+  SLIM_CU(cudaMalloc((void**)&b->tide, (n_tide + 1) * 8 + n_tide * sizeof(float)));
+  SLIM_CU(cudaMemset(b->tide, 0, (n_tide + 1) * 8 + n_tide * sizeof(float)));
   s->allocs.push_back(b->tide);
+  b->tide_f = reinterpret_cast<float*>(b->tide + n_tide + 1);
   SLIM_CU(cudaMalloc((void**)&b->iw6, (size_t)m.n_tri * 8));
   s->allocs.push_back(b->iw6);
+  SLIM_CU(cudaMalloc((void**)&b->iw6_f, (size_t)m.n_tri * sizeof(float)));
+  s->allocs.push_back(b->iw6_f);
+  b->Dacc = b->Eacc = b->Gacc = nullptr;
+  if (s->esz == 4) {
+    float** fa[] = {&b->Dacc, &b->Eacc, &b->Gacc};
+    const size_t cnt[] = {3 * n2, 2 * n2, 2 * n2};
+    for (int j = 0; j < 3; ++j) {
+      SLIM_CU(cudaMalloc((void**)fa[j], cnt[j] * sizeof(float)));
+      SLIM_CU(cudaMemset(*fa[j], 0, cnt[j] * sizeof(float)));
+      s->allocs.push_back(*fa[j]);
+    }
+  }
   b->Qbx = s->Qbx;
   b->Qby = s->Qby;
   SLIM_CU(cudaMalloc(&b->gcor_r, n2 * 2 * s->esz));
   SLIM_CU(cudaMemset(b->gcor_r, 0, n2 * 2 * s->esz));
   s->allocs.push_back(b->gcor_r);
   const int grd = (m.n_tri + 255) / 256;
-  k_wave_speed<<<grd, 256>>>(m, s->par.g, b->cw, b->icw, b->cw_f, b->icw_f, b->iw6);
+  k_wave_speed<<<grd, 256>>>(m, s->par.g, b->cw, b->icw, b->cw_f, b->icw_f, b->iw6, b->iw6_f);
   SLIM_CU(cudaGetLastError());
   return SLIM_OK;
 }
