@@ -170,7 +170,10 @@ KERNEL_OF = {"split": {"continuity": "k_cont_split", "hpg": "k_hpg", "mom_pred":
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
 # capture, valid only while the kernel sources hash to ``src``; see profiles/.
-TRAFFIC = {}
+TRAFFIC = {
+    ("k_update", "mixed", "basin_baroclinic"): dict(bytes=726.6e6, src="89bb1051f68c5eac"),
+    ("k_update", "fp64", "basin_baroclinic"): dict(bytes=1418.4e6, src="89bb1051f68c5eac"),
+}
 KSRC = ["paper_2605_16082_gb300/csrc/slim_split.cu", "paper_2605_16082_gb300/csrc/slim_split_device.cuh",
         "paper_2605_16082_gb300/csrc/slim_device.cuh", "paper_2605_16082_gb300/csrc/slim_tracer.cu",
         "paper_2605_16082_gb300/csrc/slim_internal.h"]

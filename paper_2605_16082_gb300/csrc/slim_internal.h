@@ -65,6 +65,10 @@ struct DevMesh {
   const float* enx_f;
   const float* eny_f;
   const float* elen_f;
+  // [3][n_tri] 1 / min(r_in^-, r_in^+) of interior edges (0 elsewhere): the SIPG
+  // penalty length of the horizontal diffusion
+  const double* esig;
+  const float* esig_f;
 };
 
 // Event pair around one kernel launch while profiling is on.

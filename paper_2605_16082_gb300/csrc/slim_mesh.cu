@@ -199,6 +199,14 @@ extern "C" slim_status slim_mesh_create(const double* xy, int n_vert, const int*
       einfo[e * nt + t] = nb >= 0 ? make_int4(nb, col_off[nb], col_off[nb + 1] - col_off[nb], nloc[e * nt + t])
                                   : make_int4(nb, 0, 0, 0);
     }
+  // horizontal interior-penalty length per edge: 1 / min(r_in^-, r_in^+), 0 off interior edges
+  std::vector<double> esig(3 * (size_t)nt, 0.0);
+  for (int e = 0; e < 3; ++e)
+    for (int t = 0; t < nt; ++t) {
+      const int nb = nbr[e * nt + t];
+      if (nb >= 0) esig[e * nt + t] = 1.0 / std::min(rin[t], rin[nb]);
+    }
+  std::vector<float> esigf(esig.begin(), esig.end());
   std::vector<double> lev;
   if (levels) lev.assign(levels, levels + n_levels);
   std::vector<double> hN(3 * nt), ih(3 * nt);
@@ -256,6 +264,8 @@ extern "C" slim_status slim_mesh_create(const double* xy, int n_vert, const int*
   UP(enxf, enx_f);
   UP(enyf, eny_f);
   UP(elenf, elen_f);
+  UP(esig, esig);
+  UP(esigf, esig_f);
 #undef UP
   if (!levels) { d.levels = nullptr; d.levels_f = nullptr; }
   m->col_off_h = col_off;

@@ -680,20 +680,21 @@ __global__ void k_couple2d(DevMesh m, const double* __restrict__ e1, const doubl
                            const double* __restrict__ S3y, const double* __restrict__ Sqx,
                            const double* __restrict__ Sqy, const double* __restrict__ Qbx,
                            const double* __restrict__ Qby, const double* __restrict__ Gb,
-                           const R* __restrict__ st_ev, double T, double* __restrict__ F2x,
+                           const R* __restrict__ st_ev, const double* __restrict__ iw6, double T,
+                           double iT, double* __restrict__ F2x,
                            double* __restrict__ F2y, R* __restrict__ F2x_r, R* __restrict__ F2y_r,
                            R* __restrict__ Dqx_r, R* __restrict__ Dqy_r, R* __restrict__ gcor_r,
                            R* __restrict__ st_end) {
   const int nt = m.n_tri;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
-  const double w6 = m.jh[t] * (1.0 / 6.0);
+  const double iw = iw6[t];  // 1 / (J_h/6)
   const int N = m.col_off[t + 1] - m.col_off[t];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int ia = a * nt + t;
-    const double fx = (U1[ia] - (U0[ia] + T * S3x[ia] / w6)) / T;
-    const double fy = (V1[ia] - (V0[ia] + T * S3y[ia] / w6)) / T;
+    const double fx = (U1[ia] - (U0[ia] + T * (S3x[ia] * iw))) * iT;
+    const double fy = (V1[ia] - (V0[ia] + T * (S3y[ia] * iw))) * iT;
     F2x[ia] = fx; F2y[ia] = fy;
     F2x_r[ia] = (R)fx; F2y_r[ia] = (R)fy;
     Dqx_r[ia] = (R)(Qbx[ia] - Sqx[ia]);
@@ -727,7 +728,9 @@ __global__ void k_couple2d(DevMesh m, const double* __restrict__ e1, const doubl
           Qavg = 0.5 * (Qo + Qn);
           tot += b0 * paired(j0, ei.z, Np) * (double)st_ev[j0] + b1 * paired(j1, ei.z, Np) * (double)st_ev[j1];
         }
-        g = (Gb[(ed * nt + t) * 2 + gs] - Qavg) / tot;
+        const double dG = Gb[(ed * nt + t) * 2 + gs] - Qavg;
+        // the result is stored in R: the mixed form divides in FP32
+        g = sizeof(R) == 8 ? dG / tot : (double)((float)dG / (float)tot);
       }
       gcor_r[(ed * nt + t) * 2 + gs] = (R)g;
     }
@@ -1111,7 +1114,8 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, int tide_base,
   {
     ProfScope ps(s, SLIM_PHASE_MISC, stm);
     k_couple2d<R><<<grd, blk, 0, stm>>>(m, b->Ae, b->AU, b->AV, s->Qx, s->Qy, b->S3x, b->S3y, b->Sqx,
-                                        b->Sqy, s->Qbx, s->Qby, b->Gb, st_ev, dt, b->F2x, b->F2y,
+                                        b->Sqy, s->Qbx, s->Qby, b->Gb, st_ev, b->iw6, dt, 1.0 / dt,
+                                        b->F2x, b->F2y,
                                         (R*)b->F2x_r, (R*)b->F2y_r, (R*)b->Dqx_r, (R*)b->Dqy_r,
                                         (R*)b->gcor_r, (R*)b->st_end);
     SLIM_CU(cudaGetLastError());

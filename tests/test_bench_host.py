@@ -21,7 +21,7 @@ def test_update_instances_are_one_kernel(bench):
     m = types.SimpleNamespace(n_prisms=1000, n_tri=50)
     # momentum and tracers are two instances of k_update: together they dominate
     r = dict(phases={"ext2d": (3.0, 90), "momentum": (2.0, 2), "tracers": (2.0, 2), "hpg": (0.5, 2)})
-    head, allk = bench.rooflines(r, m, "split", "mixed", "basin_baroclinic", 6657.6, "measured")
+    head, allk = bench.rooflines(r, m, "split", "mixed", "no_capture_workload", 6657.6, "measured")
     assert head["kernel"] == "k_update"
     assert allk["k_update"]["launches"] == 4
     per = bench.phase_bytes("momentum", m, 4, 0)
