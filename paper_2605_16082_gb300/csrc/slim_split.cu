@@ -351,10 +351,7 @@ __device__ __forceinline__ void momentum_extras(const DevMesh& m, int t, int k, 
                                                 const R* __restrict__ Rx, const R* __restrict__ Ry,
                                                 const PP<R>& pp, R Fx[2][3], R Fy[2][3]) {
   const int nt = m.n_tri, P = m.P;
-  if (pp.nu_h > (R)0) {
-    prism_sipg<R>(m, t, k, N, own.u, U, st, pp.nu_h, pp.pen_h, Fx);
-    prism_sipg<R>(m, t, k, N, own.v, V, st, pp.nu_h, pp.pen_h, Fy);
-  }
+  if (pp.nu_h > (R)0) prism_sipg2<R>(m, t, k, N, own.u, own.v, U, V, st, pp.nu_h, pp.pen_h, Fx, Fy);
   const R f = pp.f, irho = pp.irho0;
   const R w6 = Geo<R>::jh(m, t) * (R)(1.0 / 6.0);
 #pragma unroll
@@ -844,8 +841,7 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
     if (KIND == 0) {
       momentum_extras<R>(m, t, k, p, N, own, in.U, in.V, in.st, Rx, Ry, pp, F0, F1);
     } else if (ua.kap_h > (R)0) {
-      prism_sipg<R>(m, t, k, N, own.f0, in.F0, in.st, ua.kap_h, pp.pen_h, F0);
-      prism_sipg<R>(m, t, k, N, own.f1, in.F1, in.st, ua.kap_h, pp.pen_h, F1);
+      prism_sipg2<R>(m, t, k, N, own.f0, own.f1, in.F0, in.F1, in.st, ua.kap_h, pp.pen_h, F0, F1);
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {

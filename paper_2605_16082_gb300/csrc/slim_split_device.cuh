@@ -211,14 +211,18 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
   }
 }
 
-// Horizontal SIPG of one field on coordinate surfaces (weight nu z_zeta):
+// Horizontal SIPG of two fields on coordinate surfaces (weight nu z_zeta):
 //   -int nu z_zeta grad f . grad v + oint [{nu z_zeta grad f}.n v
 //                                          + 1/2 nu z_zeta^- grad v.n [f] - sigma {z_zeta}[f] v]
 // sigma = pen nu / min(r_in^-, r_in^+), interior faces only (natural elsewhere).
+// The two fields share the geometry: the layer thicknesses, the penalty and the
+// normal derivatives of both triangles' basis functions (the gradient of a P1
+// field dotted with n is the sum of its nodal values times those derivatives).
 template <typename R>
-__device__ __forceinline__ void prism_sipg(const DevMesh& m, int t, int k, int N, const R f[2][3],
-                                           const R* __restrict__ F, const R* __restrict__ st,
-                                           R nu, R pen, R out[2][3]) {
+__device__ __forceinline__ void prism_sipg2(const DevMesh& m, int t, int k, int N, const R f0[2][3],
+                                            const R f1[2][3], const R* __restrict__ F0,
+                                            const R* __restrict__ F1, const R* __restrict__ st,
+                                            R nu, R pen, R out0[2][3], R out1[2][3]) {
   const int nt = m.n_tri, P = m.P;
   R gx[3], gy[3], hz[3];
 #pragma unroll
@@ -227,25 +231,30 @@ __device__ __forceinline__ void prism_sipg(const DevMesh& m, int t, int k, int N
     gy[a] = Geo<R>::gy(m, a * nt + t);
     hz[a] = (R)0.5 * dz_rest_r<R>(m, a * nt + t, k, N) * st[a * nt + t];
   }
-  R gux[2], guy[2];
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    gux[c] = f[c][0] * gx[0] + f[c][1] * gx[1] + f[c][2] * gx[2];
-    guy[c] = f[c][0] * gy[0] + f[c][1] * gy[1] + f[c][2] * gy[2];
-  }
+  const R(*fs[2])[3] = {f0, f1};
+  R(*outs[2])[3] = {out0, out1};
   // volume: -nu (J_h/6)(sum hz) sum_d G_dc grad f_d . grad phi_a
   {
     const R w = nu * Geo<R>::jh(m, t) * (R)(1.0 / 6.0) * (hz[0] + hz[1] + hz[2]);
     const R G2 = (R)(2.0 / 3.0), G1 = (R)(1.0 / 3.0);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const R d0 = gux[0] * gx[a] + guy[0] * gy[a];
-      const R d1 = gux[1] * gx[a] + guy[1] * gy[a];
-      out[0][a] -= w * (G2 * d0 + G1 * d1);
-      out[1][a] -= w * (G1 * d0 + G2 * d1);
+    for (int q = 0; q < 2; ++q) {
+      R gux[2], guy[2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        gux[c] = fs[q][c][0] * gx[0] + fs[q][c][1] * gx[1] + fs[q][c][2] * gx[2];
+        guy[c] = fs[q][c][0] * gy[0] + fs[q][c][1] * gy[1] + fs[q][c][2] * gy[2];
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const R d0 = gux[0] * gx[a] + guy[0] * gy[a];
+        const R d1 = gux[1] * gx[a] + guy[1] * gy[a];
+        outs[q][0][a] -= w * (G2 * d0 + G1 * d1);
+        outs[q][1][a] -= w * (G1 * d0 + G2 * d1);
+      }
     }
   }
-  const R rin_t = (sizeof(R) == 4) ? (R)m.rin_f[t] : (R)m.rin[t];
+  const R* Fs[2] = {F0, F1};
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     const int4 ei = m.einfo[e * nt + t];
@@ -259,24 +268,15 @@ __device__ __forceinline__ void prism_sipg(const DevMesh& m, int t, int k, int N
     const int a0 = e, a1 = (e + 1) % 3;
     const R nxe = Geo<R>::nx(m, e * nt + t), nye = Geo<R>::ny(m, e * nt + t);
     const R half_len = (R)0.5 * Geo<R>::len(m, e * nt + t);
-    R fn[2][3];
-    R gnx[2] = {0, 0}, gny[2] = {0, 0};
+    const R isig = (sizeof(R) == 4) ? (R)m.esig_f[e * nt + t] : (R)m.esig[e * nt + t];
+    R dno[3], dnn[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      const R gxb = Geo<R>::gx(m, b * nt + nb), gyb = Geo<R>::gy(m, b * nt + nb);
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        fn[c][b] = F[(size_t)(c * 3 + b) * P + pn];
-        gnx[c] += fn[c][b] * gxb;
-        gny[c] += fn[c][b] * gyb;
-      }
+      dno[b] = gx[b] * nxe + gy[b] * nye;
+      dnn[b] = Geo<R>::gx(m, b * nt + nb) * nxe + Geo<R>::gy(m, b * nt + nb) * nye;
     }
     const R hzn0 = (R)0.5 * dz_rest_r<R>(m, l0 * nt + nb, k, Nn) * st[l0 * nt + nb];
     const R hzn1 = (R)0.5 * dz_rest_r<R>(m, l1 * nt + nb, k, Nn) * st[l1 * nt + nb];
-    const R rin_n = (sizeof(R) == 4) ? (R)m.rin_f[nb] : (R)m.rin[nb];
-    const R sig = pen * nu / fmin(rin_t, rin_n);
-    const R gno[2] = {gux[0] * nxe + guy[0] * nye, gux[1] * nxe + guy[1] * nye};
-    const R gnn[2] = {gnx[0] * nxe + gny[0] * nye, gnx[1] * nxe + gny[1] * nye};
     // The face integrals are polynomials of degree <= 3 per direction, integrated
     // exactly in closed form: with the edge basis b_i and psi_c,
     //   int b_i b_j = E2_ij (2/3, 1/3), int b_i b_j b_k = 1/2 (all equal) or 1/6,
@@ -285,33 +285,48 @@ __device__ __forceinline__ void prism_sipg(const DevMesh& m, int t, int k, int N
     const R hzo[2] = {hz[a0], hz[a1]}, hzn[2] = {hzn0, hzn1};
     const R Zo[2] = {t3 * ((R)2 * hzo[0] + hzo[1]), t3 * ((R)2 * hzo[1] + hzo[0])};
     const R Zn[2] = {t3 * ((R)2 * hzn[0] + hzn[1]), t3 * ((R)2 * hzn[1] + hzn[0])};
-    const R Go[2] = {t3 * ((R)2 * gno[0] + gno[1]), t3 * ((R)2 * gno[1] + gno[0])};
-    const R Gn[2] = {t3 * ((R)2 * gnn[0] + gnn[1]), t3 * ((R)2 * gnn[1] + gnn[0])};
-    // jumps at the face nodes (own vertex j <-> neighbour vertex l_j), G-weighted in zeta
-    R J[2][2], gJ[2][2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      J[0][c] = f[c][a0] - fn[c][l0];
-      J[1][c] = f[c][a1] - fn[c][l1];
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      gJ[i][0] = t3 * ((R)2 * J[i][0] + J[i][1]);
-      gJ[i][1] = t3 * ((R)2 * J[i][1] + J[i][0]);
-    }
     const R hs0 = hzo[0] + hzn[0], hs1 = hzo[1] + hzn[1];
     const R M00 = (R)0.5 * hs0 + t6 * hs1, M11 = (R)0.5 * hs1 + t6 * hs0, M01 = t6 * (hs0 + hs1);
     const R hnu = half_len * (R)0.5 * nu;
-    const R hsig = half_len * (R)0.5 * sig;
+    const R hsig = half_len * (R)0.5 * pen * nu * isig;
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const R zj = Zo[0] * gJ[0][c] + Zo[1] * gJ[1][c];
-      // flux {nu z_zeta grad f}.n tested with the edge functions, minus the penalty
-      out[c][a0] += hnu * (Zo[0] * Go[c] + Zn[0] * Gn[c]) - hsig * (M00 * gJ[0][c] + M01 * gJ[1][c]);
-      out[c][a1] += hnu * (Zo[1] * Go[c] + Zn[1] * Gn[c]) - hsig * (M01 * gJ[0][c] + M11 * gJ[1][c]);
-      // symmetry term 1/2 nu z_zeta grad v.n [f] for every own test function
+    for (int q = 0; q < 2; ++q) {
+      const R(*f)[3] = fs[q];
+      R fn[2][3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) out[c][a] += hnu * (gx[a] * nxe + gy[a] * nye) * zj;
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) fn[c][b] = Fs[q][(size_t)(c * 3 + b) * P + pn];
+      R gno[2], gnn[2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        gno[c] = f[c][0] * dno[0] + f[c][1] * dno[1] + f[c][2] * dno[2];
+        gnn[c] = fn[c][0] * dnn[0] + fn[c][1] * dnn[1] + fn[c][2] * dnn[2];
+      }
+      const R Go[2] = {t3 * ((R)2 * gno[0] + gno[1]), t3 * ((R)2 * gno[1] + gno[0])};
+      const R Gn[2] = {t3 * ((R)2 * gnn[0] + gnn[1]), t3 * ((R)2 * gnn[1] + gnn[0])};
+      // jumps at the face nodes (own vertex j <-> neighbour vertex l_j), G-weighted in zeta
+      R J[2][2], gJ[2][2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        J[0][c] = f[c][a0] - fn[c][l0];
+        J[1][c] = f[c][a1] - fn[c][l1];
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        gJ[i][0] = t3 * ((R)2 * J[i][0] + J[i][1]);
+        gJ[i][1] = t3 * ((R)2 * J[i][1] + J[i][0]);
+      }
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const R zj = hnu * (Zo[0] * gJ[0][c] + Zo[1] * gJ[1][c]);
+        // flux {nu z_zeta grad f}.n tested with the edge functions, minus the penalty
+        outs[q][c][a0] += hnu * (Zo[0] * Go[c] + Zn[0] * Gn[c]) - hsig * (M00 * gJ[0][c] + M01 * gJ[1][c]);
+        outs[q][c][a1] += hnu * (Zo[1] * Go[c] + Zn[1] * Gn[c]) - hsig * (M01 * gJ[0][c] + M11 * gJ[1][c]);
+        // symmetry term 1/2 nu z_zeta grad v.n [f] for every own test function
+#pragma unroll
+        for (int a = 0; a < 3; ++a) outs[q][c][a] += dno[a] * zj;
+      }
     }
   }
 }
