@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--tile", type=int, default=0, help="prisms per block without the autotuner")
     ap.add_argument("--occ", type=int, default=0, help="blocks per SM without the autotuner")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the 1000-step mixed-error run")
     return ap.parse_args()
 
 
@@ -317,6 +318,30 @@ def run_ours(args, rank: int, world: int):
     return m, res, clocks
 
 
+def mixed_accuracy(steps: int = 1000) -> dict:
+    """Mixed against FP64 on the square-basin tracer run (2048 triangles x 10
+    layers, dt = 5 s) after ``steps`` steps: tracer relative L2 error and the tracer
+    mass drift of both forms (outside the timed region)."""
+    from paper_2605_16082_gb300 import slim
+    W = wl.WORKLOADS["square_tracer"]
+    m = W["mesh"]()
+    u, v = wl.c1_velocity(m)
+    T = wl.c1_tracer(m)
+    out = {}
+    for pname, prec in (("fp64", slim.SLIM_FP64), ("mixed", slim.SLIM_MIXED)):
+        with slim.Model(m, prec, slim.slim_params_default(kappa_v=W["kappa_v"])) as mod:
+            for k, f in (("U", u), ("V", v), ("T", T), ("ETA", np.zeros(3 * m.n_tri))):
+                mod.upload(k, f)
+            m0 = slim.slim_tracer_mass(mod.state, 0)
+            for n in range(steps):
+                slim.slim_step(mod.state, n * W["dt"], W["dt"])
+            out[pname] = (mod.download("T"), (slim.slim_tracer_mass(mod.state, 0) - m0) / m0)
+    a, b = out["mixed"][0], out["fp64"][0]
+    return dict(workload="square_tracer", steps=steps,
+                tracer_rel_l2_mixed_vs_fp64=float(np.linalg.norm(a - b) / np.linalg.norm(b)),
+                bar=1e-5, mass_drift_mixed=float(out["mixed"][1]), mass_drift_fp64=float(out["fp64"][1]))
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -448,6 +473,8 @@ def main():
                             e2e=f.get("e2e"), phases_ms={k: v[0] for k, v in f["phases"].items()},
                             device_bytes=f["device_bytes"],
                             tiling=dict(prisms_per_block=f["tile_prisms"], blocks_per_sm=f["blocks_per_sm"]))
+    if not args.no_accuracy and "mixed" in res:
+        line["mixed_accuracy"] = mixed_accuracy()
     if not args.no_cpu:
         line["cpu_baseline"] = oracle_sample(args, m, args.cpu_seconds)
     print(json.dumps(line))

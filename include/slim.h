@@ -112,8 +112,10 @@ typedef struct slim_params {
   int n_sub;           /* external-mode steps per internal step (split)    */
   int tile_prisms;     /* prisms per thread block (0 = default 256)        */
   int check_every;     /* slim_step checks the device error flag every n steps (0 = never) */
-  int blocks_per_sm;   /* register budget of the heavy split kernels: 2 or 4 resident
-                          blocks of 256 threads per SM (0 = default 4)            */
+  int blocks_per_sm;   /* register budget of the heavy split kernels of the mixed form:
+                          2, 3 or 4 resident blocks of 256 threads per SM (0 = default
+                          4; 3 is taken as 2 with 512-prism tiles; the FP64 form
+                          always uses 2)                                          */
   int use_graph;       /* 1: slim_step replays one CUDA graph of the whole step (captured
                           on the first call and again whenever dt changes; only the
                           step's start time is updated between replays); 0: launches
@@ -260,6 +262,15 @@ slim_status slim_tracer_mass(slim_state* s, int field, double* mass_host, void* 
  * other states, other threads) race on it.  No cudaMalloc, cudaFree or
  * allocating library routine is called.  field: SLIM_FIELD_T or _S. */
 slim_status slim_tracer_mass_noalloc(slim_state* s, int field, double* mass_dev, void* stream);
+
+/* slim_selftest_conversions: diagnostic (no counterpart in the paper).  Runs the
+ * library's integer-pipe binary32 <-> binary64 conversions (used by the mixed
+ * form's 2D update) on n seeded bit patterns of every class (normal, subnormal,
+ * zero, infinity, NaN, exact rounding ties) and counts the results that differ
+ * from the GPU's own conversions (NaN compared as NaN).  Synchronises; writes the
+ * two counts to host memory. */
+slim_status slim_selftest_conversions(long long n, unsigned long long seed, long long* bad_d2f,
+                                      long long* bad_f2d);
 
 /* Number of kernels slim_step launches per call (for launch accounting). */
 int slim_step_kernel_count(const slim_state* s);

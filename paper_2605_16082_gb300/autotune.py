@@ -1,6 +1,7 @@
 """Autotuner of the launch tiling: prisms per thread block (the tile of whole
 columns each block owns: 128, 256 or 512) and the register budget of the heavy
-split-step kernels (2 or 4 resident blocks of 256 threads per SM).
+split-step kernels (2, 3 or 4 resident blocks of 256 threads per SM in the mixed
+form; the FP64 form has one budget).
 
 Every candidate is a separate mesh tiling and state; each runs a few warm-up
 steps and is timed over a few steps with CUDA events on the current stream.  The
@@ -18,7 +19,7 @@ import numpy as np
 from . import slim
 
 TILES = (128, 256, 512)
-OCCS = (2, 4)
+OCCS = (2, 3, 4)
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "slim_gb300_autotune.json")
 
 
@@ -86,10 +87,17 @@ def autotune(mesh, precision: int, params, fields: dict, dt: float, use_cache: b
     cache = _load() if use_cache else {}
     if key in cache:
         return cache[key]
-    occs = OCCS if params.scheme == slim.SLIM_SCHEME_SPLIT else (4,)
+    if params.scheme != slim.SLIM_SCHEME_SPLIT:
+        occs = (4,)
+    elif precision == slim.SLIM_FP64:
+        occs = (2,)                      # one register budget in the FP64 form
+    else:
+        occs = OCCS
     results = {}
     for tile in TILES:
         for occ in occs:
+            if occ == 3 and tile == 512:
+                continue
             ms = time_config(mesh, precision, params, fields, dt, tile, occ)
             results[f"{tile}/{occ}"] = ms
             if verbose:

@@ -113,8 +113,63 @@ template <> struct ColSum<float> {
 };
 
 // reciprocal: fast approximate for the FP32 form, exact division in FP64
+// IEEE 754 binary32 <-> binary64 conversions on the integer pipe (bit fields of
+// the two formats; exact in one direction, round-to-nearest-even in the other,
+// subnormals included).  The FP64 pipe of this GPU runs conversions at the FP64
+// rate; these keep it for the arithmetic of the mixed-form 2D update.
+__device__ __forceinline__ double f2d_bits(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned s = u & 0x80000000u, e = (u >> 23) & 0xffu, mt = u & 0x7fffffu;
+  unsigned hi, lo;
+  if (e != 0u && e != 255u) {                       // normal: rebias 127 -> 1023
+    hi = s | ((e + 896u) << 20) | (mt >> 3);
+    lo = mt << 29;
+  } else if (e == 255u) {                           // infinity / NaN (payload kept)
+    hi = s | 0x7ff00000u | (mt >> 3);
+    lo = mt << 29;
+  } else if (mt == 0u) {                            // signed zero
+    hi = s;
+    lo = 0u;
+  } else {                                          // subnormal: normalise
+    const int lz = __clz(mt) - 9;                   // leading zeros inside the 23-bit field
+    const unsigned mn = (mt << (lz + 1)) & 0x7fffffu;
+    hi = s | ((unsigned)(896 - lz) << 20) | (mn >> 3);
+    lo = mn << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ float d2f_bits(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned s = hi & 0x80000000u, mh = hi & 0xfffffu;
+  const int E = (int)((hi >> 20) & 0x7ffu);
+  unsigned f;
+  if (E > 896 && E < 1151) {                        // binary32 normal range
+    f = ((unsigned)(E - 896) << 23) | (mh << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu, half = 0x10000000u;
+    f += (rem > half || (rem == half && (f & 1u))) ? 1u : 0u;  // a carry may reach infinity
+  } else if (E == 2047) {                           // infinity / NaN
+    f = 0x7f800000u | (((mh | lo) != 0u) ? (0x400000u | (mh << 3) | (lo >> 29)) : 0u);
+  } else if (E >= 1151) {                           // overflow
+    f = 0x7f800000u;
+  } else {                                          // binary32 subnormal or zero
+    const int r = 926 - E;                          // right shift of the 53-bit significand
+    if (E == 0 || r >= 64) {
+      f = 0u;
+    } else {
+      const unsigned long long M = (1ull << 52) | ((unsigned long long)mh << 32) | lo;
+      const unsigned long long k = M >> r, rem = M & ((1ull << r) - 1ull), half = 1ull << (r - 1);
+      f = (unsigned)k + ((rem > half || (rem == half && (k & 1ull))) ? 1u : 0u);
+    }
+  }
+  return __uint_as_float(s | f);
+}
+
 template <typename R> __device__ __forceinline__ R rcp(R x);
-template <> __device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.0f, x); }
+// correctly rounded (IEEE) in both forms: the approximate reciprocal is biased,
+// and a biased inverse in the column solves and the inverse mass changes the tracer
+// mass by the same fraction every step
+template <> __device__ __forceinline__ float rcp<float>(float x) { return 1.0f / x; }
 template <> __device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
 
 // local triangle of local prism i (largest j with s_off[j] <= i)
@@ -301,10 +356,13 @@ struct Row {
   R D[2][2], L[2][2], U[2][2];
 };
 
-// idzm, idz, idzp: reciprocals of the thicknesses of layers k-1, k, k+1.
+// idzm, idz, idzp: reciprocals of the thicknesses of layers k-1, k, k+1.  With
+// op given, the operator blocks A (op->D), A_{k,k-1} (op->L) and A_{k,k+1} (op->U)
+// are returned as well (K = M - bdt A).
 template <typename R>
 __device__ __forceinline__ void assemble_row(int k, int N, R omega, R idzm, R dz, R idz, R idzp,
-                                             R W0, R W1, R Wn, R kap, R pen, R bdt, Row<R>& row) {
+                                             R W0, R W1, R Wn, R kap, R pen, R bdt, Row<R>& row,
+                                             Row<R>* op = nullptr) {
   R A[2][2] = {{0, 0}, {0, 0}}, AL[2][2] = {{0, 0}, {0, 0}}, AU[2][2] = {{0, 0}, {0, 0}};
   // advection, volume: A[c][d] = dpsi_c sum_e W_e G_ed
   const R g0 = (R)(1.0 / 3.0) * ((R)2 * W0 + W1);
@@ -339,6 +397,16 @@ __device__ __forceinline__ void assemble_row(int k, int N, R omega, R idzm, R dz
     AU[0][0] -= omega * (-c0);
     AU[1][0] -= omega * (c0 + cp - sg);
     AU[1][1] -= omega * (-cp);
+  }
+  if (op) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        op->D[i][j] = A[i][j];
+        op->L[i][j] = AL[i][j];
+        op->U[i][j] = AU[i][j];
+      }
   }
   const R mw = omega * (R)0.5 * dz;
   const R m2 = mw * (R)(2.0 / 3.0), m1 = mw * (R)(1.0 / 3.0);

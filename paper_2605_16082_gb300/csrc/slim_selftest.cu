@@ -1,0 +1,62 @@
+// Diagnostics of device building blocks against the compiler's own operations.
+#include <string>
+
+#include "slim_device.cuh"
+#include "slim_kernels.h"
+
+namespace slim {
+namespace {
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// i-th test pattern: raw bits (every class) or a double near the binary32 range
+__global__ void k_conv_check(long long n, unsigned long long seed, unsigned long long* bad) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long r = splitmix64(seed ^ (unsigned long long)i * 0xd1342543de82ef95ull);
+    unsigned long long db = r;
+    if (i & 1) {  // exponent within [866, 1156]: subnormal, normal and overflowing binary32
+      const unsigned long long E = 866 + (r >> 52) % 291;
+      db = (r & 0x800fffffffffffffull) | (E << 52);
+    }
+    if ((i & 7) == 2) db &= 0xffffffffe0000000ull | ((r >> 7) & 0x10000000ull);  // exact halves
+    const double x = __longlong_as_double((long long)db);
+    const float a = d2f_bits(x), b = (float)x;
+    const bool ok1 = (__float_as_uint(a) == __float_as_uint(b)) || (a != a && b != b);
+    const float y = __uint_as_float((unsigned)(r >> 17));
+    const double c = f2d_bits(y), d = (double)y;
+    const bool ok2 = (__double_as_longlong(c) == __double_as_longlong(d)) || (c != c && d != d);
+    if (!ok1) atomicAdd(&bad[0], 1ull);
+    if (!ok2) atomicAdd(&bad[1], 1ull);
+  }
+}
+
+}  // namespace
+}  // namespace slim
+
+using namespace slim;
+
+extern "C" slim_status slim_selftest_conversions(long long n, unsigned long long seed,
+                                                 long long* bad_d2f, long long* bad_f2d) {
+  clear_error();
+  if (n < 0 || !bad_d2f || !bad_f2d) { set_error("bad argument"); return SLIM_ERR_ARG; }
+  unsigned long long* d = nullptr;
+  cudaError_t e = cudaMalloc((void**)&d, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(d, 0, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess && n > 0) {
+    k_conv_check<<<4 * 152, 256>>>(n, seed, d);
+    e = cudaGetLastError();
+  }
+  unsigned long long h[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  if (d) cudaFree(d);
+  if (e != cudaSuccess) { set_error(std::string("selftest: ") + cudaGetErrorString(e)); return SLIM_ERR_CUDA; }
+  *bad_d2f = (long long)h[0];
+  *bad_f2d = (long long)h[1];
+  return SLIM_OK;
+}

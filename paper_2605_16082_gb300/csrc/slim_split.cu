@@ -46,16 +46,36 @@ struct MBO {
   static constexpr int value = (occ * 256 / TP) > 0 ? (occ * 256 / TP) : 1;
 };
 
-#define SLIM_TPO_SWITCH(TP, OC, ...)                                                   \
-  switch (TP * 10 + OC) {                                                              \
-    case 1282: { constexpr int TPc = 128, OCc = 2; __VA_ARGS__; } break;               \
-    case 1284: { constexpr int TPc = 128, OCc = 4; __VA_ARGS__; } break;               \
-    case 2562: { constexpr int TPc = 256, OCc = 2; __VA_ARGS__; } break;               \
-    case 2564: { constexpr int TPc = 256, OCc = 4; __VA_ARGS__; } break;               \
-    case 5122: { constexpr int TPc = 512, OCc = 2; __VA_ARGS__; } break;               \
-    case 5124: { constexpr int TPc = 512, OCc = 4; __VA_ARGS__; } break;               \
-    default: return cudaErrorInvalidValue;                                             \
+// Launch shapes TP x OCC.  The FP64 form has the one register budget OCC 2; the
+// mixed form has OCC 2, 3, 4 (3 only for 128- and 256-thread tiles).
+#define SLIM_TPO_SWITCH(R, TP, OC, ...)                                                \
+  if constexpr (sizeof(R) == 8) {                                                      \
+    switch (TP) {                                                                      \
+      case 128: { constexpr int TPc = 128, OCc = 2; __VA_ARGS__; } break;              \
+      case 256: { constexpr int TPc = 256, OCc = 2; __VA_ARGS__; } break;              \
+      case 512: { constexpr int TPc = 512, OCc = 2; __VA_ARGS__; } break;              \
+      default: return cudaErrorInvalidValue;                                           \
+    }                                                                                  \
+  } else {                                                                             \
+    switch (TP * 10 + OC) {                                                            \
+      case 1282: { constexpr int TPc = 128, OCc = 2; __VA_ARGS__; } break;             \
+      case 1283: { constexpr int TPc = 128, OCc = 3; __VA_ARGS__; } break;             \
+      case 1284: { constexpr int TPc = 128, OCc = 4; __VA_ARGS__; } break;             \
+      case 2562: { constexpr int TPc = 256, OCc = 2; __VA_ARGS__; } break;             \
+      case 2563: { constexpr int TPc = 256, OCc = 3; __VA_ARGS__; } break;             \
+      case 2564: { constexpr int TPc = 256, OCc = 4; __VA_ARGS__; } break;             \
+      case 5122: { constexpr int TPc = 512, OCc = 2; __VA_ARGS__; } break;             \
+      case 5124: { constexpr int TPc = 512, OCc = 4; __VA_ARGS__; } break;             \
+      default: return cudaErrorInvalidValue;                                           \
+    }                                                                                  \
   }
+
+// resident-block budget of the heavy kernels from the parameters (0 = 4; a tile of
+// 512 prisms has no 3-block budget and takes 2)
+inline int occ_of(const slim_params& p, int TP) {
+  const int o = (p.blocks_per_sm >= 2 && p.blocks_per_sm <= 4) ? p.blocks_per_sm : 4;
+  return (o == 3 && TP == 512) ? 2 : o;
+}
 
 #define SLIM_TP_SWITCH2(TP, ...)                                \
   switch (TP) {                                                 \
@@ -623,7 +643,7 @@ __global__ void __launch_bounds__(256)
     const int ip = ((j >> 1) * nt + t) * 2 + (j & 1);
     if (KIND == 0) bf.Gacc[ip] = Fe[j];
     if (KIND == 1) bf.Gacc[ip] += Fe[j];
-    if (KIND == 2) bf.Gb[ip] += (double)((bf.Gacc[ip] + 4.0f * Fe[j]) * wq);
+    if (KIND == 2) bf.Gb[ip] += f2d_bits((bf.Gacc[ip] + 4.0f * Fe[j]) * wq);
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -653,13 +673,14 @@ __global__ void __launch_bounds__(256)
       float* o[3] = {io.eo, io.Uo, io.Vo};
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
+        // conversions on the integer pipe: the FP64 pipe keeps the three FP64 sums
         const double qn = x[c][ia];
-        if (c == 1) bf.Qbx[ia] += wn * (qn + (double)bf.Eacc[ia]);
-        if (c == 2) bf.Qby[ia] += wn * (qn + (double)bf.Eacc[n2 + ia]);
+        if (c == 1) bf.Qbx[ia] += wn * (qn + f2d_bits(bf.Eacc[ia]));
+        if (c == 2) bf.Qby[ia] += wn * (qn + f2d_bits(bf.Eacc[n2 + ia]));
         const float inc = bf.Dacc[c * n2 + ia] * (1.0f / 6.0f) + d[c] * (2.0f / 3.0f);
-        const double qnew = qn + (double)inc;
+        const double qnew = qn + f2d_bits(inc);
         x[c][ia] = qnew;
-        o[c][ia] = (float)qnew;
+        o[c][ia] = d2f_bits(qnew);
       }
     }
   }
@@ -814,7 +835,8 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
   R* s_b = reinterpret_cast<R*>(smem + ob);                 // [12][TPX]
   R* s_W = s_b + 12 * (size_t)TPX;                          // [6][TPX]
   R* s_C = s_W + 6 * (size_t)TPX;                           // [3][4][TPX]
-  R* s_st = s_C + 12 * (size_t)TPX;                         // [3][TP]
+  R* s_x = s_C + 12 * (size_t)TPX;                          // [12][TPX] f0 (implicit)
+  R* s_st = s_x + (IMPL ? 12 : 0) * (size_t)TPX;            // [3][TP]
   const Tile tl = tile_of_block(m);
   const int i = threadIdx.x;
   const int nt = m.n_tri, P = m.P;
@@ -847,28 +869,30 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
     for (int a = 0; a < 3; ++a) {
       const int ia = a * nt + t;
       const R dr = dz_rest_r<R>(m, ia, k, N);
-      const R hz0 = (R)0.5 * dr * st0[ia];
+      // increment form f1 = f0 + d: rhs - M1 f0 = (M0 - M1) f0 + dt (...), with the
+      // stretch difference st0 - st1 exact; the inverse mass (explicit) and the
+      // column solve (implicit) then act on the increment only
+      const R dhz = (R)0.5 * dr * (st0[ia] - st1[ia]);
       R b[2][2];
       const size_t i0 = (size_t)a * P + p, i1 = (size_t)(3 + a) * P + p;
-      lumped<R>(w6 * hz0, G0[i0], G0[i1], b[0][0], b[0][1]);
-      lumped<R>(w6 * hz0, G1[i0], G1[i1], b[1][0], b[1][1]);
+      const R g00 = G0[i0], g01 = G0[i1], g10 = G1[i0], g11 = G1[i1];
+      lumped<R>(w6 * dhz, g00, g01, b[0][0], b[0][1]);
+      lumped<R>(w6 * dhz, g10, g11, b[1][0], b[1][1]);
       R add0 = 0, add1 = 0;
       if (KIND == 0) {  // M1 F2D / H1 = (J_h/12) dz_rest (1/h) F2D
         const R cfac = Geo<R>::jh(m, t) * (R)(1.0 / 12.0) * dr * Geo<R>::ih(m, ia);
         add0 = cfac * F2x[ia];
         add1 = cfac * F2y[ia];
       }
-      R r00 = b[0][0] + dt * (F0[0][a] + add0), r01 = b[0][1] + dt * (F0[1][a] + add0);
-      R r10 = b[1][0] + dt * (F1[0][a] + add1), r11 = b[1][1] + dt * (F1[1][a] + add1);
-      if (IMPL) {
-        s_b[(0 * 3 + a) * TPX + slot] = r00;
-        s_b[(1 * 3 + a) * TPX + slot] = r01;
-        s_b[(2 * 3 + a) * TPX + slot] = r10;
-        s_b[(3 * 3 + a) * TPX + slot] = r11;
-      } else {
-        // + dt A(W, st_ev) f_ev, A couples the layers above and below
+      R rr[2][2] = {{b[0][0] + dt * (F0[0][a] + add0), b[0][1] + dt * (F0[1][a] + add0)},
+                    {b[1][0] + dt * (F1[0][a] + add1), b[1][1] + dt * (F1[1][a] + add1)}};
+      {
+        // + dt A(W, st) f, A couples the layers above and below.  Explicit: the
+        // evaluation state on its geometry.  Implicit (increment form): the start
+        // state f0 with the operator of the column solve (geometry st1), so that
+        // the solve runs on rhs - (M1 - dt A) f0 and returns the increment.
         const R kap = ua.kap_v, pen = pp.pen_v;
-        const R stv = in.st[ia];
+        const R stv = IMPL ? st1[ia] : in.st[ia];
         const R dz = dr * stv, idz = rcp<R>(dz);
         R idzm = idz, idzp = idz;
         if (m.n_levels != 0) {
@@ -879,9 +903,9 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
         const R Wn = (k + 1 < N) ? W[(size_t)a * P + p + 1] : (R)0;
         R A[2][2], AL[2][2], AU[2][2];
         vertical_A<R>(k, N, w6, idzm, idz, idzp, W0, W1, Wn, kap, pen, A, AL, AU);
-        const R* Fs[2] = {in.F0 ? in.F0 : in.U, in.F1 ? in.F1 : in.V};
-        R rr[2][2] = {{r00, r01}, {r10, r11}};
-        const R fk[2][2] = {{own.f0[0][a], own.f0[1][a]}, {own.f1[0][a], own.f1[1][a]}};
+        const R* Fs[2] = {IMPL ? G0 : (in.F0 ? in.F0 : in.U), IMPL ? G1 : (in.F1 ? in.F1 : in.V)};
+        const R fk[2][2] = {{IMPL ? g00 : own.f0[0][a], IMPL ? g01 : own.f0[1][a]},
+                            {IMPL ? g10 : own.f1[0][a], IMPL ? g11 : own.f1[1][a]}};
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           R fm0 = 0, fm1 = 0, fp0 = 0, fp1 = 0;
@@ -892,13 +916,24 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
             rr[q][rw] += dt * (A[rw][0] * fk[q][0] + A[rw][1] * fk[q][1] + AL[rw][0] * fm0 +
                                AL[rw][1] * fm1 + AU[rw][0] * fp0 + AU[rw][1] * fp1);
         }
+      }
+      if (IMPL) {
+        s_b[(0 * 3 + a) * TPX + slot] = rr[0][0];
+        s_b[(1 * 3 + a) * TPX + slot] = rr[0][1];
+        s_b[(2 * 3 + a) * TPX + slot] = rr[1][0];
+        s_b[(3 * 3 + a) * TPX + slot] = rr[1][1];
+        s_x[(0 * 3 + a) * TPX + slot] = g00;
+        s_x[(1 * 3 + a) * TPX + slot] = g01;
+        s_x[(2 * 3 + a) * TPX + slot] = g10;
+        s_x[(3 * 3 + a) * TPX + slot] = g11;
+      } else {
         // M1^-1: (6 / (J_h hz1)) [[2,-1],[-1,2]] per vertex-layer
         const R hz1 = (R)0.5 * dr * st1[ia];
         const R im = rcp<R>(w6 * hz1);
-        o0[0][a] = im * ((R)2 * rr[0][0] - rr[0][1]);
-        o0[1][a] = im * ((R)2 * rr[0][1] - rr[0][0]);
-        o1[0][a] = im * ((R)2 * rr[1][0] - rr[1][1]);
-        o1[1][a] = im * ((R)2 * rr[1][1] - rr[1][0]);
+        o0[0][a] = g00 + im * ((R)2 * rr[0][0] - rr[0][1]);
+        o0[1][a] = g01 + im * ((R)2 * rr[0][1] - rr[0][0]);
+        o1[0][a] = g10 + im * ((R)2 * rr[1][0] - rr[1][1]);
+        o1[1][a] = g11 + im * ((R)2 * rr[1][1] - rr[1][0]);
       }
     }
     if (IMPL) {
@@ -919,13 +954,13 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
                         ua.kap_v, pp.pen_v, dt);
     }
     __syncthreads();
-    if (i < tl.np) {
+    if (i < tl.np) {  // f1 = f0 + increment
 #pragma unroll
       for (int c = 0; c < 2; ++c)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          o0[c][a] = s_b[(c * 3 + a) * TPX + slot];
-          o1[c][a] = s_b[((2 + c) * 3 + a) * TPX + slot];
+          o0[c][a] = s_x[(c * 3 + a) * TPX + slot] + s_b[(c * 3 + a) * TPX + slot];
+          o1[c][a] = s_x[((2 + c) * 3 + a) * TPX + slot] + s_b[((2 + c) * 3 + a) * TPX + slot];
         }
     }
   }
@@ -947,9 +982,10 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
 size_t tile_smem(const DevMesh& m, int TP, size_t esz, int rows) {
   return ((TP + 1) * sizeof(int) + 15) / 16 * 16 + (size_t)rows * (TP + m.max_tile_tris) * esz;
 }
-size_t update_smem(const DevMesh& m, int TP, size_t esz) {
-  return ((TP + 1) * sizeof(int) + 15) / 16 * 16 + (size_t)30 * (TP + m.max_tile_tris) * esz +
-         (size_t)3 * TP * esz;
+// s_b [12], s_W [6], s_C [12] (+ s_x [12] for the implicit update) x TPX, s_st [3] x TP
+size_t update_smem(const DevMesh& m, int TP, size_t esz, bool impl) {
+  return ((TP + 1) * sizeof(int) + 15) / 16 * 16 +
+         (size_t)(impl ? 42 : 30) * (TP + m.max_tile_tris) * esz + (size_t)3 * TP * esz;
 }
 
 template <typename R>
@@ -974,7 +1010,7 @@ PP<R> phys(const slim_params& p) {
 template <typename R>
 cudaError_t launch_hpg(const DevMesh& m, int TP, int occ, const R* T, const R* S, const R* st,
                        const PP<R>& pp, R* Rx, R* Ry, cudaStream_t s) {
-  SLIM_TPO_SWITCH(TP, occ, {
+  SLIM_TPO_SWITCH(R, TP, occ, {
     const size_t sm = tile_smem(m, TPc, sizeof(R), 12);
     cudaError_t e = set_smem2(k_hpg<R, TPc, OCc>, sm);
     if (e != cudaSuccess) return e;
@@ -986,7 +1022,7 @@ cudaError_t launch_hpg(const DevMesh& m, int TP, int occ, const R* T, const R* S
 template <typename R>
 cudaError_t launch_mompred(const DevMesh& m, int TP, int occ, const AdvIn<R>& in, const R* Rx,
                            const R* Ry, const PP<R>& pp, SplitBufs* b, cudaStream_t s) {
-  SLIM_TPO_SWITCH(TP, occ, {
+  SLIM_TPO_SWITCH(R, TP, occ, {
     const size_t sm = tile_smem(m, TPc, sizeof(R), 12);
     cudaError_t e = set_smem2(k_mompred<R, TPc, OCc>, sm);
     if (e != cudaSuccess) return e;
@@ -1013,8 +1049,8 @@ cudaError_t launch_update(const DevMesh& m, int TP, int occ, const AdvIn<R>& in,
                           const R* W, const R* Rx, const R* Ry, const R* F2x, const R* F2y,
                           const R* st0, const R* st1, const PP<R>& pp, const UA<R>& ua,
                           R* O0, R* O1, int* err, cudaStream_t s) {
-  SLIM_TPO_SWITCH(TP, occ, {
-    const size_t sm = update_smem(m, TPc, sizeof(R));
+  SLIM_TPO_SWITCH(R, TP, occ, {
+    const size_t sm = update_smem(m, TPc, sizeof(R), IMPL);
     cudaError_t e = set_smem2(k_update<R, TPc, KIND, IMPL, OCc>, sm);
     if (e != cudaSuccess) return e;
     k_update<R, TPc, KIND, IMPL, OCc><<<m.n_tiles, TPc, sm, s>>>(m, in, G0, G1, W, Rx, Ry, F2x, F2y, st0,
@@ -1033,7 +1069,7 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, int tide_base,
   const DevMesh& m = s->mesh->d;
   SplitBufs* b = s->sp;
   const int TP = s->mesh->tile_prisms;
-  const int occ = s->par.blocks_per_sm == 2 ? 2 : 4;
+  const int occ = occ_of(s->par, TP);
   const PP<R> pp = phys<R>(s->par);
   const int nt = m.n_tri;
   const size_t n2 = (size_t)3 * nt;
@@ -1280,7 +1316,7 @@ slim_status split_hpg(slim_state* s, cudaStream_t st) {
                                (const double*)s->st_cur, phys<double>(s->par), (double*)s->Rx,
                                (double*)s->Ry, st));
   else
-    SLIM_CU(launch_hpg<float>(m, s->mesh->tile_prisms, s->par.blocks_per_sm == 2 ? 2 : 4, (const float*)s->T, (const float*)s->S,
+    SLIM_CU(launch_hpg<float>(m, s->mesh->tile_prisms, occ_of(s->par, s->mesh->tile_prisms), (const float*)s->T, (const float*)s->S,
                               (const float*)s->st_cur, phys<float>(s->par), (float*)s->Rx,
                               (float*)s->Ry, st));
   return SLIM_OK;

@@ -350,8 +350,10 @@ __device__ __forceinline__ void vertical_A(int k, int N, R omega, R idzm, R idz,
 }
 
 // 2x2-block Thomas sweep of one vertex column with two right-hand sides sharing
-// the matrix (M(st) - bdt A).  b?t/b?b: right-hand sides of field ? (top/bottom
-// rows), overwritten by the solution; C0..C3 scratch.
+// the matrix K = M(st) - bdt A.  b?t/b?b: right-hand sides of field ? (top/bottom
+// rows), overwritten by the solution; C0..C3 scratch.  Increment form when x0 is
+// given (top/bottom of field 0, then of field 1, by layer): the b are rhs - M x0,
+// the sweep adds bdt A x0, solves for the increment and returns x0 + increment.
 template <typename R>
 __device__ __forceinline__ void column_thomas2(const DevMesh& m, int t, int ia, int N, R st,
                                                const R* __restrict__ Wt, const R* __restrict__ Wb,
@@ -359,7 +361,7 @@ __device__ __forceinline__ void column_thomas2(const DevMesh& m, int t, int ia, 
                                                R* __restrict__ b1t, R* __restrict__ b1b,
                                                R* __restrict__ C0, R* __restrict__ C1,
                                                R* __restrict__ C2, R* __restrict__ C3, R kap, R pen,
-                                               R bdt) {
+                                               R bdt, const R* const* x0 = nullptr) {
   const R omega = Geo<R>::jh(m, t) * (R)(1.0 / 6.0);
   R z[2][2] = {{0, 0}, {0, 0}};
   R c00 = 0, c01 = 0, c10 = 0, c11 = 0;
@@ -373,8 +375,27 @@ __device__ __forceinline__ void column_thomas2(const DevMesh& m, int t, int ia, 
       idzp = rcp<R>(dzp);
     }
     const R Wn = (k + 1 < N) ? Wt[k + 1] : (R)0;
-    Row<R> row;
-    assemble_row<R>(k, N, omega, idzm, dz, idz, idzp, Wt[k], Wb[k], Wn, kap, pen, bdt, row);
+    Row<R> row, op;
+    assemble_row<R>(k, N, omega, idzm, dz, idz, idzp, Wt[k], Wb[k], Wn, kap, pen, bdt, row, &op);
+    R ax[2][2] = {{0, 0}, {0, 0}};  // bdt A x0 of both fields
+    if (x0) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const R* xt = x0[2 * q];
+        const R* xb = x0[2 * q + 1];
+        R a0 = op.D[0][0] * xt[k] + op.D[0][1] * xb[k], a1 = op.D[1][0] * xt[k] + op.D[1][1] * xb[k];
+        if (k > 0) {
+          a0 += op.L[0][0] * xt[k - 1] + op.L[0][1] * xb[k - 1];
+          a1 += op.L[1][0] * xt[k - 1] + op.L[1][1] * xb[k - 1];
+        }
+        if (k + 1 < N) {
+          a0 += op.U[0][0] * xt[k + 1] + op.U[0][1] * xb[k + 1];
+          a1 += op.U[1][0] * xt[k + 1] + op.U[1][1] * xb[k + 1];
+        }
+        ax[q][0] = bdt * a0;
+        ax[q][1] = bdt * a1;
+      }
+    }
     R Dp[2][2];
     Dp[0][0] = row.D[0][0] - (row.L[0][0] * c00 + row.L[0][1] * c10);
     Dp[0][1] = row.D[0][1] - (row.L[0][0] * c01 + row.L[0][1] * c11);
@@ -386,8 +407,8 @@ __device__ __forceinline__ void column_thomas2(const DevMesh& m, int t, int ia, 
     R* bb[2] = {b0b, b1b};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      const R y0 = bt[q][k] - (row.L[0][0] * z[q][0] + row.L[0][1] * z[q][1]);
-      const R y1 = bb[q][k] - (row.L[1][0] * z[q][0] + row.L[1][1] * z[q][1]);
+      const R y0 = (bt[q][k] + ax[q][0]) - (row.L[0][0] * z[q][0] + row.L[0][1] * z[q][1]);
+      const R y1 = (bb[q][k] + ax[q][1]) - (row.L[1][0] * z[q][0] + row.L[1][1] * z[q][1]);
       z[q][0] = Di[0][0] * y0 + Di[0][1] * y1;
       z[q][1] = Di[1][0] * y0 + Di[1][1] * y1;
       bt[q][k] = z[q][0];
@@ -406,14 +427,20 @@ __device__ __forceinline__ void column_thomas2(const DevMesh& m, int t, int ia, 
   R* bb[2] = {b0b, b1b};
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
-    R x0 = z[q][0], x1 = z[q][1];
+    R y0 = z[q][0], y1 = z[q][1];
     for (int k = N - 2; k >= 0; --k) {
-      const R n0 = bt[q][k] - (C0[k] * x0 + C1[k] * x1);
-      const R n1 = bb[q][k] - (C2[k] * x0 + C3[k] * x1);
+      const R n0 = bt[q][k] - (C0[k] * y0 + C1[k] * y1);
+      const R n1 = bb[q][k] - (C2[k] * y0 + C3[k] * y1);
       bt[q][k] = n0;
       bb[q][k] = n1;
-      x0 = n0;
-      x1 = n1;
+      y0 = n0;
+      y1 = n1;
+    }
+    if (x0) {
+      for (int k = 0; k < N; ++k) {
+        bt[q][k] += x0[2 * q][k];
+        bb[q][k] += x0[2 * q + 1][k];
+      }
     }
   }
 }

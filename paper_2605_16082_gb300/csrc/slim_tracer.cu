@@ -18,6 +18,7 @@
 // 1 + eta/h in the compute type (st arrays), so the mixed form runs no FP64
 // arithmetic in the 3D kernels; the FP64 elevation update stays in the
 // continuity kernel's column epilogue.
+#include <cmath>
 #include <float.h>
 
 #include <algorithm>
@@ -133,7 +134,9 @@ __device__ __forceinline__ void column_thomas(const DevMesh& m, int t, int ia, i
                                               R* __restrict__ bt, R* __restrict__ bb,
                                               R* __restrict__ C0, R* __restrict__ C1,
                                               R* __restrict__ C2, R* __restrict__ C3, R kap, R pen,
-                                              R bdt, R flux_top, R flux_bot) {
+                                              R bdt, R flux_top, R flux_bot,
+                                              const R* __restrict__ x0t = nullptr,
+                                              const R* __restrict__ x0b = nullptr) {
   const R omega = Geo<R>::jh(m, t) * (R)(1.0 / 6.0);
   R z0 = 0, z1 = 0;
   R c00 = 0, c01 = 0, c10 = 0, c11 = 0;
@@ -148,11 +151,27 @@ __device__ __forceinline__ void column_thomas(const DevMesh& m, int t, int ia, i
       idzp = rcp<R>(dzp);
     }
     const R Wn = (k + 1 < N) ? Wt[k + 1] : (R)0;
-    Row<R> row;
-    assemble_row<R>(k, N, omega, idzm, dz, idz, idzp, Wt[k], Wb[k], Wn, kap, pen, bdt, row);
+    Row<R> row, op;
+    assemble_row<R>(k, N, omega, idzm, dz, idz, idzp, Wt[k], Wb[k], Wn, kap, pen, bdt, row, &op);
     R b0 = bt[k], b1 = bb[k];
     if (k == 0) b0 += bdt * omega * flux_top;
     if (k == N - 1) b1 -= bdt * omega * flux_bot;
+    if (x0t) {  // increment form: the caller's b is rhs - M x0; add bdt A x0
+      const R xt = x0t[k], xb = x0b[k];
+      R a0 = op.D[0][0] * xt + op.D[0][1] * xb, a1 = op.D[1][0] * xt + op.D[1][1] * xb;
+      if (k > 0) {
+        const R ut = x0t[k - 1], ub = x0b[k - 1];
+        a0 += op.L[0][0] * ut + op.L[0][1] * ub;
+        a1 += op.L[1][0] * ut + op.L[1][1] * ub;
+      }
+      if (k + 1 < N) {
+        const R dt_ = x0t[k + 1], db = x0b[k + 1];
+        a0 += op.U[0][0] * dt_ + op.U[0][1] * db;
+        a1 += op.U[1][0] * dt_ + op.U[1][1] * db;
+      }
+      b0 += bdt * a0;
+      b1 += bdt * a1;
+    }
     // D' = D - L C_{k-1},  y = b - L z_{k-1}
     R Dp[2][2];
     Dp[0][0] = row.D[0][0] - (row.L[0][0] * c00 + row.L[0][1] * c10);
@@ -186,17 +205,24 @@ __device__ __forceinline__ void column_thomas(const DevMesh& m, int t, int ia, i
     x0 = n0;
     x1 = n1;
   }
+  if (x0t) {  // the solution is x0 + increment
+    for (int k = 0; k < N; ++k) {
+      bt[k] += x0t[k];
+      bb[k] += x0b[k];
+    }
+  }
 }
 
 // shared-memory carve-up of the solve kernels (TPX = TP + most triangles per tile)
 template <typename R, int TP>
 struct SolveSmem {
-  size_t off_b, off_W, off_C, off_st, bytes;
+  size_t off_b, off_W, off_C, off_x, off_st, bytes;
   __host__ __device__ SolveSmem(int TPX) {
     off_b = ((TP + 1) * sizeof(int) + 15) / 16 * 16;
     off_W = off_b + 6 * (size_t)TPX * sizeof(R);
     off_C = off_W + 6 * (size_t)TPX * sizeof(R);
-    off_st = off_C + 12 * (size_t)TPX * sizeof(R);
+    off_x = off_C + 12 * (size_t)TPX * sizeof(R);   // reference state of the increment form
+    off_st = off_x + 6 * (size_t)TPX * sizeof(R);
     bytes = off_st + 3 * (size_t)TP * sizeof(R);
   }
 };
@@ -205,15 +231,18 @@ template <typename R, int TP>
 __device__ __forceinline__ void solve_tile_columns(const DevMesh& m, const Tile& tl,
                                                    const int* s_off, int TPX, R* s_b, R* s_W,
                                                    R* s_C, const R* s_st, const StageParams& sp,
-                                                   R bdt) {
+                                                   R bdt, const R* s_x = nullptr) {
   for (int j = threadIdx.x; j < 3 * tl.nt; j += TP) {
     const int a = j / tl.nt, lt = j - a * tl.nt;
     const int t = tl.t0 + lt, base = s_off[lt] + lt, N = s_off[lt + 1] - s_off[lt];
     R* C = s_C + (size_t)a * 4 * TPX + base;
+    // reference state of the increment form (shared memory, same layout as s_b)
+    const R* x0t = s_x ? s_x + a * TPX + base : nullptr;
+    const R* x0b = s_x ? s_x + (3 + a) * TPX + base : nullptr;
     column_thomas<R>(m, t, a * m.n_tri + t, N, s_st[a * TP + lt], s_W + a * TPX + base,
                      s_W + (3 + a) * TPX + base, s_b + a * TPX + base, s_b + (3 + a) * TPX + base,
                      C, C + TPX, C + 2 * TPX, C + 3 * TPX, (R)sp.kappa, (R)sp.penalty, bdt,
-                     (R)sp.flux_top, (R)sp.flux_bot);
+                     (R)sp.flux_top, (R)sp.flux_bot, x0t, x0b);
   }
 }
 
@@ -253,6 +282,7 @@ __global__ void __launch_bounds__(TP, (MinBlocks<R, TP>::value)) k_tracer_stage(
   R* s_b = reinterpret_cast<R*>(smem + L.off_b);
   R* s_W = reinterpret_cast<R*>(smem + L.off_W);
   R* s_C = reinterpret_cast<R*>(smem + L.off_C);
+  R* s_x = reinterpret_cast<R*>(smem + L.off_x);
   R* s_st = reinterpret_cast<R*>(smem + L.off_st);
   const Tile tl = tile_of_block(m);
   const int i = threadIdx.x;
@@ -275,24 +305,33 @@ __global__ void __launch_bounds__(TP, (MinBlocks<R, TP>::value)) k_tracer_stage(
     prism_rh<R, false>(m, t, k, p, N, own, U, V, Tp, Text, st_n, out);
     const R w12 = Geo<R>::jh(m, t) * (R)(1.0 / 12.0);
     const R G2 = (R)(2.0 / 3.0), G1 = (R)(1.0 / 3.0);
+    // Increment form T_out = T_p + D: the solve gets rhs - M(st_s) T_p, which with
+    // alpha + beta = 1 and st_x = st_n + th_x (st_np1 - st_n) is
+    //   (J_h/12) dz_rest G [alpha st_n (T_n - T_p) + (beta th_p - th_s) dst T_p]
+    //   + beta dt R_h,   dst = st_np1 - st_n (an exact difference),
+    // and adds beta dt A T_p itself.  The solve's own rounding then scales only the
+    // increment instead of the whole state in every stage.
+    const R ks = beta * th_p - th_s;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const int ia = a * nt + t;
       const R sn = st_n[ia];
-      const R sp_ = sn + th_p * (st_np1[ia] - sn);
+      const R dst = st_np1[ia] - sn;
       const R dr = w12 * dz_rest_r<R>(m, ia, k, N);
-      const R mn = dr * sn;
-      const R mp = dr * sp_;
       const R tn0 = Tn[(size_t)(0 * 3 + a) * m.P + p], tn1 = Tn[(size_t)(1 * 3 + a) * m.P + p];
       const R tp0 = own.T[0][a], tp1 = own.T[1][a];
-      s_b[a * TPX + slot] = alpha * mn * (G2 * tn0 + G1 * tn1) + beta * (mp * (G2 * tp0 + G1 * tp1) + dt * out[0][a]);
-      s_b[(3 + a) * TPX + slot] = alpha * mn * (G1 * tn0 + G2 * tn1) + beta * (mp * (G1 * tp0 + G2 * tp1) + dt * out[1][a]);
+      const R u0 = alpha * sn * (tn0 - tp0) + ks * dst * tp0;
+      const R u1 = alpha * sn * (tn1 - tp1) + ks * dst * tp1;
+      s_b[a * TPX + slot] = dr * (G2 * u0 + G1 * u1) + beta * dt * out[0][a];
+      s_b[(3 + a) * TPX + slot] = dr * (G1 * u0 + G2 * u1) + beta * dt * out[1][a];
+      s_x[a * TPX + slot] = tp0;
+      s_x[(3 + a) * TPX + slot] = tp1;
     }
 #pragma unroll
     for (int r = 0; r < 6; ++r) s_W[r * TPX + slot] = W[(size_t)r * m.P + p];
   }
   __syncthreads();
-  solve_tile_columns<R, TP>(m, tl, s_off, TPX, s_b, s_W, s_C, s_st, sp, beta * dt);
+  solve_tile_columns<R, TP>(m, tl, s_off, TPX, s_b, s_W, s_C, s_st, sp, beta * dt, s_x);
   __syncthreads();
   write_tile<R>(m, tl, TPX, slot, s_b, Tout, err);
 }
@@ -494,12 +533,19 @@ cudaError_t launch_tracer_stage(const DevMesh& m, int TP, const R* U, const R* V
                                 const R* st_np1, double th_p, double th_s, double alpha,
                                 double beta, double dt, const StageParams& sp, int* err,
                                 cudaStream_t stm) {
+  // The weights of the convex combination in the compute type with alpha + beta = 1
+  // exactly (multiples of 2^-24 in FP32, 2^-52 in FP64): weights whose sum is not one
+  // scale the tracer mass by that sum in every step (1/3 and 2/3 rounded to FP32
+  // sum to 1 + 3e-8).
+  const double q = sizeof(R) == 4 ? 16777216.0 : 4503599627370496.0;
+  const double aq = std::nearbyint(alpha * q) / q;
+  const double bq = (alpha + beta == 1.0) ? 1.0 - aq : beta;
   SLIM_TP_SWITCH(TP, {
     const size_t sm = SolveSmem<R, TPc>(TPc + m.max_tile_tris).bytes;
     cudaError_t e = set_smem(k_tracer_stage<R, TPc>, sm);
     if (e != cudaSuccess) return e;
     k_tracer_stage<R, TPc><<<m.n_tiles, TPc, sm, stm>>>(m, U, V, Tn, Tp, Text, W, Tout, st_n, st_np1,
-                                                        (R)th_p, (R)th_s, (R)alpha, (R)beta, (R)dt,
+                                                        (R)th_p, (R)th_s, (R)aq, (R)bq, (R)dt,
                                                         sp, err);
   });
   return cudaGetLastError();

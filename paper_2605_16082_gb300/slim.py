@@ -28,7 +28,7 @@ EXPORTED = ["slim_params_default", "slim_status_string", "slim_last_error", "sli
             "slim_state_field_ptr", "slim_state_check", "slim_rhs3d", "slim_continuity",
             "slim_rhs2d", "slim_vertical_solve", "slim_hpg", "slim_step", "slim_tracer_mass",
             "slim_step_kernel_count", "slim_profile_begin", "slim_profile_end",
-            "slim_phase_name", "slim_tracer_mass_noalloc"]
+            "slim_phase_name", "slim_tracer_mass_noalloc", "slim_selftest_conversions"]
 PHASES = ["continuity", "tracer_stage", "hpg", "mom_pred", "ext2d", "momentum", "tracers", "misc"]
 
 
@@ -82,6 +82,8 @@ def lib() -> C.CDLL:
             "slim_profile_end": ([_vp, _dp, C.POINTER(_i)], _i),
             "slim_phase_name": ([_i], C.c_char_p),
             "slim_tracer_mass_noalloc": ([_vp, _i, _vp, _vp], _i),
+            "slim_selftest_conversions": ([C.c_longlong, C.c_ulonglong, C.POINTER(C.c_longlong),
+                                           C.POINTER(C.c_longlong)], _i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -223,6 +225,14 @@ def slim_tracer_mass_noalloc(state: int, field: int, mass_dev: int, stream: int 
     """Tracer mass into one device double at ``mass_dev`` without device allocation
     (asynchronous on ``stream``)."""
     _check(lib().slim_tracer_mass_noalloc(state, int(field), mass_dev, stream))
+
+
+def slim_selftest_conversions(n: int, seed: int = 0) -> tuple[int, int]:
+    """Mismatch counts (binary64->binary32, binary32->binary64) of the library's
+    integer-pipe conversions against the GPU's own, over n seeded patterns."""
+    a, b = C.c_longlong(-1), C.c_longlong(-1)
+    _check(lib().slim_selftest_conversions(int(n), int(seed), C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def slim_step_kernel_count(state: int) -> int:

@@ -243,5 +243,14 @@ def test_autotune_returns_a_measured_configuration(slim):
     p = params(slim)
     res = autotune.autotune(m, slim.SLIM_MIXED, p, ini, 20.0, use_cache=False)
     assert res["tile_prisms"] in autotune.TILES and res["blocks_per_sm"] in autotune.OCCS
-    assert len(res["all"]) == len(autotune.TILES) * len(autotune.OCCS)
+    # every (tile, budget) pair except the 3-block budget of 512-prism tiles
+    assert len(res["all"]) == len(autotune.TILES) * len(autotune.OCCS) - 1
+    assert "512/3" not in res["all"]
     assert res["ms_per_step"] == min(res["all"].values()) > 0
+
+
+def test_integer_pipe_conversions_match_the_gpu(slim):
+    """The mixed 2D update converts between binary32 and binary64 with integer bit
+    arithmetic; every pattern class must give the GPU's own result bit for bit."""
+    bad_d2f, bad_f2d = slim.slim_selftest_conversions(1 << 24, seed=7)
+    assert (bad_d2f, bad_f2d) == (0, 0)
