@@ -5,6 +5,7 @@ arithmetic's error, stated per test.  Every case spans several thread-block
 tiles with a ragged last tile; edge cases cover one-layer columns, uneven
 columns, open boundaries and all tile sizes.
 """
+import os
 import numpy as np
 import pytest
 
@@ -288,3 +289,49 @@ def test_tracer_graph_replay_matches_launches(slim):
                 slim.slim_step(mod.state, n * 20.0, 20.0)
             res.append(mod.download("T"))
     assert np.array_equal(res[0], res[1])
+
+
+def _golden_c1_1000():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c1_tracer_1000.txt")
+    vals, idx, smp = {}, [], []
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            a, b = line.split()
+            if a.isdigit():
+                idx.append(int(a)); smp.append(float(b))
+            else:
+                vals[a] = float(b)
+    return vals, np.array(idx), np.array(smp)
+
+
+def test_mixed_tracer_error_after_1000_steps(slim):
+    """Mixed form of the square-basin tracer run against the FP64 form after 1000
+    steps: tracer relative L2 error at most 1e-5.  The FP64 form is tied to the
+    oracle's own 1000-step run (stored mass and 256 stored nodes)."""
+    vals, idx, smp = _golden_c1_1000()
+    steps = int(vals["steps"])
+    W = wl.WORKLOADS["square_tracer"]
+    m = W["mesh"]()
+    u, v = wl.c1_velocity(m)
+    T = wl.c1_tracer(m)
+    res = {}
+    for prec in (slim.SLIM_FP64, slim.SLIM_MIXED):
+        with _setup(slim, m, u, v, T, prec, kappa_v=W["kappa_v"]) as mod:
+            m0 = slim.slim_tracer_mass(mod.state, 0)
+            for n in range(steps):
+                slim.slim_step(mod.state, n * W["dt"], W["dt"])
+            slim.slim_state_check(mod.state)
+            res[prec] = (mod.download("T"), m0, slim.slim_tracer_mass(mod.state, 0))
+    T64, m0_64, m1_64 = res[slim.SLIM_FP64]
+    Tmx, m0_mx, m1_mx = res[slim.SLIM_MIXED]
+    scale = np.abs(smp).max()
+    assert np.abs(T64[idx] - smp).max() < 1e-10 * scale          # FP64 form = oracle
+    assert abs(m0_64 - vals["mass0"]) < 1e-13 * abs(vals["mass0"])
+    assert abs(m1_64 - vals["mass"]) < 1e-12 * abs(vals["mass"])
+    err = rel_l2(Tmx, T64)
+    drift = (m1_mx - m0_mx) / m0_mx
+    print(f"mixed vs FP64 after {steps} steps: tracer rel L2 {err:.3e}, mass drift {drift:.3e}")
+    assert err <= 1e-5
+    assert abs(drift) < 1e-5
