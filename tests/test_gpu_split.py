@@ -6,11 +6,13 @@ and the vertical flux W, see TOL_R).  Cases: a graded basin with an
 open tidal boundary (several tiles, ragged last tile), a square basin, and a
 z-level basin with uneven columns (1..N layers, walls against shallower
 neighbours)."""
+import copy
+
 import numpy as np
 import pytest
 
 import workloads as wl
-from helpers import rel_l2
+from helpers import prisms_of, rel_l2, restrict2, restrict3, ring_submesh
 
 pytestmark = pytest.mark.gpu
 
@@ -254,3 +256,76 @@ def test_integer_pipe_conversions_match_the_gpu(slim):
     arithmetic; every pattern class must give the GPU's own result bit for bit."""
     bad_d2f, bad_f2d = slim.slim_selftest_conversions(1 << 24, seed=7)
     assert (bad_d2f, bad_f2d) == (0, 0)
+
+
+@pytest.fixture(scope="module")
+def basin_full():
+    """The basin baroclinic workload at full size (197,480 triangles x 20 sigma
+    layers, 20 subcycles per step), with the inputs the bench times."""
+    W = wl.WORKLOADS["basin_baroclinic"]
+    m = W["mesh"]()
+    ini = wl.c2_initial_state(m)
+    fields = dict(U=ini["u"], V=ini["v"], T=ini["T"], S=ini["S"], ETA=ini["eta"], QX=ini["U"], QY=ini["V"])
+    par = dict(scheme=1, n_sub=W["n_sub"], kappa_v=W["kappa_v"], nu_v=W["nu_v"],
+               kappa_h=W.get("kappa_h", 0.0), nu_h=W.get("nu_h", 0.0))
+    return m, fields, par, W["n_sub"] * wl.fields.dt_2d(m)
+
+
+def test_split_full_size_in_the_bench_configuration(slim, basin_full):
+    """Full size, bench launch configuration (512-prism tiles; mixed with 4 blocks
+    per SM): constant tracers stay constant, tracer mass is conserved (open
+    boundary closed), the
+    hydrostatic pressure gradient matches the oracle at sampled columns, and the
+    two forms agree after two steps."""
+    from oracle import baroclinic as bc
+    from oracle.mesh import OMesh
+    m, fields, par, dt = basin_full
+    res = {}
+    for prec, occ, tol_c, tol_m in ((slim.SLIM_FP64, 2, 1e-12, 1e-13), (slim.SLIM_MIXED, 4, 1e-5, 1e-6)):
+        p = slim.slim_params_default(**par)
+        p.tile_prisms, p.blocks_per_sm = 512, occ
+        const = dict(fields, T=np.full_like(fields["T"], 20.0), S=np.full_like(fields["S"], 35.0))
+        with model(slim, m, prec, p, const, tile=512) as mod:
+            for n in range(2):
+                slim.slim_step(mod.state, n * dt, dt)
+            slim.slim_state_check(mod.state)
+            assert np.abs(mod.download("T") - 20.0).max() < tol_c * 20.0
+            assert np.abs(mod.download("S") - 35.0).max() < tol_c * 35.0
+        # tracer mass: the same mesh with the open boundary closed (no exchange)
+        closed = copy.copy(m)
+        closed.bnd = np.where(m.bnd == 2, 1, m.bnd).astype(m.bnd.dtype)
+        with model(slim, closed, prec, p, fields, tile=512) as mod:
+            m0 = slim.slim_tracer_mass(mod.state, 0)
+            for n in range(2):
+                slim.slim_step(mod.state, n * dt, dt)
+            slim.slim_state_check(mod.state)
+            assert abs(slim.slim_tracer_mass(mod.state, 0) - m0) < tol_m * abs(m0)
+        with model(slim, m, prec, p, fields, tile=512) as mod:
+            for n in range(2):
+                slim.slim_step(mod.state, n * dt, dt)
+            slim.slim_state_check(mod.state)
+            res[prec] = {f: mod.download(f) for f, _ in FIELDS3 + FIELDS2}
+            if prec == slim.SLIM_FP64:
+                # hydrostatic pressure gradient of the stepped state at sampled columns
+                slim.slim_hpg(mod.state)
+                rx, ry = mod.download("R_X"), mod.download("R_Y")
+    for f in ("T", "S"):
+        assert rel_l2(res[slim.SLIM_MIXED][f], res[slim.SLIM_FP64][f]) < 1e-6, f
+    for f in ("U", "V", "ETA", "QX", "QY"):
+        assert rel_l2(res[slim.SLIM_MIXED][f], res[slim.SLIM_FP64][f]) < 1e-3, f
+    st = res[slim.SLIM_FP64]
+    rng = np.random.default_rng(3)
+    seeds = np.unique(np.concatenate([rng.choice(m.n_tri, 10, replace=False),
+                                      np.nonzero((m.bnd == 2).any(axis=1))[0][:2], [0, m.n_tri - 1]]))
+    p = slim.slim_params_default(**par)
+    got, ref = [], []
+    for sd in seeds:
+        sub, tmap, pos = ring_submesh(m, np.array([sd]), 2)
+        om = OMesh(sub)
+        ox, oy = bc.hpg(om, oracle_params(p), restrict3(st["T"], m, tmap), restrict3(st["S"], m, tmap),
+                        restrict2(st["ETA"], m, tmap))
+        pr = prisms_of(sub.n_layers, pos)
+        got.append(np.concatenate([restrict3(rx, m, np.array([sd])).ravel(),
+                                   restrict3(ry, m, np.array([sd])).ravel()]))
+        ref.append(np.concatenate([ox[:, :, pr].ravel(), oy[:, :, pr].ravel()]))
+    assert rel_l2(np.concatenate(got), np.concatenate(ref)) < TOL_R
