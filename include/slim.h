@@ -120,12 +120,16 @@ typedef struct slim_params {
                           on the first call and again whenever dt changes; only the
                           step's start time is updated between replays); 0: launches
                           every kernel.  Profiling (slim_profile_begin) uses launches. */
+  int persistent_2d;   /* 1: the mixed form's 2D external run of a stage is one
+                          cooperative launch over all subcycles with a grid barrier
+                          between stages (bounded wait: SLIM_ERR_TIMEOUT via the error
+                          flag); 0: one launch per stage.  Same results bit for bit. */
 } slim_params;
 
 /* Fill *p with the defaults: g 9.81, rho0 1025, f 1e-4, alpha 2e-4, beta 7.6e-4,
    T0 10, S0 35, kappa_v = nu_v = 1e-3, kappa_h = nu_h = 0, Cd 2.5e-3, no boundary
    fluxes, penalty_v 4, penalty_h 6, tide 1 m / 44712 s, SLIM_SCHEME_TRACER,
-   n_sub 20, tile 256, check_every 0, blocks_per_sm 0, use_graph 1.  Returns
+   n_sub 20, tile 256, check_every 0, blocks_per_sm 0, use_graph 1, persistent_2d 1.  Returns
    SLIM_ERR_ARG for a null pointer. */
 slim_status slim_params_default(slim_params* p);
 
@@ -271,6 +275,15 @@ slim_status slim_tracer_mass_noalloc(slim_state* s, int field, double* mass_dev,
  * two counts to host memory. */
 slim_status slim_selftest_conversions(long long n, unsigned long long seed, long long* bad_d2f,
                                       long long* bad_f2d);
+
+/* slim_selftest_barrier: diagnostic (no counterpart in the paper).  Runs `rounds`
+ * rounds of the library's bounded grid barrier (the one between the stages of the
+ * persistent 2D run) in a cooperative launch of n_blocks blocks (1..1024); block
+ * skip_block (>= 0) leaves before the first round, so the others' wait runs out.
+ * Writes the device error bits (4 = a bounded wait gave up) and the number of
+ * arrivals to host memory; synchronises. */
+slim_status slim_selftest_barrier(int n_blocks, int skip_block, int rounds, int* err_bits,
+                                  int* arrivals);
 
 /* Number of kernels slim_step launches per call (for launch accounting). */
 int slim_step_kernel_count(const slim_state* s);

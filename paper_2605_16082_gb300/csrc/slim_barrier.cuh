@@ -1,0 +1,44 @@
+// Bounded grid-wide barrier for cooperative launches.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "slim_kernels.h"
+
+namespace slim {
+
+// Grid-wide barrier of a cooperative launch (all blocks resident): arrival counter
+// bar[0] and generation bar[1] in device memory.  The wait is bounded: after
+// kBarrierPolls polls the block records SLIM_ERRBIT_TIMEOUT and returns false, and
+// the kernel ends (the other blocks then time out at their next barrier).
+constexpr int kBarrierPolls = 1 << 21;  // about 0.15 s of 64-ns sleeps
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblk, int* err, int* s_fail) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    const unsigned g0 = *vgen;
+    __threadfence();
+    int fail = 0;
+    if (atomicAdd(bar, 1u) == nblk - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      int it = 0;
+      while (*vgen == g0) {
+        if (++it > kBarrierPolls) {
+          fail = 1;
+          atomicOr(err, (int)SLIM_ERRBIT_TIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    *s_fail = fail;
+  }
+  __syncthreads();
+  return *s_fail == 0;
+}
+
+}  // namespace slim

@@ -38,6 +38,7 @@ extern "C" slim_status slim_params_default(slim_params* p) {
   p->check_every = 0;
   p->blocks_per_sm = 0;
   p->use_graph = 1;
+  p->persistent_2d = 1;
   return SLIM_OK;
 }
 

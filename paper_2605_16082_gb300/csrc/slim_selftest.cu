@@ -1,6 +1,7 @@
 // Diagnostics of device building blocks against the compiler's own operations.
 #include <string>
 
+#include "slim_barrier.cuh"
 #include "slim_device.cuh"
 #include "slim_kernels.h"
 
@@ -36,10 +37,51 @@ __global__ void k_conv_check(long long n, unsigned long long seed, unsigned long
   }
 }
 
+// rounds of the grid barrier; block skip_block (if >= 0) leaves before the first
+__global__ void k_barrier_check(unsigned* bar, int* err, int skip_block, int rounds, int* arrivals) {
+  __shared__ int s_fail;
+  for (int r = 0; r < rounds; ++r) {
+    if ((int)blockIdx.x == skip_block) return;
+    if (threadIdx.x == 0) atomicAdd(arrivals, 1);
+    if (!grid_barrier(bar, gridDim.x, err, &s_fail)) return;
+  }
+}
+
 }  // namespace
 }  // namespace slim
 
 using namespace slim;
+
+extern "C" slim_status slim_selftest_barrier(int n_blocks, int skip_block, int rounds, int* err_bits,
+                                             int* arrivals) {
+  clear_error();
+  if (n_blocks < 1 || n_blocks > 1024 || rounds < 0 || !err_bits || !arrivals) {
+    set_error("bad argument");
+    return SLIM_ERR_ARG;
+  }
+  int* d = nullptr;  // [0] error bits, [1] arrivals, [2..3] barrier words
+  cudaError_t e = cudaMalloc((void**)&d, 4 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(d, 0, 4 * sizeof(int));
+  if (e == cudaSuccess) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_blocks);
+    cfg.blockDim = dim3(128);
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_barrier_check, reinterpret_cast<unsigned*>(d + 2), d, skip_block,
+                           rounds, d + 1);
+  }
+  int h[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  if (d) cudaFree(d);
+  if (e != cudaSuccess) { set_error(std::string("selftest: ") + cudaGetErrorString(e)); return SLIM_ERR_CUDA; }
+  *err_bits = h[0];
+  *arrivals = h[1];
+  return SLIM_OK;
+}
 
 extern "C" slim_status slim_selftest_conversions(long long n, unsigned long long seed,
                                                  long long* bad_d2f, long long* bad_f2d) {

@@ -12,6 +12,7 @@
 #include "slim_kernels.h"
 #include "slim_split.h"
 #include "slim_split_device.cuh"
+#include "slim_barrier.cuh"
 
 namespace slim {
 
@@ -26,6 +27,9 @@ struct SplitBufs {
   float* tide_f;  // the same stage values in FP32 (after the doubles in the same buffer)
   // mixed form: FP32 stage-increment sums of the 2D subcycle and FP32 1/(w/6)
   float *Dacc, *Eacc, *Gacc, *iw6_f;
+  // persistent 2D run: grid barrier words (arrival count, generation) and grid size
+  unsigned* bar;
+  int run_blocks;
   double *Qbx, *Qby;  // the state's time-averaged transport buffers
   // compute-type copies for the 3D kernels
   void *F2x_r, *F2y_r, *Dqx_r, *Dqy_r, *gcor_r, *st_half, *st_end;
@@ -479,9 +483,18 @@ struct Ext2dIO {
   void *eor, *Uor, *Vor;        // stage output shadow (RC); null in the FP64 form
 };
 
+// Loads of stage values: plain, or through L2 for values that other blocks of the
+// same (persistent) launch wrote (the L1 caches of the SMs are not coherent).
+struct LdPlain {
+  template <typename T> static __device__ __forceinline__ T ld(const T* p) { return *p; }
+};
+struct LdL2 {
+  template <typename T> static __device__ __forceinline__ T ld(const T* p) { return __ldcg(p); }
+};
+
 // Residual of the 2D stage at the RC state (er, Ur, Vr) of triangle t; Fe
 // receives the eta flux at the 6 edge points (edge-major, 2 points per edge).
-template <typename RC>
+template <typename RC, typename LD = LdPlain>
 __device__ __forceinline__ void ext2d_residual(const DevMesh& m, const SplitBufs& bf, const RC* er,
                                                const RC* Ur, const RC* Vr, RC g, RC tide, int t,
                                                RC Re[3], RC RU[3], RC RV[3], RC Fe[6]) {
@@ -490,7 +503,7 @@ __device__ __forceinline__ void ext2d_residual(const DevMesh& m, const SplitBufs
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int ia = a * nt + t;
-    e[a] = er[ia]; U[a] = Ur[ia]; V[a] = Vr[ia];
+    e[a] = LD::ld(er + ia); U[a] = LD::ld(Ur + ia); V[a] = LD::ld(Vr + ia);
     H[a] = Geo<RC>::h(m, ia) + e[a];
     gx[a] = Geo<RC>::gx(m, ia); gy[a] = Geo<RC>::gy(m, ia);
   }
@@ -518,9 +531,9 @@ __device__ __forceinline__ void ext2d_residual(const DevMesh& m, const SplitBufs
     if (ei.x >= 0) {
       const int l0 = ei.w & 3, l1 = (ei.w >> 2) & 3;
       const int i0 = l0 * nt + ei.x, i1 = l1 * nt + ei.x;
-      en0 = er[i0]; en1 = er[i1];
-      qn0 = Ur[i0] * nx + Vr[i0] * ny;
-      qn1 = Ur[i1] * nx + Vr[i1] * ny;
+      en0 = LD::ld(er + i0); en1 = LD::ld(er + i1);
+      qn0 = LD::ld(Ur + i0) * nx + LD::ld(Vr + i0) * ny;
+      qn1 = LD::ld(Ur + i1) * nx + LD::ld(Vr + i1) * ny;
     }
     const RC qo0 = U[a0] * nx + V[a0] * ny, qo1 = U[a1] * nx + V[a1] * ny;
 #pragma unroll
@@ -625,15 +638,15 @@ struct Mx2dIO {
   double *e, *U, *V;             // FP64 subcycle start, updated in place by KIND 2
 };
 
-template <int KIND>
-__global__ void __launch_bounds__(256)
-    k_ext2d_mx(DevMesh m, SplitBufs bf, Mx2dIO io, float g, int tide_idx, float dt, float wq,
-               double wn) {
+// one stage for triangle t (its own accumulators and FP64 state are only touched by
+// the thread that owns t)
+template <int KIND, typename LD>
+__device__ __forceinline__ void ext2d_mx_tri(const DevMesh& m, const SplitBufs& bf, const Mx2dIO& io,
+                                             float g, float tide, float dt, float wq, double wn,
+                                             int t) {
   const int nt = m.n_tri;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nt) return;
   float Re[3], RU[3], RV[3], Fe[6];
-  ext2d_residual<float>(m, bf, io.er, io.Ur, io.Vr, g, bf.tide_f[tide_idx], t, Re, RU, RV, Fe);
+  ext2d_residual<float, LD>(m, bf, io.er, io.Ur, io.Vr, g, tide, t, Re, RU, RV, Fe);
   const float bdw = dt * bf.iw6_f[t];
   const float* S3x = (const float*)bf.S3x_r;
   const float* S3y = (const float*)bf.S3y_r;
@@ -683,6 +696,38 @@ __global__ void __launch_bounds__(256)
         o[c][ia] = d2f_bits(qnew);
       }
     }
+  }
+}
+
+// The whole external run of the mixed form in one cooperative launch: every stage
+// of every subcycle over all triangles (grid-stride, so each triangle keeps its
+// thread), a grid barrier between stages.
+struct Mx2dRun {
+  Mx2dIO io[3];
+  int n_sub, tide_base;
+  float g, dt, wq;
+  double wn;
+  unsigned* bar;
+  int* err;
+};
+
+// Stages [first, first + count) of the run (stage index 3 q + kind); a grid
+// barrier between consecutive stages of one launch.  With count = 1 it is one
+// ordinary launch per stage (no barrier); the whole run is one cooperative launch.
+__global__ void __launch_bounds__(256) k_ext2d_run(DevMesh m, SplitBufs bf, Mx2dRun r, int first,
+                                                   int count) {
+  __shared__ int s_fail;
+  const int nt = m.n_tri;
+  const int stride = gridDim.x * blockDim.x;
+  for (int gs = first; gs < first + count; ++gs) {
+    const int st = gs % 3;
+    const float tide = bf.tide_f[r.tide_base + gs];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
+      if (st == 0) ext2d_mx_tri<0, LdL2>(m, bf, r.io[0], r.g, tide, r.dt, r.wq, r.wn, t);
+      else if (st == 1) ext2d_mx_tri<1, LdL2>(m, bf, r.io[1], r.g, tide, r.dt, r.wq, r.wn, t);
+      else ext2d_mx_tri<2, LdL2>(m, bf, r.io[2], r.g, tide, r.dt, r.wq, r.wn, t);
+    }
+    if (gs + 1 < first + count && !grid_barrier(r.bar, gridDim.x, r.err, &s_fail)) return;
   }
 }
 
@@ -1122,23 +1167,44 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, int tide_base,
       }
     }
   } else {
-    // FP32 stage values in the B and C shadows, FP64 state in A (updated by KIND 2)
-    const float gf = (float)s->par.g, dtf = (float)dts, wq = (float)(1.0 / (6.0 * n_sub));
-    const double wn = 1.0 / n_sub;
-    const float* A3[3] = {(const float*)b->Ae_r, (const float*)b->AU_r, (const float*)b->AV_r};
-    for (int q = 0; q < n_sub; ++q) {
-      for (int st = 0; st < 3; ++st) {
-        const int tide_idx = tide_base + 3 * q + st;
-        Mx2dIO io;
-        io.en = A3[0]; io.Un = A3[1]; io.Vn = A3[2];
-        io.e = b->Ae; io.U = b->AU; io.V = b->AV;
-        const int so = (st + 1) % 3;  // A -> B -> C -> A
-        io.er = (const float*)Fr[st][0]; io.Ur = (const float*)Fr[st][1]; io.Vr = (const float*)Fr[st][2];
-        io.eo = (float*)Fr[so][0]; io.Uo = (float*)Fr[so][1]; io.Vo = (float*)Fr[so][2];
+    // mixed: FP32 stage values in the B and C shadows, FP64 state in A (updated by
+    // the last stage of each subcycle); the whole run in one cooperative launch with
+    // a grid barrier between stages, or one launch per stage
+    Mx2dRun run;
+    for (int st = 0; st < 3; ++st) {
+      Mx2dIO& io = run.io[st];
+      io.en = (const float*)b->Ae_r; io.Un = (const float*)b->AU_r; io.Vn = (const float*)b->AV_r;
+      io.e = b->Ae; io.U = b->AU; io.V = b->AV;
+      const int so = (st + 1) % 3;
+      io.er = (const float*)Fr[st][0]; io.Ur = (const float*)Fr[st][1]; io.Vr = (const float*)Fr[st][2];
+      io.eo = (float*)Fr[so][0]; io.Uo = (float*)Fr[so][1]; io.Vo = (float*)Fr[so][2];
+    }
+    run.n_sub = n_sub;
+    run.tide_base = tide_base;
+    run.g = (float)s->par.g;
+    run.dt = (float)dts;
+    run.wq = (float)(1.0 / (6.0 * n_sub));
+    run.wn = 1.0 / n_sub;
+    run.bar = b->bar;
+    run.err = s->err;
+    if (s->par.persistent_2d) {
+      SLIM_CU(cudaMemsetAsync(b->bar, 0, sizeof(unsigned), stm));  // arrival count
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(b->run_blocks);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = stm;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      ProfScope ps(s, SLIM_PHASE_EXT2D, stm);
+      SLIM_CU(cudaLaunchKernelEx(&cfg, k_ext2d_run, m, *b, run, 0, 3 * n_sub));
+    } else {
+      for (int gs = 0; gs < 3 * n_sub; ++gs) {
         ProfScope ps(s, SLIM_PHASE_EXT2D, stm);
-        if (st == 0) k_ext2d_mx<0><<<grd, blk, 0, stm>>>(m, *b, io, gf, tide_idx, dtf, wq, wn);
-        if (st == 1) k_ext2d_mx<1><<<grd, blk, 0, stm>>>(m, *b, io, gf, tide_idx, dtf, wq, wn);
-        if (st == 2) k_ext2d_mx<2><<<grd, blk, 0, stm>>>(m, *b, io, gf, tide_idx, dtf, wq, wn);
+        k_ext2d_run<<<grd, blk, 0, stm>>>(m, *b, run, gs, 1);
         SLIM_CU(cudaGetLastError());
       }
     }
@@ -1273,7 +1339,17 @@ slim_status split_alloc(slim_state* s) {
   SLIM_CU(cudaMalloc((void**)&b->iw6_f, (size_t)m.n_tri * sizeof(float)));
   s->allocs.push_back(b->iw6_f);
   b->Dacc = b->Eacc = b->Gacc = nullptr;
+  b->bar = nullptr;
+  b->run_blocks = 0;
   if (s->esz == 4) {
+    SLIM_CU(cudaMalloc((void**)&b->bar, 2 * sizeof(unsigned)));
+    SLIM_CU(cudaMemset(b->bar, 0, 2 * sizeof(unsigned)));
+    s->allocs.push_back(b->bar);
+    int dev = 0, sms = 0, per_sm = 0;
+    SLIM_CU(cudaGetDevice(&dev));
+    SLIM_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SLIM_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ext2d_run, 256, 0));
+    b->run_blocks = std::max(1, std::min(sms * per_sm, (m.n_tri + 255) / 256));
     float** fa[] = {&b->Dacc, &b->Eacc, &b->Gacc};
     const size_t cnt[] = {3 * n2, 2 * n2, 2 * n2};
     for (int j = 0; j < 3; ++j) {
@@ -1357,8 +1433,10 @@ slim_status split_step(slim_state* s, double t, double dt, cudaStream_t st) {
 int split_kernel_count(const slim_state* s) {
   // time kernel; per stage: hpg, mompred, 3 n_sub_stage external stages, couple,
   // continuity, momentum, tracers; the mixed form's 2D shadow conversions (3 per stage)
+  // (the persistent mixed run is one launch per stage)
   const int n = s->par.n_sub;
-  return 1 + 2 * 6 + 3 * (n / 2 + n) + (s->prec == SLIM_MIXED ? 6 : 0);
+  const int ext = (s->prec == SLIM_MIXED && s->par.persistent_2d) ? 2 : 3 * (n / 2 + n);
+  return 1 + 2 * 6 + ext + (s->prec == SLIM_MIXED ? 6 : 0);
 }
 
 }  // namespace slim

@@ -28,7 +28,8 @@ EXPORTED = ["slim_params_default", "slim_status_string", "slim_last_error", "sli
             "slim_state_field_ptr", "slim_state_check", "slim_rhs3d", "slim_continuity",
             "slim_rhs2d", "slim_vertical_solve", "slim_hpg", "slim_step", "slim_tracer_mass",
             "slim_step_kernel_count", "slim_profile_begin", "slim_profile_end",
-            "slim_phase_name", "slim_tracer_mass_noalloc", "slim_selftest_conversions"]
+            "slim_phase_name", "slim_tracer_mass_noalloc", "slim_selftest_conversions",
+            "slim_selftest_barrier"]
 PHASES = ["continuity", "tracer_stage", "hpg", "mom_pred", "ext2d", "momentum", "tracers", "misc"]
 
 
@@ -37,7 +38,8 @@ class SlimParams(C.Structure):
         "g", "rho0", "coriolis_f", "eos_alpha", "eos_beta", "eos_T0", "eos_S0", "kappa_v",
         "nu_v", "kappa_h", "nu_h", "drag_cd", "flux_top", "flux_bot", "penalty_v", "penalty_h",
         "tide_amp", "tide_period")] + [(n, C.c_int) for n in (
-        "scheme", "n_sub", "tile_prisms", "check_every", "blocks_per_sm", "use_graph")]
+        "scheme", "n_sub", "tile_prisms", "check_every", "blocks_per_sm", "use_graph",
+        "persistent_2d")]
 
 
 class SlimError(RuntimeError):
@@ -84,6 +86,7 @@ def lib() -> C.CDLL:
             "slim_tracer_mass_noalloc": ([_vp, _i, _vp, _vp], _i),
             "slim_selftest_conversions": ([C.c_longlong, C.c_ulonglong, C.POINTER(C.c_longlong),
                                            C.POINTER(C.c_longlong)], _i),
+            "slim_selftest_barrier": ([_i, _i, _i, C.POINTER(_i), C.POINTER(_i)], _i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -232,6 +235,14 @@ def slim_selftest_conversions(n: int, seed: int = 0) -> tuple[int, int]:
     integer-pipe conversions against the GPU's own, over n seeded patterns."""
     a, b = C.c_longlong(-1), C.c_longlong(-1)
     _check(lib().slim_selftest_conversions(int(n), int(seed), C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def slim_selftest_barrier(n_blocks: int, skip_block: int, rounds: int) -> tuple[int, int]:
+    """(device error bits, arrivals) of `rounds` rounds of the bounded grid barrier."""
+    a, b = C.c_int(-1), C.c_int(-1)
+    _check(lib().slim_selftest_barrier(int(n_blocks), int(skip_block), int(rounds), C.byref(a),
+                                       C.byref(b)))
     return a.value, b.value
 
 

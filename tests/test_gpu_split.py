@@ -329,3 +329,34 @@ def test_split_full_size_in_the_bench_configuration(slim, basin_full):
                                    restrict3(ry, m, np.array([sd])).ravel()]))
         ref.append(np.concatenate([ox[:, :, pr].ravel(), oy[:, :, pr].ravel()]))
     assert rel_l2(np.concatenate(got), np.concatenate(ref)) < TOL_R
+
+
+@pytest.mark.parametrize("mesh", ["basin", "wide"])
+def test_persistent_2d_run_matches_stage_launches(slim, mesh):
+    """The mixed form's 2D run as one cooperative launch with a grid barrier between
+    stages gives the per-stage launches' result bit for bit, with and without the
+    CUDA graph; the wide mesh has more triangles than the launch has threads."""
+    m = case_mesh("basin") if mesh == "basin" else wl.c2_mesh(140_000, 2, 0)
+    ini = initial(m)
+    outs = []
+    for pers, graph in ((0, 0), (1, 0), (1, 1)):
+        p = params(slim)
+        p.persistent_2d, p.use_graph = pers, graph
+        with model(slim, m, slim.SLIM_MIXED, p, ini) as mod:
+            for n in range(3):
+                slim.slim_step(mod.state, n * 30.0, 30.0)
+            slim.slim_state_check(mod.state)
+            outs.append({f: mod.download(f) for f, _ in FIELDS3 + FIELDS2 + [("QBAR_X", "")]})
+    for o in outs[1:]:
+        for f in o:
+            assert np.array_equal(o[f], outs[0][f]), f
+
+
+def test_grid_barrier_rounds_and_bounded_timeout(slim):
+    """The grid barrier of the persistent run: 50 rounds of 8 blocks complete with
+    every arrival counted; a block that never arrives makes the others' bounded wait
+    run out, which is reported in the error bits (no hang, no fault)."""
+    bits, arr = slim.slim_selftest_barrier(8, -1, 50)
+    assert (bits, arr) == (0, 8 * 50)
+    bits, arr = slim.slim_selftest_barrier(8, 3, 5)
+    assert bits & 4 and arr == 7
