@@ -880,8 +880,7 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
   R* s_b = reinterpret_cast<R*>(smem + ob);                 // [12][TPX]
   R* s_W = s_b + 12 * (size_t)TPX;                          // [6][TPX]
   R* s_C = s_W + 6 * (size_t)TPX;                           // [3][4][TPX]
-  R* s_x = s_C + 12 * (size_t)TPX;                          // [12][TPX] f0 (implicit)
-  R* s_st = s_x + (IMPL ? 12 : 0) * (size_t)TPX;            // [3][TP]
+  R* s_st = s_C + 12 * (size_t)TPX;                         // [3][TP]
   const Tile tl = tile_of_block(m);
   const int i = threadIdx.x;
   const int nt = m.n_tri, P = m.P;
@@ -931,13 +930,11 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
       }
       R rr[2][2] = {{b[0][0] + dt * (F0[0][a] + add0), b[0][1] + dt * (F0[1][a] + add0)},
                     {b[1][0] + dt * (F1[0][a] + add1), b[1][1] + dt * (F1[1][a] + add1)}};
-      {
-        // + dt A(W, st) f, A couples the layers above and below.  Explicit: the
-        // evaluation state on its geometry.  Implicit (increment form): the start
-        // state f0 with the operator of the column solve (geometry st1), so that
-        // the solve runs on rhs - (M1 - dt A) f0 and returns the increment.
+      if (!IMPL) {
+        // + dt A(W, st_ev) f_ev, A couples the layers above and below (the implicit
+        // update adds dt A f0 inside the column solve instead)
         const R kap = ua.kap_v, pen = pp.pen_v;
-        const R stv = IMPL ? st1[ia] : in.st[ia];
+        const R stv = in.st[ia];
         const R dz = dr * stv, idz = rcp<R>(dz);
         R idzm = idz, idzp = idz;
         if (m.n_levels != 0) {
@@ -948,9 +945,8 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
         const R Wn = (k + 1 < N) ? W[(size_t)a * P + p + 1] : (R)0;
         R A[2][2], AL[2][2], AU[2][2];
         vertical_A<R>(k, N, w6, idzm, idz, idzp, W0, W1, Wn, kap, pen, A, AL, AU);
-        const R* Fs[2] = {IMPL ? G0 : (in.F0 ? in.F0 : in.U), IMPL ? G1 : (in.F1 ? in.F1 : in.V)};
-        const R fk[2][2] = {{IMPL ? g00 : own.f0[0][a], IMPL ? g01 : own.f0[1][a]},
-                            {IMPL ? g10 : own.f1[0][a], IMPL ? g11 : own.f1[1][a]}};
+        const R* Fs[2] = {in.F0 ? in.F0 : in.U, in.F1 ? in.F1 : in.V};
+        const R fk[2][2] = {{own.f0[0][a], own.f0[1][a]}, {own.f1[0][a], own.f1[1][a]}};
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           R fm0 = 0, fm1 = 0, fp0 = 0, fp1 = 0;
@@ -967,10 +963,6 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
         s_b[(1 * 3 + a) * TPX + slot] = rr[0][1];
         s_b[(2 * 3 + a) * TPX + slot] = rr[1][0];
         s_b[(3 * 3 + a) * TPX + slot] = rr[1][1];
-        s_x[(0 * 3 + a) * TPX + slot] = g00;
-        s_x[(1 * 3 + a) * TPX + slot] = g01;
-        s_x[(2 * 3 + a) * TPX + slot] = g10;
-        s_x[(3 * 3 + a) * TPX + slot] = g11;
       } else {
         // M1^-1: (6 / (J_h hz1)) [[2,-1],[-1,2]] per vertex-layer
         const R hz1 = (R)0.5 * dr * st1[ia];
@@ -988,6 +980,44 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
   }
   if (IMPL) {
     __syncthreads();
+    // increment form: every prism adds dt A(W, st1) f0 to its own rows of rhs - M1 f0
+    // from the tile's shared arrays (in parallel, before the column sweeps)
+    if (i < tl.np) {
+      const int lt = tile_tri_of(s_off, tl.nt, i);
+      const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
+      const R w6 = Geo<R>::jh(m, t) * (R)(1.0 / 6.0);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int ia = a * nt + t;
+        const R stv = s_st[a * TP + lt];
+        const R dz = dz_rest_r<R>(m, ia, k, N) * stv, idz = rcp<R>(dz);
+        R idzm = idz, idzp = idz;
+        if (m.n_levels != 0) {
+          if (k > 0) idzm = rcp<R>(dz_rest_r<R>(m, ia, k - 1, N) * stv);
+          if (k + 1 < N) idzp = rcp<R>(dz_rest_r<R>(m, ia, k + 1, N) * stv);
+        }
+        const R W0 = s_W[a * TPX + slot], W1 = s_W[(3 + a) * TPX + slot];
+        const R Wn = (k + 1 < N) ? s_W[a * TPX + slot + 1] : (R)0;
+        R A[2][2], AL[2][2], AU[2][2];
+        vertical_A<R>(k, N, w6, idzm, idz, idzp, W0, W1, Wn, ua.kap_v, pp.pen_v, A, AL, AU);
+        const int p = tl.p0 + i;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const R* Gq = q ? G1 : G0;
+          const R* xt = Gq + (size_t)a * P + p;   // top nodes of field q (global, L2)
+          const R* xb = Gq + (size_t)(3 + a) * P + p;
+          R fm0 = 0, fm1 = 0, fp0 = 0, fp1 = 0;
+          if (k > 0) { fm0 = xt[-1]; fm1 = xb[-1]; }
+          if (k + 1 < N) { fp0 = xt[1]; fp1 = xb[1]; }
+          const R f0 = xt[0], f1 = xb[0];
+          s_b[(2 * q * 3 + a) * TPX + slot] +=
+              dt * (A[0][0] * f0 + A[0][1] * f1 + AL[0][0] * fm0 + AL[0][1] * fm1 + AU[0][0] * fp0 + AU[0][1] * fp1);
+          s_b[((2 * q + 1) * 3 + a) * TPX + slot] +=
+              dt * (A[1][0] * f0 + A[1][1] * f1 + AL[1][0] * fm0 + AL[1][1] * fm1 + AU[1][0] * fp0 + AU[1][1] * fp1);
+        }
+      }
+    }
+    __syncthreads();
     for (int j = threadIdx.x; j < 3 * tl.nt; j += TP) {
       const int a = j / tl.nt, lt = j - a * tl.nt;
       const int t = tl.t0 + lt, base = s_off[lt] + lt, N = s_off[lt + 1] - s_off[lt];
@@ -1004,8 +1034,9 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
       for (int c = 0; c < 2; ++c)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          o0[c][a] = s_x[(c * 3 + a) * TPX + slot] + s_b[(c * 3 + a) * TPX + slot];
-          o1[c][a] = s_x[((2 + c) * 3 + a) * TPX + slot] + s_b[((2 + c) * 3 + a) * TPX + slot];
+          const size_t idx = (size_t)(c * 3 + a) * P + tl.p0 + i;
+          o0[c][a] = G0[idx] + s_b[(c * 3 + a) * TPX + slot];
+          o1[c][a] = G1[idx] + s_b[((2 + c) * 3 + a) * TPX + slot];
         }
     }
   }
@@ -1027,10 +1058,10 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
 size_t tile_smem(const DevMesh& m, int TP, size_t esz, int rows) {
   return ((TP + 1) * sizeof(int) + 15) / 16 * 16 + (size_t)rows * (TP + m.max_tile_tris) * esz;
 }
-// s_b [12], s_W [6], s_C [12] (+ s_x [12] for the implicit update) x TPX, s_st [3] x TP
-size_t update_smem(const DevMesh& m, int TP, size_t esz, bool impl) {
-  return ((TP + 1) * sizeof(int) + 15) / 16 * 16 +
-         (size_t)(impl ? 42 : 30) * (TP + m.max_tile_tris) * esz + (size_t)3 * TP * esz;
+// s_b [12], s_W [6], s_C [12] x TPX, s_st [3] x TP
+size_t update_smem(const DevMesh& m, int TP, size_t esz, bool) {
+  return ((TP + 1) * sizeof(int) + 15) / 16 * 16 + (size_t)30 * (TP + m.max_tile_tris) * esz +
+         (size_t)3 * TP * esz;
 }
 
 template <typename R>
