@@ -27,6 +27,9 @@ struct SplitBufs {
   float* tide_f;  // the same stage values in FP32 (after the doubles in the same buffer)
   // mixed form: FP32 stage-increment sums of the 2D subcycle and FP32 1/(w/6)
   float *Dacc, *Eacc, *Gacc, *iw6_f;
+  // non-advective momentum terms (viscosity, Coriolis, -r/rho0, drag) of the stage's
+  // evaluation state, [6][P] each: written by the prediction, read by the update
+  void *Ex, *Ey;
   // persistent 2D run: grid barrier words (arrival count, generation) and grid size
   unsigned* bar;
   int run_blocks;
@@ -410,7 +413,7 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
     k_mompred(DevMesh m, AdvIn<R> in, const R* __restrict__ Rx, const R* __restrict__ Ry,
               PP<R> pp, double* __restrict__ S3x, double* __restrict__ S3y,
               double* __restrict__ Sqx, double* __restrict__ Sqy, R* __restrict__ S3x_r,
-              R* __restrict__ S3y_r) {
+              R* __restrict__ S3y_r, R* __restrict__ Ex, R* __restrict__ Ey) {
   extern __shared__ __align__(16) unsigned char smem[];
   int* s_off = reinterpret_cast<int*>(smem);
   const int TPX = TP + m.max_tile_tris;
@@ -426,7 +429,18 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
     const int p = tl.p0 + i, slot = i + lt;
     R Fx[2][3] = {{0, 0, 0}, {0, 0, 0}}, Fy[2][3] = {{0, 0, 0}, {0, 0, 0}}, qx[2][3], qy[2][3];
     prism_adv<R, false>(m, t, k, p, N, own, in, Fx, Fy, qx, qy);
-    momentum_extras<R>(m, t, k, p, N, own, in.U, in.V, in.st, Rx, Ry, pp, Fx, Fy);
+    // the non-advective terms are the update's too (same state): kept for it
+    R ex[2][3] = {{0, 0, 0}, {0, 0, 0}}, ey[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    momentum_extras<R>(m, t, k, p, N, own, in.U, in.V, in.st, Rx, Ry, pp, ex, ey);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        Fx[c][a] += ex[c][a];
+        Fy[c][a] += ey[c][a];
+        Ex[(size_t)(c * 3 + a) * m.P + p] = ex[c][a];
+        Ey[(size_t)(c * 3 + a) * m.P + p] = ey[c][a];
+      }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       s_v[(0 * 3 + a) * TPX + slot] = Fx[0][a] + Fx[1][a];
@@ -857,6 +871,7 @@ __global__ void __launch_bounds__(TP, (MB<R, TP>::value))
 // ---------------------------------------------------------------------------
 // 3D update of a field pair (KIND 0: momentum u, v; KIND 1: tracers T, S)
 //   M1 f1 = M0 f0 + dt (R_h(f_ev; qbar) + extras [+ M1 F2D/H1] [+ A f_ev]),
+// the momentum extras (Ex, Ey) stored by the prediction of the same state,
 // implicit: (M1 - dt A(W, st1)) f1 = ... without A f_ev.
 // ---------------------------------------------------------------------------
 template <typename R>
@@ -869,7 +884,7 @@ struct UA {
 template <typename R, int TP, int KIND, bool IMPL, int OCC>
 __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
     k_update(DevMesh m, AdvIn<R> in, const R* __restrict__ G0, const R* __restrict__ G1,
-             const R* __restrict__ W, const R* __restrict__ Rx, const R* __restrict__ Ry,
+             const R* __restrict__ W, const R* __restrict__ Ex, const R* __restrict__ Ey,
              const R* __restrict__ F2x, const R* __restrict__ F2y, const R* __restrict__ st0,
              const R* __restrict__ st1, PP<R> pp, UA<R> ua, R* O0, R* O1,
              int* __restrict__ err) {
@@ -905,7 +920,14 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
     prism_adv<R, false>(m, t, k, p, N, own, in, F0, F1, qx, qy);
     const R w6 = Geo<R>::jh(m, t) * (R)(1.0 / 6.0);
     if (KIND == 0) {
-      momentum_extras<R>(m, t, k, p, N, own, in.U, in.V, in.st, Rx, Ry, pp, F0, F1);
+      // viscosity, Coriolis, -r/rho0 and drag of this state, from the prediction
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          F0[c][a] += Ex[(size_t)(c * 3 + a) * P + p];
+          F1[c][a] += Ey[(size_t)(c * 3 + a) * P + p];
+        }
     } else if (ua.kap_h > (R)0) {
       prism_sipg2<R>(m, t, k, N, own.f0, own.f1, in.F0, in.F1, in.st, ua.kap_h, pp.pen_h, F0, F1);
     }
@@ -1103,7 +1125,7 @@ cudaError_t launch_mompred(const DevMesh& m, int TP, int occ, const AdvIn<R>& in
     cudaError_t e = set_smem2(k_mompred<R, TPc, OCc>, sm);
     if (e != cudaSuccess) return e;
     k_mompred<R, TPc, OCc><<<m.n_tiles, TPc, sm, s>>>(m, in, Rx, Ry, pp, b->S3x, b->S3y, b->Sqx, b->Sqy,
-                                                 (R*)b->S3x_r, (R*)b->S3y_r);
+                                                 (R*)b->S3x_r, (R*)b->S3y_r, (R*)b->Ex, (R*)b->Ey);
   });
   return cudaGetLastError();
 }
@@ -1122,14 +1144,14 @@ cudaError_t launch_cont_split(const DevMesh& m, int TP, const AdvIn<R>& in, cons
 
 template <typename R, int KIND, bool IMPL>
 cudaError_t launch_update(const DevMesh& m, int TP, int occ, const AdvIn<R>& in, const R* G0, const R* G1,
-                          const R* W, const R* Rx, const R* Ry, const R* F2x, const R* F2y,
+                          const R* W, const R* Ex, const R* Ey, const R* F2x, const R* F2y,
                           const R* st0, const R* st1, const PP<R>& pp, const UA<R>& ua,
                           R* O0, R* O1, int* err, cudaStream_t s) {
   SLIM_TPO_SWITCH(R, TP, occ, {
     const size_t sm = update_smem(m, TPc, sizeof(R), IMPL);
     cudaError_t e = set_smem2(k_update<R, TPc, KIND, IMPL, OCc>, sm);
     if (e != cudaSuccess) return e;
-    k_update<R, TPc, KIND, IMPL, OCc><<<m.n_tiles, TPc, sm, s>>>(m, in, G0, G1, W, Rx, Ry, F2x, F2y, st0,
+    k_update<R, TPc, KIND, IMPL, OCc><<<m.n_tiles, TPc, sm, s>>>(m, in, G0, G1, W, Ex, Ey, F2x, F2y, st0,
                                                             st1, pp, ua, O0, O1, err);
   });
   return cudaGetLastError();
@@ -1268,10 +1290,12 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, int tide_base,
   {
     ProfScope ps(s, SLIM_PHASE_MOMENTUM, stm);
     if (implicit)
-      SLIM_CU((launch_update<R, 0, true>(m, TP, occ, cin, U0, V0, (const R*)s->W, Rx, Ry, (const R*)b->F2x_r,
+      SLIM_CU((launch_update<R, 0, true>(m, TP, occ, cin, U0, V0, (const R*)s->W, (const R*)b->Ex,
+                                         (const R*)b->Ey, (const R*)b->F2x_r,
                                          (const R*)b->F2y_r, st0, st1, pp, um, u_out, v_out, s->err, stm)));
     else
-      SLIM_CU((launch_update<R, 0, false>(m, TP, occ, cin, U0, V0, (const R*)s->W, Rx, Ry, (const R*)b->F2x_r,
+      SLIM_CU((launch_update<R, 0, false>(m, TP, occ, cin, U0, V0, (const R*)s->W, (const R*)b->Ex,
+                                          (const R*)b->Ey, (const R*)b->F2x_r,
                                           (const R*)b->F2y_r, st0, st1, pp, um, u_out, v_out, s->err, stm)));
   }
   {
@@ -1391,6 +1415,11 @@ slim_status split_alloc(slim_state* s) {
   }
   b->Qbx = s->Qbx;
   b->Qby = s->Qby;
+  for (void** p : {&b->Ex, &b->Ey}) {
+    SLIM_CU(cudaMalloc(p, (size_t)6 * m.P * s->esz));
+    SLIM_CU(cudaMemset(*p, 0, (size_t)6 * m.P * s->esz));
+    s->allocs.push_back(*p);
+  }
   SLIM_CU(cudaMalloc(&b->gcor_r, n2 * 2 * s->esz));
   SLIM_CU(cudaMemset(b->gcor_r, 0, n2 * 2 * s->esz));
   s->allocs.push_back(b->gcor_r);
