@@ -43,6 +43,47 @@ class Params:
     tide_amp: float = 1.0
     tide_period: float = 44712.0
     n_sub: int = 20
+    forcing: bool = False        # prescribed exterior velocity / tracers (Forcing)
+
+
+@dataclasses.dataclass
+class Forcing:
+    """Open-boundary forcing given at two times t_a < t_b and linear in time between
+    them (Sec. 3, data management: forcing fields vary linearly between two input
+    states and are interpolated where they are used): exterior velocity (u, v) and
+    tracers (T, S) at the open-boundary nodes, (2, 3, P) like the state.  theta(t) =
+    (t - t_a)/(t_b - t_a) is not clamped, so the data stay linear in time."""
+    t_a: float
+    t_b: float
+    u_a: np.ndarray
+    v_a: np.ndarray
+    u_b: np.ndarray
+    v_b: np.ndarray
+    T_a: np.ndarray
+    S_a: np.ndarray
+    T_b: np.ndarray
+    S_b: np.ndarray
+
+    def theta(self, t: float) -> float:
+        return (t - self.t_a) / (self.t_b - self.t_a)
+
+    def at(self, t: float):
+        th = self.theta(t)
+        lerp = lambda a, b: a + th * (b - a)
+        return lerp(self.u_a, self.u_b), lerp(self.v_a, self.v_b), lerp(self.T_a, self.T_b), lerp(self.S_a, self.S_b)
+
+
+def exterior_transport(om: OMesh, u_x, v_x):
+    """Exterior layer transport q_ext = (dz_rest/2) u_ext at the nodes (the rest
+    thickness, so that its column sum is linear in time with the data)."""
+    return tr.transport(om.thickness(np.zeros((3, om.n_tri))), u_x, v_x)
+
+
+def exterior_column_transport(om: OMesh, u_x, v_x):
+    """Q_ext = column sum of q_ext (3, n_tri): the 2D exterior transport as the
+    vertical sum of the 3D one (the linear-transport consistency of Sec. 2.5)."""
+    qx, qy = exterior_transport(om, u_x, v_x)
+    return tr.column_sum(om, qx), tr.column_sum(om, qy)
 
 
 @dataclasses.dataclass
@@ -56,6 +97,7 @@ class State:
     V: np.ndarray
     T_ext: np.ndarray | None = None
     S_ext: np.ndarray | None = None
+    forcing: Forcing | None = None
 
 
 # 2-point Gauss along edges: parameter lam from vertex e (0) to vertex e+1 (1)
@@ -282,12 +324,16 @@ def bottom_drag(om: OMesh, par: Params, u: np.ndarray, v: np.ndarray) -> tuple[n
     return Dx, Dy
 
 
-def momentum_horizontal(om: OMesh, par: Params, u, v, qx, qy, rx, ry, dz, face_corr=None):
+def momentum_horizontal(om: OMesh, par: Params, u, v, qx, qy, rx, ry, dz, face_corr=None, ext=None):
     """F_3D^h(u, q, r) (Eq. 11): advection -div(q u) (upwind), horizontal viscosity,
     Coriolis -f e_z x u, baroclinic pressure gradient -r/rho0 (lumped mass), bottom
-    drag.  dz: layer thickness of the transport geometry."""
-    Fx = tr.horizontal_residual(om, qx, qy, u, face_corr=face_corr)
-    Fy = tr.horizontal_residual(om, qx, qy, v, face_corr=face_corr)
+    drag.  dz: layer thickness of the transport geometry.  ext = (u_ext, v_ext,
+    qx_ext, qy_ext): prescribed exterior velocity and transport at open boundaries."""
+    ux = vx = qe = None
+    if ext is not None:
+        ux, vx, qe = ext[0], ext[1], (ext[2], ext[3])
+    Fx = tr.horizontal_residual(om, qx, qy, u, T_ext=ux, face_corr=face_corr, q_ext=qe)
+    Fy = tr.horizontal_residual(om, qx, qy, v, T_ext=vx, face_corr=face_corr, q_ext=qe)
     Fx += horizontal_viscosity(om, dz, u, par.nu_h, par.penalty_h)
     Fy += horizontal_viscosity(om, dz, v, par.nu_h, par.penalty_h)
     Fx += lumped_source(om, dz, par.f * v - rx / par.rho0)
@@ -303,7 +349,7 @@ def tide(par: Params, t: float) -> float:
     return par.tide_amp * math.cos(2.0 * math.pi * t / par.tide_period)
 
 
-def mode2d_residual(om: OMesh, par: Params, eta, U, V, time: float):
+def mode2d_residual(om: OMesh, par: Params, eta, U, V, time: float, Q_ext=None):
     """(R_eta, R_U, R_V) (3, n_tri) and the numerical eta flux at every edge point
     (n_tri, 3, 2) for the state (eta, Q = (U, V)):
       R_eta,a = int Q . grad phi_a - oint phi_a F_eta
@@ -311,7 +357,8 @@ def mode2d_residual(om: OMesh, par: Params, eta, U, V, time: float):
     with H = h + eta, c = sqrt(g (h^- + h^+)/2) (rest depth) at each edge point,
       F_eta = {Q}.n + c/2 (eta^- - eta^+),   eta^ = {eta} + (q^- - q^+)/(2c)
     (upwind flux of the linear wave system).  Walls: eta^+ = eta^-, q^+ = -q^-.
-    Open boundary: eta^+ = A cos(2 pi t / T_M2), Q^+ = Q^-."""
+    Open boundary: eta^+ = A cos(2 pi t / T_M2), Q^+ = Q^- (or the prescribed
+    exterior transport Q_ext = (Qx, Qy) at this time, (3, n_tri))."""
     nt = om.n_tri
     g = par.g
     h = om.h.T                                             # (3, n_tri)
@@ -352,8 +399,12 @@ def mode2d_residual(om: OMesh, par: Params, eta, U, V, time: float):
             qn = (wv[0] * (U[l0, nbs] * n[:, 0] + V[l0, nbs] * n[:, 1])
                   + wv[1] * (U[l1, nbs] * n[:, 0] + V[l1, nbs] * n[:, 1]))
             # exterior states
+            q_open = qo
+            if Q_ext is not None:
+                q_open = (wv[0] * (Q_ext[0][own[0]] * n[:, 0] + Q_ext[1][own[0]] * n[:, 1])
+                          + wv[1] * (Q_ext[0][own[1]] * n[:, 0] + Q_ext[1][own[1]] * n[:, 1]))
             e_ext = np.where(ok, en, np.where(is_open, A_tide, eo))
-            q_ext = np.where(ok, qn, np.where(is_open, qo, -qo))
+            q_ext = np.where(ok, qn, np.where(is_open, q_open, -qo))
             # wave speed of the rest depth (the linear-wave Riemann problem)
             ho = wv[0] * h[own[0]] + wv[1] * h[own[1]]
             hn = wv[0] * h[l0, nbs] + wv[1] * h[l1, nbs]
@@ -376,12 +427,15 @@ SSP_B = (1.0, 0.25, 2.0 / 3.0)
 SSP_BUTCHER_B = (1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0)
 
 
-def mode2d_run(om: OMesh, par: Params, eta0, U0, V0, S3x, S3y, t0: float, T_total: float, n: int):
+def mode2d_run(om: OMesh, par: Params, eta0, U0, V0, S3x, S3y, t0: float, T_total: float, n: int,
+               Q_ab=None, forcing: Forcing | None = None):
     """n SSP-RK3 subcycles of length T_total/n of the 2D mode with the frozen 3D
     source S3 (column sums of F_3D^h).  Returns the end state, the time-averaged
     transport Qbar = (1/n) sum_m sum_s b_s Q^(m,s) (b = 1/6, 1/6, 2/3: the weights
     with which the stage inputs enter the update, so that eta_end - eta0 =
-    -T_total (6/J_h) div(Qbar, Gbar)) and the matching average eta face flux Gbar."""
+    -T_total (6/J_h) div(Qbar, Gbar)) and the matching average eta face flux Gbar.
+    With forcing, Q_ab = (Q_ext at t_a, Q_ext at t_b) and the open boundary takes
+    Q_ext(t) = Q_a + theta(t)(Q_b - Q_a) at each stage time."""
     w = np.tile(om.Jh / 6.0, (3, 1))
     dts = T_total / n
     eta, U, V = eta0.copy(), U0.copy(), V0.copy()
@@ -392,7 +446,12 @@ def mode2d_run(om: OMesh, par: Params, eta0, U0, V0, S3x, S3y, t0: float, T_tota
         e_n, U_n, V_n = eta, U, V
         e_s, U_s, V_s = eta, U, V
         for s in range(3):
-            Re, RU, RV, Fe = mode2d_residual(om, par, e_s, U_s, V_s, time + stage_t[s] * dts)
+            ts = time + stage_t[s] * dts
+            Qx = None
+            if forcing is not None:
+                th = forcing.theta(ts)
+                Qx = (Q_ab[0][0] + th * (Q_ab[1][0] - Q_ab[0][0]), Q_ab[0][1] + th * (Q_ab[1][1] - Q_ab[0][1]))
+            Re, RU, RV, Fe = mode2d_residual(om, par, e_s, U_s, V_s, ts, Q_ext=Qx)
             bw = SSP_BUTCHER_B[s] / n
             Qbx += bw * U_s; Qby += bw * V_s; Gb += bw * Fe
             e_new = SSP_A[s] * e_n + SSP_B[s] * (e_s + dts * Re / w)
@@ -424,12 +483,14 @@ def corrected_transport(om: OMesh, dz, qx, qy, Qbx, Qby):
     return qx + 0.5 * (frac * Dx)[None], qy + 0.5 * (frac * Dy)[None]
 
 
-def face_correction(om: OMesh, dz, Qbx, Qby, Gb):
+def face_correction(om: OMesh, dz, Qbx, Qby, Gb, Q_ext=None):
     """Per prism and lateral-face quadrature point, the additive correction of the
     normal transport c_k (Gbar - {Qbar}.n)/2 (units of q.n) that makes the column sum
     of the 3D lateral fluxes equal the 2D averaged face flux Gbar.  c_k = layer
     fraction of the face: (dz_k^- + dz_k^+) / sum over paired layers (own only at an
-    open boundary).  Walls: 0.  Returns (P, 3, 2) [p][edge][edge point]."""
+    open boundary).  {Qbar} on an open boundary is the interior Qbar, or with a
+    prescribed exterior transport Q_ext (3, n_tri) the mean of both.  Walls: 0.
+    Returns (P, 3, 2) [p][edge][edge point]."""
     P = om.P
     t, k = om.t_of, om.k_of
     corr = np.zeros((P, 3, 2))
@@ -459,7 +520,12 @@ def face_correction(om: OMesh, dz, Qbx, Qby, Gb):
             ln0, ln1 = np.where(has_nb, loc[:, 0], 0), np.where(has_nb, loc[:, 1], 0)
             Qn = (wv[0] * (Qbx[ln0, tn] * n[:, 0] + Qby[ln0, tn] * n[:, 1])
                   + wv[1] * (Qbx[ln1, tn] * n[:, 0] + Qby[ln1, tn] * n[:, 1]))
-            Qavg = np.where(has_nb, 0.5 * (Qo + Qn), Qo)
+            Q_open = Qo
+            if Q_ext is not None:
+                Qx = (wv[0] * (Q_ext[0][own[0], t] * n[:, 0] + Q_ext[1][own[0], t] * n[:, 1])
+                      + wv[1] * (Q_ext[0][own[1], t] * n[:, 0] + Q_ext[1][own[1], t] * n[:, 1]))
+                Q_open = 0.5 * (Qo + Qx)
+            Qavg = np.where(has_nb, 0.5 * (Qo + Qn), Q_open)
             delta = Gb[t, e, gi] - Qavg
             ck = np.where(tot > 0, pair / np.where(tot > 0, tot, 1.0), 0.0)
             corr[:, e, gi] = np.where(ok | is_open, 0.5 * ck * delta, 0.0)
@@ -497,27 +563,40 @@ def split_stage(om: OMesh, par: Params, st0: State, ev: State, t0: float, dt: fl
     tracers (the component order of Sec. 2, Fig. 1a; turbulence is not built)."""
     dz_ev = om.thickness(ev.eta)
     dz0 = om.thickness(st0.eta)
+    # open-boundary forcing: the 2D run of this stage spans [t0, t0 + dt] and sees
+    # Q_ext(t) linear in t; the 3D terms take the exterior state at the middle of
+    # that run, whose column transport is the run's average of Q_ext
+    Fo = st0.forcing if par.forcing else None
+    ext3 = qe = Q_mid = Q_ab = None
+    T_x, S_x = st0.T_ext, st0.S_ext
+    if Fo is not None:
+        ux, vx, T_x, S_x = Fo.at(t0 + 0.5 * dt)
+        qe = exterior_transport(om, ux, vx)
+        ext3 = (ux, vx, qe[0], qe[1])
+        Q_mid = exterior_column_transport(om, ux, vx)
+        Q_ab = (exterior_column_transport(om, Fo.u_a, Fo.v_a), exterior_column_transport(om, Fo.u_b, Fo.v_b))
     # 1. density and horizontal pressure gradient
     rx, ry = hpg(om, par, ev.T, ev.S, ev.eta)
     # 2. prediction of F_3D^h with the transport q of the evaluation state
     qx, qy = tr.transport(dz_ev, ev.u, ev.v)
-    Fpx, Fpy = momentum_horizontal(om, par, ev.u, ev.v, qx, qy, rx, ry, dz_ev)
+    Fpx, Fpy = momentum_horizontal(om, par, ev.u, ev.v, qx, qy, rx, ry, dz_ev, ext=ext3)
     S3x, S3y = _col_sum3(om, Fpx), _col_sum3(om, Fpy)
     # 3. external mode from the state at t0
-    eta1, U1, V1, Qbx, Qby, Gb = mode2d_run(om, par, st0.eta, st0.U, st0.V, S3x, S3y, t0, dt, n_sub)
+    eta1, U1, V1, Qbx, Qby, Gb = mode2d_run(om, par, st0.eta, st0.U, st0.V, S3x, S3y, t0, dt, n_sub,
+                                            Q_ab=Q_ab, forcing=Fo)
     # 4. 2D momentum forcing F2D = (Q1 - (Q0 + dt S3/w))/dt
     w = np.tile(om.Jh / 6.0, (3, 1))
     F2x = (U1 - (st0.U + dt * S3x / w)) / dt
     F2y = (V1 - (st0.V + dt * S3y / w)) / dt
     # 5. corrected transport and the vertical flux (continuity over [t0, t0 + dt])
     qbx, qby = corrected_transport(om, dz_ev, qx, qy, Qbx, Qby)
-    corr = face_correction(om, dz_ev, Qbx, Qby, Gb)
+    corr = face_correction(om, dz_ev, Qbx, Qby, Gb, Q_ext=Q_mid)
     dz1 = om.thickness(eta1)
-    R1 = tr.horizontal_residual(om, qbx, qby, np.ones_like(qbx), face_corr=corr)
+    R1 = tr.horizontal_residual(om, qbx, qby, np.ones_like(qbx), face_corr=corr, q_ext=qe)
     F = R1 - ((om.Jh[om.t_of] / 12.0)[None] * (dz1 - dz0) / dt)[None]
     W = tr.solve_continuity(om, F)
     # 6. momentum: M1 u1 = M0 u0 + dt (F_3D^h(u_ev, qbar, r) + M1 F2D/H1 + [A u1 | A u_ev])
-    Fx, Fy = momentum_horizontal(om, par, ev.u, ev.v, qbx, qby, rx, ry, dz_ev, face_corr=corr)
+    Fx, Fy = momentum_horizontal(om, par, ev.u, ev.v, qbx, qby, rx, ry, dz_ev, face_corr=corr, ext=ext3)
     H1 = np.zeros((3, om.n_tri))
     for a in range(3):
         np.add.at(H1[a], om.t_of, dz1[a])
@@ -527,8 +606,8 @@ def split_stage(om: OMesh, par: Params, st0: State, ev: State, t0: float, dt: fl
     rhs_u = tr.apply_mass(om, dz0, st0.u) + dt * (Fx + cpl_x)
     rhs_v = tr.apply_mass(om, dz0, st0.v) + dt * (Fy + cpl_y)
     # tracers: M1 T1 = M0 T0 + dt (R_h(T_ev, qbar) + [A T1 | A T_ev])
-    RT = tr.horizontal_residual(om, qbx, qby, ev.T, T_ext=st0.T_ext, face_corr=corr)
-    RS = tr.horizontal_residual(om, qbx, qby, ev.S, T_ext=st0.S_ext, face_corr=corr)
+    RT = tr.horizontal_residual(om, qbx, qby, ev.T, T_ext=T_x, face_corr=corr, q_ext=qe)
+    RS = tr.horizontal_residual(om, qbx, qby, ev.S, T_ext=S_x, face_corr=corr, q_ext=qe)
     RT += horizontal_viscosity(om, dz_ev, ev.T, par.kappa_h, par.penalty_h)
     RS += horizontal_viscosity(om, dz_ev, ev.S, par.kappa_h, par.penalty_h)
     rhs_T = tr.apply_mass(om, dz0, st0.T) + dt * RT
@@ -549,7 +628,8 @@ def split_stage(om: OMesh, par: Params, st0: State, ev: State, t0: float, dt: fl
     if diag is not None:
         diag.update(W=W, r=(rx, ry), S3=(S3x, S3y), F2D=(F2x, F2y), Qbar=(Qbx, Qby), Gbar=Gb,
                     qbar=(qbx, qby), corr=corr, F3h=(Fx, Fy), R1=R1)
-    return State(u=u1, v=v1, T=T1, S=S1, eta=eta1, U=U1, V=V1, T_ext=st0.T_ext, S_ext=st0.S_ext)
+    return State(u=u1, v=v1, T=T1, S=S1, eta=eta1, U=U1, V=V1, T_ext=st0.T_ext, S_ext=st0.S_ext,
+                 forcing=st0.forcing)
 
 
 def split_step(om: OMesh, par: Params, st: State, t: float, dt: float, diag1=None, diag2=None) -> State:

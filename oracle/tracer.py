@@ -44,7 +44,8 @@ def transport(dz: np.ndarray, u: np.ndarray, v: np.ndarray) -> tuple[np.ndarray,
 
 def horizontal_residual(om: OMesh, qx: np.ndarray, qy: np.ndarray, T: np.ndarray,
                         T_ext: np.ndarray | None = None,
-                        face_corr: np.ndarray | None = None) -> np.ndarray:
+                        face_corr: np.ndarray | None = None,
+                        q_ext: tuple[np.ndarray, np.ndarray] | None = None) -> np.ndarray:
     """R_h(q, T)_{c,a,p} = int_K q T . grad(phi_a) psi_c J_h
                          - sum_lateral faces int phi_a psi_c (q.n)^ T^ dl dzeta
 
@@ -52,6 +53,9 @@ def horizontal_residual(om: OMesh, qx: np.ndarray, qy: np.ndarray, T: np.ndarray
     the mean of both sides {q}.n; T^ is upwind at each face quadrature point.
     Walls carry no flux.  Open boundaries use the interior transport and, for
     inflow, the exterior state ``T_ext`` (same layout as T; zero-gradient when None).
+    With ``q_ext`` (an exterior transport at the own nodes, same layout as qx, qy)
+    the open-boundary face transport is the mean of the interior and exterior ones,
+    as on interior faces.
     ``face_corr`` (P, 3, 2): an additive correction of the normal transport per
     lateral face and edge quadrature point (the same at both zeta points), used
     for the transport that matches the averaged 2D face flux.
@@ -90,7 +94,7 @@ def horizontal_residual(om: OMesh, qx: np.ndarray, qy: np.ndarray, T: np.ndarray
             for zq, wz in zip(GAUSS_Z, GAUSS_W):
                 ps = psi(zq)
                 qn_own = np.zeros(om.P); T_own = np.zeros(om.P)
-                qn_nb = np.zeros(om.P); T_nb = np.zeros(om.P)
+                qn_nb = np.zeros(om.P); T_nb = np.zeros(om.P); qn_x = np.zeros(om.P)
                 for j in range(2):
                     a = own[j]
                     an = np.where(ok, loc[:, j], 0)
@@ -100,11 +104,14 @@ def horizontal_residual(om: OMesh, qx: np.ndarray, qy: np.ndarray, T: np.ndarray
                         T_own += b * T[c, a]
                         qn_nb += b * (qx[c, an, pn_safe] * nx + qy[c, an, pn_safe] * ny)
                         T_nb += b * T[c, an, pn_safe]
+                        if q_ext is not None:
+                            qn_x += b * (q_ext[0][c, a] * nx + q_ext[1][c, a] * ny)
                 if T_ext is not None:
                     T_x = sum(wv[j] * ps[c] * T_ext[c, own[j]] for j in range(2) for c in range(2))
                 else:
                     T_x = T_own
-                qn = np.where(ok, 0.5 * (qn_own + qn_nb), np.where(is_open, qn_own, 0.0))
+                qn_open = qn_own if q_ext is None else 0.5 * (qn_own + qn_x)
+                qn = np.where(ok, 0.5 * (qn_own + qn_nb), np.where(is_open, qn_open, 0.0))
                 if face_corr is not None:
                     qn = qn + np.where(ok | is_open, face_corr[:, e, gi], 0.0)
                 T_other = np.where(ok, T_nb, T_x)

@@ -871,8 +871,11 @@ __global__ void __launch_bounds__(TP, (MB<R, TP>::value))
 // ---------------------------------------------------------------------------
 // 3D update of a field pair (KIND 0: momentum u, v; KIND 1: tracers T, S)
 //   M1 f1 = M0 f0 + dt (R_h(f_ev; qbar) + extras [+ M1 F2D/H1] [+ A f_ev]),
-// the momentum extras (Ex, Ey) stored by the prediction of the same state,
-// implicit: (M1 - dt A(W, st1)) f1 = ... without A f_ev.
+// implicit: (M1 - dt A(W, st1)) f1 = ... without A f_ev; the momentum extras (Ex,
+// Ey) are the ones the prediction stored for the same state.  The outputs O0, O1
+// may be the start state G0, G1 itself (the last stage updates in place): each
+// thread reads its own prism's start values before writing them, and neither
+// pair is declared restrict.
 // ---------------------------------------------------------------------------
 template <typename R>
 struct UA {
@@ -883,7 +886,7 @@ struct UA {
 
 template <typename R, int TP, int KIND, bool IMPL, int OCC>
 __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
-    k_update(DevMesh m, AdvIn<R> in, const R* __restrict__ G0, const R* __restrict__ G1,
+    k_update(DevMesh m, AdvIn<R> in, const R* G0, const R* G1,
              const R* __restrict__ W, const R* __restrict__ Ex, const R* __restrict__ Ey,
              const R* __restrict__ F2x, const R* __restrict__ F2y, const R* __restrict__ st0,
              const R* __restrict__ st1, PP<R> pp, UA<R> ua, R* O0, R* O1,

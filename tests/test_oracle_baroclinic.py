@@ -272,3 +272,73 @@ def test_split_closed_basin_conserves_tracer_mass():
         st = bc.split_step(om, par, st, n * 20.0, 20.0)
     assert np.abs(st.u).max() > 1e-3
     assert abs(tr.tracer_mass(om, st.eta, st.T) - m0) < 1e-13 * abs(m0)
+
+
+def _forced(m, om, T0=12.5, S0=35.0, t_a=-100.0, t_b=400.0):
+    """Open-boundary forcing linear in time: the exterior velocity turns from inflow
+    to outflow between t_a and t_b; constant exterior tracers."""
+    st = _state(m, om)
+    st.T = np.full_like(st.T, T0); st.S = np.full_like(st.S, S0)
+    st.T_ext, st.S_ext = st.T.copy(), st.S.copy()
+    z = np.zeros_like(st.u)
+    st.forcing = bc.Forcing(t_a=t_a, t_b=t_b, u_a=z - 0.05, v_a=z + 0.01, u_b=z + 0.03, v_b=z - 0.02,
+                            T_a=st.T.copy(), S_a=st.S.copy(), T_b=st.T.copy(), S_b=st.S.copy())
+    return st
+
+
+def test_split_forcing_keeps_constant_tracers_constant():
+    """Exterior velocity linear in time at the open boundary (Sec. 3 forcing, the
+    linear-transport consistency of Sec. 2.5): the 2D mode sees Q_ext(t), the 3D
+    terms the exterior state at the middle of each stage's 2D run, so the tracer
+    transport matches the averaged 2D flux and constants stay constant."""
+    m = flat_or_shelf(n=5, N=4, slope=True, open_x=True)
+    om = OMesh(m)
+    par = bc.Params(tide_amp=0.3, tide_period=900.0, n_sub=6, nu_h=0.5, forcing=True)
+    st = _forced(m, om)
+    for n in range(2):
+        d1, d2 = {}, {}
+        st = bc.split_step(om, par, st, n * 30.0, 30.0, d1, d2)
+    assert np.abs(st.u).max() > 1e-4
+    assert np.abs(st.T - 12.5).max() < 1e-12 * 12.5
+    assert np.abs(st.S - 35.0).max() < 1e-12 * 35.0
+    for d in (d1, d2):
+        Sx, _ = bc.column_sum_q(om, *d["qbar"])
+        assert np.allclose(Sx, d["Qbar"][0], rtol=0, atol=1e-12 * np.abs(d["Qbar"][0]).max())
+        # the 3D column fluxes equal the averaged 2D fluxes: no flux through the surface
+        scale = tr.column_sum(om, np.abs(d["R1"])).max()
+        assert np.abs(d["W"][0][:, om.col_off[:-1]]).max() < 1e-12 * scale
+
+
+def test_split_forcing_correction_must_see_the_exterior_transport(monkeypatch):
+    """The same run with a face correction that ignores the exterior transport (a
+    planted inconsistency: the 3D open-boundary transport includes q_ext, the
+    correction's {Qbar} does not): the 3D column fluxes no longer equal the 2D ones
+    and a flux through the surface appears, so the pin above tests the exterior
+    transport's place in the correction.  (Constants survive either way: the
+    continuity carries the surface flux too.)"""
+    m = flat_or_shelf(n=5, N=4, slope=True, open_x=True)
+    om = OMesh(m)
+    par = bc.Params(tide_amp=0.3, tide_period=900.0, n_sub=6, nu_h=0.5, forcing=True)
+    st = _forced(m, om)
+    orig = bc.face_correction
+    monkeypatch.setattr(bc, "face_correction", lambda om_, dz, Qx, Qy, Gb, Q_ext=None: orig(om_, dz, Qx, Qy, Gb))
+    d2 = {}
+    st = bc.split_step(om, par, st, 0.0, 30.0, {}, d2)
+    scale = tr.column_sum(om, np.abs(d2["R1"])).max()
+    assert np.abs(d2["W"][0][:, om.col_off[:-1]]).max() > 1e-6 * scale
+
+
+def test_split_forcing_steady_data_does_not_depend_on_its_times():
+    """Forcing whose two states are equal gives the same step whatever t_a, t_b."""
+    m = flat_or_shelf(n=4, N=3, slope=True, open_x=True)
+    om = OMesh(m)
+    par = bc.Params(tide_amp=0.3, tide_period=900.0, n_sub=4, forcing=True)
+    outs = []
+    for t_a, t_b in ((-50.0, 80.0), (-1e4, 3e4)):
+        st = _forced(m, om, t_a=t_a, t_b=t_b)
+        f = st.forcing
+        f.u_b, f.v_b = f.u_a.copy(), f.v_a.copy()
+        st.T = st.T + 0.1 * np.arange(st.T.size).reshape(st.T.shape) / st.T.size
+        outs.append(bc.split_step(om, par, st, 0.0, 20.0))
+    for name in ("u", "v", "T", "S", "eta", "U", "V"):
+        assert np.array_equal(getattr(outs[0], name), getattr(outs[1], name)), name
