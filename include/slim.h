@@ -87,7 +87,19 @@ enum {
   SLIM_FIELD_S3_X = 22,     /* 2D column sum of the 3D horizontal momentum terms (last stage) */
   SLIM_FIELD_S3_Y = 23,
   SLIM_FIELD_F2D_X = 24,    /* 2D momentum forcing F2D of the last stage (Sec. 2.2)          */
-  SLIM_FIELD_F2D_Y = 25
+  SLIM_FIELD_F2D_Y = 25,
+  /* Open-boundary forcing of the split scheme (read at open-boundary nodes only;
+   * used when slim_params.forcing = 1): exterior velocity at time forcing_t_a
+   * (U_EXT, V_EXT) and at forcing_t_b (U_EXT_B, V_EXT_B), exterior tracers at
+   * forcing_t_b (T_EXT_B, S_EXT_B; those at forcing_t_a are T_EXT, S_EXT).  An
+   * upload of a time-a field also sets its time-b field (steady forcing needs one
+   * upload); uploading T or S sets both exterior tracer levels. */
+  SLIM_FIELD_U_EXT = 26,
+  SLIM_FIELD_V_EXT = 27,
+  SLIM_FIELD_U_EXT_B = 28,
+  SLIM_FIELD_V_EXT_B = 29,
+  SLIM_FIELD_T_EXT_B = 30,
+  SLIM_FIELD_S_EXT_B = 31
 };
 
 typedef struct slim_params {
@@ -124,12 +136,23 @@ typedef struct slim_params {
                           cooperative launch over all subcycles with a grid barrier
                           between stages (bounded wait: SLIM_ERR_TIMEOUT via the error
                           flag); 0: one launch per stage.  Same results bit for bit. */
+  double forcing_t_a;  /* times of the two open-boundary forcing states (forcing_t_b >  */
+  double forcing_t_b;  /* forcing_t_a); the data are linear in time between and beyond */
+  int forcing;         /* 1: split scheme with prescribed exterior velocity and tracers at
+                          open boundaries, interpolated in time inside the kernels: the
+                          2D mode takes the exterior transport Q_ext(t) (the column sum
+                          of (dz_rest/2) u_ext) at every stage time, the 3D open faces
+                          the mean of the interior and exterior transport and the
+                          exterior state at the middle of the stage's 2D run (Sec. 3
+                          forcing data, Sec. 2.5 consistency); 0: interior transport and
+                          static exterior tracer profiles. */
 } slim_params;
 
 /* Fill *p with the defaults: g 9.81, rho0 1025, f 1e-4, alpha 2e-4, beta 7.6e-4,
    T0 10, S0 35, kappa_v = nu_v = 1e-3, kappa_h = nu_h = 0, Cd 2.5e-3, no boundary
    fluxes, penalty_v 4, penalty_h 6, tide 1 m / 44712 s, SLIM_SCHEME_TRACER,
-   n_sub 20, tile 256, check_every 0, blocks_per_sm 0, use_graph 1, persistent_2d 1.  Returns
+   n_sub 20, tile 256, check_every 0, blocks_per_sm 0, use_graph 1, persistent_2d 1,
+   forcing 0 (forcing_t_a 0, forcing_t_b 1).  Returns
    SLIM_ERR_ARG for a null pointer. */
 slim_status slim_params_default(slim_params* p);
 

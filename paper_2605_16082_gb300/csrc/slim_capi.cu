@@ -39,6 +39,9 @@ extern "C" slim_status slim_params_default(slim_params* p) {
   p->blocks_per_sm = 0;
   p->use_graph = 1;
   p->persistent_2d = 1;
+  p->forcing_t_a = 0.0;
+  p->forcing_t_b = 1.0;
+  p->forcing = 0;
   return SLIM_OK;
 }
 
@@ -56,6 +59,15 @@ slim_status check_params(const slim_params* par) {
   }
   if (!(par->kappa_v >= 0) || !(par->nu_v >= 0) || !(par->penalty_v > 0)) {
     set_error("diffusivities must be >= 0 and penalty > 0");
+    return SLIM_ERR_ARG;
+  }
+  if (par->forcing != 0 && par->forcing != 1) { set_error("forcing must be 0 or 1"); return SLIM_ERR_ARG; }
+  if (par->forcing && par->scheme != SLIM_SCHEME_SPLIT) {
+    set_error("open-boundary forcing needs the split scheme");
+    return SLIM_ERR_ARG;
+  }
+  if (par->forcing && !(par->forcing_t_b > par->forcing_t_a)) {
+    set_error("forcing_t_b must be later than forcing_t_a");
     return SLIM_ERR_ARG;
   }
   return SLIM_OK;
@@ -113,6 +125,12 @@ bool field_ref(slim_state* s, int field, FieldRef* r) {
     case SLIM_FIELD_R_Y: *r = {s->Ry, true, dbl3}; return true;
     case SLIM_FIELD_T_EXT: *r = {s->Text, true, dbl3}; return true;
     case SLIM_FIELD_S_EXT: *r = {s->Sext, true, dbl3}; return true;
+    case SLIM_FIELD_U_EXT: if (!s->Uxa) return false; *r = {s->Uxa, true, dbl3}; return true;
+    case SLIM_FIELD_V_EXT: if (!s->Vxa) return false; *r = {s->Vxa, true, dbl3}; return true;
+    case SLIM_FIELD_U_EXT_B: if (!s->Uxb) return false; *r = {s->Uxb, true, dbl3}; return true;
+    case SLIM_FIELD_V_EXT_B: if (!s->Vxb) return false; *r = {s->Vxb, true, dbl3}; return true;
+    case SLIM_FIELD_T_EXT_B: if (!s->Textb) return false; *r = {s->Textb, true, dbl3}; return true;
+    case SLIM_FIELD_S_EXT_B: if (!s->Sextb) return false; *r = {s->Sextb, true, dbl3}; return true;
     case SLIM_FIELD_ETA: *r = {s->eta, false, true}; return true;
     case SLIM_FIELD_QX: *r = {s->Qx, false, true}; return true;
     case SLIM_FIELD_QY: *r = {s->Qy, false, true}; return true;
@@ -233,6 +251,11 @@ extern "C" slim_status slim_state_alloc(const slim_mesh* m, slim_precision prec,
   if ((st = refresh_stretch(s, 0)) != SLIM_OK) { free_state(s); return st; }
   if (par->scheme == SLIM_SCHEME_SPLIT) {
     if (par->n_sub < 2 || par->n_sub % 2) { free_state(s); set_error("n_sub must be even"); return SLIM_ERR_ARG; }
+    void** fx[] = {&s->Uxa, &s->Vxa, &s->Uxb, &s->Vxb, &s->Textb, &s->Sextb};
+    for (void** f : fx) {
+      if ((st = dev_alloc(s, f, n3 * s->esz)) != SLIM_OK) { free_state(s); return st; }
+      cudaMemset(*f, 0, n3 * s->esz);
+    }
     if ((st = split_alloc(s)) != SLIM_OK) { free_state(s); return st; }
   }
   s->aux2d_len = split_aux2d_len(m->d);
@@ -272,15 +295,26 @@ extern "C" slim_status slim_state_upload(slim_state* s, int field, const double*
   if (!field_ref(s, field, &r) || field == SLIM_FIELD_W) { set_error("field cannot be uploaded"); return SLIM_ERR_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
   const size_t n = field_len(s, r.is3d);
-  void* ext = field == SLIM_FIELD_T ? s->Text : field == SLIM_FIELD_S ? s->Sext : nullptr;
+  // fields that an upload also sets: the exterior tracer levels (T, S) and the
+  // second forcing level of a first-level exterior field
+  void* mirror[2] = {nullptr, nullptr};
+  switch (field) {
+    case SLIM_FIELD_T: mirror[0] = s->Text; mirror[1] = s->Textb; break;
+    case SLIM_FIELD_S: mirror[0] = s->Sext; mirror[1] = s->Sextb; break;
+    case SLIM_FIELD_T_EXT: mirror[0] = s->Textb; break;
+    case SLIM_FIELD_S_EXT: mirror[0] = s->Sextb; break;
+    case SLIM_FIELD_U_EXT: mirror[0] = s->Uxb; break;
+    case SLIM_FIELD_V_EXT: mirror[0] = s->Vxb; break;
+  }
+  const size_t bytes = n * (r.is_double ? sizeof(double) : sizeof(float));
   if (r.is_double) {
     SLIM_CUDA_TRY(cudaMemcpyAsync(r.ptr, host, n * sizeof(double), cudaMemcpyHostToDevice, st));
-    if (ext) SLIM_CUDA_TRY(cudaMemcpyAsync(ext, r.ptr, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   } else {
     SLIM_CUDA_TRY(cudaMemcpyAsync(s->stage64, host, n * sizeof(double), cudaMemcpyHostToDevice, st));
     SLIM_LAUNCH(launch_convert_d2f(s->stage64, (float*)r.ptr, n, st));
-    if (ext) SLIM_CUDA_TRY(cudaMemcpyAsync(ext, r.ptr, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
   }
+  for (void* mp : mirror)
+    if (mp) SLIM_CUDA_TRY(cudaMemcpyAsync(mp, r.ptr, bytes, cudaMemcpyDeviceToDevice, st));
   if (field == SLIM_FIELD_ETA) return refresh_stretch(s, st);
   return SLIM_OK;
 }
@@ -463,15 +497,9 @@ slim_status step_graph(slim_state* s, double t, double dt, cudaStream_t user) {
     }
     s->g_dt = dt;
   } else if (s->g_time_node) {
-    // same arguments as captured, new start time
-    s->g_args_t = t;
-    s->g_args_dt = dt;
-    s->g_args_n = s->par.n_sub;
-    s->g_args_amp = s->par.tide_amp;
-    s->g_args_period = s->par.tide_period;
-    s->g_args_out = split_tide_ptr(s);
-    void* args[6] = {&s->g_args_t, &s->g_args_dt, &s->g_args_n, &s->g_args_amp, &s->g_args_period,
-                     &s->g_args_out};
+    // same graph, new start time: the time kernel's one (struct) argument
+    split_time_args(s, t, dt, s->g_time_args);
+    void* args[1] = {s->g_time_args};
     cudaKernelNodeParams kp = s->g_time_params;
     kp.kernelParams = args;
     kp.extra = nullptr;

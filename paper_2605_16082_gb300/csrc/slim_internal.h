@@ -101,6 +101,10 @@ struct slim_state {
   void* T = nullptr; void* S = nullptr; void* U = nullptr; void* V = nullptr;
   void* W = nullptr;
   void* Text = nullptr; void* Sext = nullptr;   // open-boundary exterior profiles
+  // open-boundary forcing of the split scheme: exterior velocity at the two forcing
+  // times and the exterior tracers at the second (null for the tracer scheme)
+  void* Uxa = nullptr; void* Vxa = nullptr; void* Uxb = nullptr; void* Vxb = nullptr;
+  void* Textb = nullptr; void* Sextb = nullptr;
   void* tmp[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // stage buffers
   void* Rx = nullptr; void* Ry = nullptr;       // baroclinic pressure gradient
   // 2D fields (double)
@@ -127,10 +131,7 @@ struct slim_state {
   cudaGraphNode_t g_time_node = nullptr;
   cudaKernelNodeParams g_time_params{};
   double g_dt = 0.0;
-  double g_args_t = 0.0, g_args_dt = 0.0, g_args_amp = 0.0, g_args_period = 0.0;
-  int g_args_n = 0;
-  double* g_args_out = nullptr;
-  void* g_args[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  alignas(16) unsigned char g_time_args[128];  // the time kernel's argument for the next replay
   // phase timing (slim_profile_*)
   bool prof_on = false;
   int prof_max = 0;

@@ -7,6 +7,7 @@
 //   -> 3D momentum and tracers, vertically implicit (stage 1) or explicit (stage 2).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <string>
 
 #include "slim_kernels.h"
@@ -25,6 +26,15 @@ struct SplitBufs {
   void *S3x_r, *S3y_r;
   double* tide;  // open-boundary elevation per external stage of the step (+1 slot)
   float* tide_f;  // the same stage values in FP32 (after the doubles in the same buffer)
+  // open-boundary forcing: theta per external stage slot (+ the rhs2d slot + the two
+  // split-stage middles), its FP32 copy; Q_ext column sums [4][3][n_tri] (x, y at
+  // t_a, x, y at t_b) in FP64 and FP32; the flag the step was built with
+  double* theta;
+  float* theta_f;
+  double* Qext;
+  float* Qext_f;
+  int forcing;
+  int n_tide;
   // mixed form: FP32 stage-increment sums of the 2D subcycle and FP32 1/(w/6)
   float *Dacc, *Eacc, *Gacc, *iw6_f;
   // non-advective momentum terms (viscosity, Coriolis, -r/rho0, drag) of the stage's
@@ -117,23 +127,81 @@ __device__ __forceinline__ R zhat_r(const DevMesh& m, int i, int k) {
 // stage 1 runs n/2 subcycles over dt/2, stage 2 n subcycles over dt, each
 // subcycle's SSP-RK3 stages at times (0, 1, 1/2) x the subcycle length
 // ---------------------------------------------------------------------------
-__global__ void k_tide(double t0, double dt, int n, double amp, double period, double* __restrict__ out) {
-  const int n1 = n / 2;
-  const int total = 3 * (n1 + n);
+// Time data of one step for every external stage: the open-boundary elevation
+// (the analytic M2 tide) and the forcing's theta = (t - t_a)/(t_b - t_a) at each
+// stage time, and theta at the middle of each split stage's 2D run.  Slot layout
+// (n1 = n/2 stages of the first split stage, then n of the second, 3 stages each):
+// tide [total + 1] doubles, its FP32 copy [total]; theta [total + 3] doubles (stage
+// slots, the slim_rhs2d slot, the two middles), its FP32 copy.
+struct TideArgs {
+  double t0, dt, amp, period, ta, tb;
+  int n;
+  double* out;
+  double* theta;
+};
+
+__global__ void k_tide(TideArgs a) {
+  const int n1 = a.n / 2;
+  const int total = 3 * (n1 + a.n);
   const double off[3] = {0.0, 1.0, 0.5};
-  float* out_f = reinterpret_cast<float*>(out + total + 1);  // FP32 copies after the doubles
-  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+  float* out_f = reinterpret_cast<float*>(a.out + total + 1);  // FP32 copies after the doubles
+  float* th_f = reinterpret_cast<float*>(a.theta + total + 3);
+  const double ith = 1.0 / (a.tb - a.ta);
+  for (int i = threadIdx.x; i < total + 2; i += blockDim.x) {
     double time;
+    if (i >= total) {  // middles of the two split stages' 2D runs
+      time = a.t0 + (i == total ? 0.25 : 0.5) * a.dt;
+      const double th = (time - a.ta) * ith;
+      a.theta[total + 1 + (i - total)] = th;
+      th_f[total + 1 + (i - total)] = (float)th;
+      continue;
+    }
     if (i < 3 * n1) {
-      const double dts = 0.5 * dt / n1;
-      time = t0 + (i / 3 + off[i % 3]) * dts;
+      const double dts = 0.5 * a.dt / n1;
+      time = a.t0 + (i / 3 + off[i % 3]) * dts;
     } else {
       const int j = i - 3 * n1;
-      const double dts = dt / n;
-      time = t0 + (j / 3 + off[j % 3]) * dts;
+      const double dts = a.dt / a.n;
+      time = a.t0 + (j / 3 + off[j % 3]) * dts;
     }
-    out[i] = amp * cos(2.0 * M_PI * time / period);
-    out_f[i] = (float)out[i];
+    a.out[i] = a.amp * cos(2.0 * M_PI * time / a.period);
+    out_f[i] = (float)a.out[i];
+    const double th = (time - a.ta) * ith;
+    a.theta[i] = th;
+    th_f[i] = (float)th;
+  }
+}
+
+// Column sums of the exterior layer transport (dz_rest/2) u_ext at both forcing
+// times (Q_ext at the vertices of triangles with an open edge; 0 elsewhere).
+template <typename R>
+__global__ void k_ext_sums(DevMesh m, const R* __restrict__ Uxa, const R* __restrict__ Vxa,
+                           const R* __restrict__ Uxb, const R* __restrict__ Vxb,
+                           double* __restrict__ Q, float* __restrict__ Qf) {
+  const int nt = m.n_tri;
+  const size_t n2 = (size_t)3 * nt;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    bool open = false;
+    for (int e = 0; e < 3; ++e) open |= (m.einfo[e * nt + t].x == -2);
+    const int p0 = m.col_off[t], N = m.col_off[t + 1] - p0;
+    for (int a = 0; a < 3; ++a) {
+      const int ia = a * nt + t;
+      double s[4] = {0.0, 0.0, 0.0, 0.0};
+      if (open) {
+        for (int k = 0; k < N; ++k) {
+          const double hr = 0.5 * dz_rest_r<double>(m, ia, k, N);
+          const size_t i0 = (size_t)a * m.P + p0 + k, i1 = (size_t)(3 + a) * m.P + p0 + k;
+          s[0] += hr * ((double)Uxa[i0] + (double)Uxa[i1]);
+          s[1] += hr * ((double)Vxa[i0] + (double)Vxa[i1]);
+          s[2] += hr * ((double)Uxb[i0] + (double)Uxb[i1]);
+          s[3] += hr * ((double)Vxb[i0] + (double)Vxb[i1]);
+        }
+      }
+      for (int c = 0; c < 4; ++c) {
+        Q[c * n2 + ia] = s[c];
+        Qf[c * n2 + ia] = (float)s[c];
+      }
+    }
   }
 }
 
@@ -481,10 +549,12 @@ template <typename RC> struct Ext2dGeo;
 template <> struct Ext2dGeo<double> {
   static __device__ __forceinline__ double c(const SplitBufs& b, int i) { return b.cw[i]; }
   static __device__ __forceinline__ double ic(const SplitBufs& b, int i) { return b.icw[i]; }
+  static __device__ __forceinline__ const double* Q(const SplitBufs& b) { return b.Qext; }
 };
 template <> struct Ext2dGeo<float> {
   static __device__ __forceinline__ float c(const SplitBufs& b, int i) { return b.cw_f[i]; }
   static __device__ __forceinline__ float ic(const SplitBufs& b, int i) { return b.icw_f[i]; }
+  static __device__ __forceinline__ const float* Q(const SplitBufs& b) { return b.Qext_f; }
 };
 
 // Stage buffers: FP64 state for the update plus its compute-type shadow for the
@@ -506,12 +576,25 @@ struct LdL2 {
   template <typename T> static __device__ __forceinline__ T ld(const T* p) { return __ldcg(p); }
 };
 
+// Forced open boundary: the exterior normal transport Q_ext(t).n at an edge point,
+// Q_ext = Q_a + theta (Q_b - Q_a) at the edge's two vertices (i0, i1) weighted b0, b1.
+// Out of line: it runs on open edges only and keeps its registers off the main path.
+template <typename RC>
+__device__ __noinline__ RC forced_qn(const SplitBufs& bf, int nt, int i0, int i1, RC b0, RC b1, RC nx,
+                                     RC ny, RC th) {
+  const RC* Q = Ext2dGeo<RC>::Q(bf);
+  const size_t n2 = (size_t)3 * nt;
+  const RC x0 = Q[i0] + th * (Q[2 * n2 + i0] - Q[i0]), y0 = Q[n2 + i0] + th * (Q[3 * n2 + i0] - Q[n2 + i0]);
+  const RC x1 = Q[i1] + th * (Q[2 * n2 + i1] - Q[i1]), y1 = Q[n2 + i1] + th * (Q[3 * n2 + i1] - Q[n2 + i1]);
+  return b0 * (x0 * nx + y0 * ny) + b1 * (x1 * nx + y1 * ny);
+}
+
 // Residual of the 2D stage at the RC state (er, Ur, Vr) of triangle t; Fe
 // receives the eta flux at the 6 edge points (edge-major, 2 points per edge).
 template <typename RC, typename LD = LdPlain>
 __device__ __forceinline__ void ext2d_residual(const DevMesh& m, const SplitBufs& bf, const RC* er,
-                                               const RC* Ur, const RC* Vr, RC g, RC tide, int t,
-                                               RC Re[3], RC RU[3], RC RV[3], RC Fe[6]) {
+                                               const RC* Ur, const RC* Vr, RC g, RC tide, RC th,
+                                               int t, RC Re[3], RC RU[3], RC RV[3], RC Fe[6]) {
   const int nt = m.n_tri;
   RC e[3], U[3], V[3], H[3], gx[3], gy[3];
 #pragma unroll
@@ -562,7 +645,7 @@ __device__ __forceinline__ void ext2d_residual(const DevMesh& m, const SplitBufs
         qx = b0 * qn0 + b1 * qn1;
       } else if (ei.x == -2) {
         ex = tide;
-        qx = qo;
+        qx = bf.forcing ? forced_qn<RC>(bf, nt, a0 * nt + t, a1 * nt + t, b0, b1, nx, ny, th) : qo;
       } else {
         ex = eo_;
         qx = -qo;
@@ -589,7 +672,7 @@ __global__ void __launch_bounds__(256)
   if (t >= nt) return;
   RC Re[3], RU[3], RV[3], Fe[6];
   ext2d_residual<RC>(m, bf, (const RC*)io.er, (const RC*)io.Ur, (const RC*)io.Vr, (RC)g_,
-                     (RC)bf.tide[tide_idx], t, Re, RU, RV, Fe);
+                     (RC)bf.tide[tide_idx], (RC)bf.theta[tide_idx], t, Re, RU, RV, Fe);
   if (MODE == 1) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -656,11 +739,11 @@ struct Mx2dIO {
 // the thread that owns t)
 template <int KIND, typename LD>
 __device__ __forceinline__ void ext2d_mx_tri(const DevMesh& m, const SplitBufs& bf, const Mx2dIO& io,
-                                             float g, float tide, float dt, float wq, double wn,
-                                             int t) {
+                                             float g, float tide, float th, float dt, float wq,
+                                             double wn, int t) {
   const int nt = m.n_tri;
   float Re[3], RU[3], RV[3], Fe[6];
-  ext2d_residual<float, LD>(m, bf, io.er, io.Ur, io.Vr, g, tide, t, Re, RU, RV, Fe);
+  ext2d_residual<float, LD>(m, bf, io.er, io.Ur, io.Vr, g, tide, th, t, Re, RU, RV, Fe);
   const float bdw = dt * bf.iw6_f[t];
   const float* S3x = (const float*)bf.S3x_r;
   const float* S3y = (const float*)bf.S3y_r;
@@ -735,11 +818,11 @@ __global__ void __launch_bounds__(256) k_ext2d_run(DevMesh m, SplitBufs bf, Mx2d
   const int stride = gridDim.x * blockDim.x;
   for (int gs = first; gs < first + count; ++gs) {
     const int st = gs % 3;
-    const float tide = bf.tide_f[r.tide_base + gs];
+    const float tide = bf.tide_f[r.tide_base + gs], th = bf.theta_f[r.tide_base + gs];
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
-      if (st == 0) ext2d_mx_tri<0, LdL2>(m, bf, r.io[0], r.g, tide, r.dt, r.wq, r.wn, t);
-      else if (st == 1) ext2d_mx_tri<1, LdL2>(m, bf, r.io[1], r.g, tide, r.dt, r.wq, r.wn, t);
-      else ext2d_mx_tri<2, LdL2>(m, bf, r.io[2], r.g, tide, r.dt, r.wq, r.wn, t);
+      if (st == 0) ext2d_mx_tri<0, LdL2>(m, bf, r.io[0], r.g, tide, th, r.dt, r.wq, r.wn, t);
+      else if (st == 1) ext2d_mx_tri<1, LdL2>(m, bf, r.io[1], r.g, tide, th, r.dt, r.wq, r.wn, t);
+      else ext2d_mx_tri<2, LdL2>(m, bf, r.io[2], r.g, tide, th, r.dt, r.wq, r.wn, t);
     }
     if (gs + 1 < first + count && !grid_barrier(r.bar, gridDim.x, r.err, &s_fail)) return;
   }
@@ -761,7 +844,8 @@ __global__ void k_couple2d(DevMesh m, const double* __restrict__ e1, const doubl
                            double iT, double* __restrict__ F2x,
                            double* __restrict__ F2y, R* __restrict__ F2x_r, R* __restrict__ F2y_r,
                            R* __restrict__ Dqx_r, R* __restrict__ Dqy_r, R* __restrict__ gcor_r,
-                           R* __restrict__ st_end) {
+                           R* __restrict__ st_end, const double* __restrict__ Qext,
+                           const double* __restrict__ th_mid) {
   const int nt = m.n_tri;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
@@ -796,6 +880,16 @@ __global__ void k_couple2d(DevMesh m, const double* __restrict__ e1, const doubl
         const int i0 = a0 * nt + t, i1 = a1 * nt + t;
         const double Qo = b0 * (Qbx[i0] * nx + Qby[i0] * ny) + b1 * (Qbx[i1] * nx + Qby[i1] * ny);
         double Qavg = Qo;
+        if (ei.x == -2 && Qext) {  // forced open boundary: mean with the exterior transport
+          const double th = *th_mid;
+          const size_t n2 = (size_t)3 * nt;
+          auto qe = [&](int i) {
+            const double x = Qext[i] + th * (Qext[2 * n2 + i] - Qext[i]);
+            const double y = Qext[n2 + i] + th * (Qext[3 * n2 + i] - Qext[n2 + i]);
+            return x * nx + y * ny;
+          };
+          Qavg = 0.5 * (Qo + b0 * qe(i0) + b1 * qe(i1));
+        }
         const int Np = ei.x >= 0 ? min(N, ei.z) : N;
         double tot = b0 * paired(i0, N, Np) * (double)st_ev[i0] + b1 * paired(i1, N, Np) * (double)st_ev[i1];
         if (ei.x >= 0) {
@@ -1180,7 +1274,18 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, int tide_base,
     ProfScope ps(s, SLIM_PHASE_HPG, stm);
     SLIM_CU(launch_hpg<R>(m, TP, occ, T_ev, S_ev, st_ev, pp, Rx, Ry, stm));
   }
-  AdvIn<R> pin{u_ev, v_ev, nullptr, nullptr, nullptr, nullptr, st_ev, nullptr, nullptr, nullptr};
+  // open-boundary forcing: exterior state at theta of the middle of this stage's
+  // 2D run (slot n_tide + 1 for the first split stage, n_tide + 2 for the second)
+  const int mid = b->n_tide + (tide_base == 0 ? 1 : 2);
+  const R* th_mid = sizeof(R) == 8 ? (const R*)(const void*)(b->theta + mid)
+                                   : (const R*)(const void*)(b->theta_f + mid);
+  const bool fx = s->par.forcing != 0;
+  const R* Uxa = fx ? (const R*)s->Uxa : nullptr;
+  const R* Vxa = fx ? (const R*)s->Vxa : nullptr;
+  const R* Uxb = fx ? (const R*)s->Uxb : nullptr;
+  const R* Vxb = fx ? (const R*)s->Vxb : nullptr;
+  AdvIn<R> pin{u_ev, v_ev, nullptr, nullptr, Uxa, Vxa, st_ev, nullptr, nullptr, nullptr,
+               Uxa, Vxa, Uxb, Vxb, Uxb, Vxb, th_mid};
   {
     ProfScope ps(s, SLIM_PHASE_MOM_PRED, stm);
     SLIM_CU(launch_mompred<R>(m, TP, occ, pin, Rx, Ry, pp, b, stm));
@@ -1271,11 +1376,12 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, int tide_base,
                                         b->Sqy, s->Qbx, s->Qby, b->Gb, st_ev, b->iw6, dt, 1.0 / dt,
                                         b->F2x, b->F2y,
                                         (R*)b->F2x_r, (R*)b->F2y_r, (R*)b->Dqx_r, (R*)b->Dqy_r,
-                                        (R*)b->gcor_r, (R*)b->st_end);
+                                        (R*)b->gcor_r, (R*)b->st_end, fx ? b->Qext : nullptr,
+                                        b->theta + mid);
     SLIM_CU(cudaGetLastError());
   }
-  AdvIn<R> cin{u_ev, v_ev, nullptr, nullptr, nullptr, nullptr, st_ev, (const R*)b->Dqx_r,
-               (const R*)b->Dqy_r, (const R*)b->gcor_r};
+  AdvIn<R> cin{u_ev, v_ev, nullptr, nullptr, Uxa, Vxa, st_ev, (const R*)b->Dqx_r,
+               (const R*)b->Dqy_r, (const R*)b->gcor_r, Uxa, Vxa, Uxb, Vxb, Uxb, Vxb, th_mid};
   {
     ProfScope ps(s, SLIM_PHASE_CONTINUITY, stm);
     SLIM_CU(launch_cont_split<R>(m, TP, cin, s->eta, b->Ae, dt, (R*)s->W, stm));
@@ -1285,7 +1391,8 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, int tide_base,
   UA<R> um{(R)dt, (R)s->par.nu_v, (R)s->par.nu_h};
   UA<R> ut{(R)dt, (R)s->par.kappa_v, (R)s->par.kappa_h};
   AdvIn<R> tin{u_ev, v_ev, T_ev, S_ev, (const R*)s->Text, (const R*)s->Sext, st_ev,
-               (const R*)b->Dqx_r, (const R*)b->Dqy_r, (const R*)b->gcor_r};
+               (const R*)b->Dqx_r, (const R*)b->Dqy_r, (const R*)b->gcor_r, Uxa, Vxa, Uxb, Vxb,
+               fx ? (const R*)s->Textb : nullptr, fx ? (const R*)s->Sextb : nullptr, th_mid};
   const R* U0 = (const R*)s->U;
   const R* V0 = (const R*)s->V;
   const R* T0 = (const R*)s->T;
@@ -1325,7 +1432,17 @@ slim_status step_t(slim_state* s, double t, double dt, cudaStream_t stm) {
   // step: its time argument is the only one that changes between steps)
   {
     ProfScope ps(s, SLIM_PHASE_MISC, stm);
-    k_tide<<<1, 128, 0, stm>>>(t, dt, s->par.n_sub, s->par.tide_amp, s->par.tide_period, b->tide);
+    TideArgs ta;
+    split_time_args(s, t, dt, &ta);
+    k_tide<<<1, 128, 0, stm>>>(ta);
+    SLIM_CU(cudaGetLastError());
+  }
+  b->forcing = s->par.forcing;
+  if (b->forcing) {
+    ProfScope ps(s, SLIM_PHASE_MISC, stm);
+    const int grd = std::min((m.n_tri + 255) / 256, 2048);
+    k_ext_sums<R><<<grd, 256, 0, stm>>>(m, (const R*)s->Uxa, (const R*)s->Vxa, (const R*)s->Uxb,
+                                        (const R*)s->Vxb, b->Qext, b->Qext_f);
     SLIM_CU(cudaGetLastError());
   }
   slim_status r = stage<R>(s, t, 0.5 * dt, s->par.n_sub / 2, 0, true, U, V, T, S, (const R*)s->st_cur,
@@ -1353,7 +1470,20 @@ slim_status step_t(slim_state* s, double t, double dt, cudaStream_t stm) {
 size_t split_aux2d_len(const DevMesh& m) { return (size_t)16 * m.n_tri; }
 
 const void* split_time_kernel() { return (const void*)k_tide; }
-double* split_tide_ptr(slim_state* s) { return s->sp ? s->sp->tide : nullptr; }
+void split_time_args(const slim_state* s, double t, double dt, void* out) {
+  static_assert(sizeof(TideArgs) <= 128, "time kernel argument");
+  TideArgs a;
+  a.t0 = t;
+  a.dt = dt;
+  a.amp = s->par.tide_amp;
+  a.period = s->par.tide_period;
+  a.ta = s->par.forcing_t_a;
+  a.tb = s->par.forcing_t_b > s->par.forcing_t_a ? s->par.forcing_t_b : s->par.forcing_t_a + 1.0;
+  a.n = s->par.n_sub;
+  a.out = s->sp->tide;
+  a.theta = s->sp->theta;
+  std::memcpy(out, &a, sizeof(a));
+}
 
 slim_status split_alloc(slim_state* s) {
   if (s->sp) return SLIM_OK;
@@ -1392,6 +1522,16 @@ slim_status split_alloc(slim_state* s) {
   SLIM_CU(cudaMemset(b->tide, 0, (n_tide + 1) * 8 + n_tide * sizeof(float)));
   s->allocs.push_back(b->tide);
   b->tide_f = reinterpret_cast<float*>(b->tide + n_tide + 1);
+  b->n_tide = (int)n_tide;
+  b->forcing = 0;
+  SLIM_CU(cudaMalloc((void**)&b->theta, (n_tide + 3) * (8 + sizeof(float))));
+  SLIM_CU(cudaMemset(b->theta, 0, (n_tide + 3) * (8 + sizeof(float))));
+  s->allocs.push_back(b->theta);
+  b->theta_f = reinterpret_cast<float*>(b->theta + n_tide + 3);
+  SLIM_CU(cudaMalloc((void**)&b->Qext, 4 * n2 * (8 + sizeof(float))));
+  SLIM_CU(cudaMemset(b->Qext, 0, 4 * n2 * (8 + sizeof(float))));
+  s->allocs.push_back(b->Qext);
+  b->Qext_f = reinterpret_cast<float*>(b->Qext + 4 * n2);
   SLIM_CU(cudaMalloc((void**)&b->iw6, (size_t)m.n_tri * 8));
   s->allocs.push_back(b->iw6);
   SLIM_CU(cudaMalloc((void**)&b->iw6_f, (size_t)m.n_tri * sizeof(float)));
@@ -1467,7 +1607,23 @@ slim_status split_rhs2d(slim_state* s, double t, double* out, cudaStream_t st) {
   SplitBufs* b = s->sp;
   const double tide = s->par.tide_amp * std::cos(2.0 * M_PI * t / s->par.tide_period);
   const int slot = 3 * (s->par.n_sub / 2 + s->par.n_sub);
+  b->forcing = s->par.forcing;
+  const double th = s->par.forcing
+                        ? (t - s->par.forcing_t_a) / (s->par.forcing_t_b - s->par.forcing_t_a) : 0.0;
   SLIM_CU(cudaMemcpyAsync(b->tide + slot, &tide, sizeof(double), cudaMemcpyHostToDevice, st));
+  SLIM_CU(cudaMemcpyAsync(b->theta + slot, &th, sizeof(double), cudaMemcpyHostToDevice, st));
+  if (s->par.forcing) {
+    const int grd = std::min((m.n_tri + 255) / 256, 2048);
+    if (s->prec == SLIM_FP64)
+      k_ext_sums<double><<<grd, 256, 0, st>>>(m, (const double*)s->Uxa, (const double*)s->Vxa,
+                                              (const double*)s->Uxb, (const double*)s->Vxb, b->Qext,
+                                              b->Qext_f);
+    else
+      k_ext_sums<float><<<grd, 256, 0, st>>>(m, (const float*)s->Uxa, (const float*)s->Vxa,
+                                             (const float*)s->Uxb, (const float*)s->Vxb, b->Qext,
+                                             b->Qext_f);
+    SLIM_CU(cudaGetLastError());
+  }
   SLIM_CU(cudaStreamSynchronize(st));
   const int grd = (m.n_tri + 255) / 256;
   Ext2dIO io{};

@@ -15,5 +15,6 @@ slim_status split_step(slim_state* s, double t, double dt, cudaStream_t st);
 int split_kernel_count(const slim_state* s);
 // the step's time kernel (its first argument is the step's start time)
 const void* split_time_kernel();
-double* split_tide_ptr(slim_state* s);  // output buffer of the time kernel
+// the time kernel's argument (a struct of at most 128 bytes) for a step at t, dt
+void split_time_args(const slim_state* s, double t, double dt, void* out);
 }  // namespace slim

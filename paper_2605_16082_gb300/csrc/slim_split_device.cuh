@@ -20,6 +20,15 @@ struct AdvIn {
   const R* Dqx;    // [3][n_tri] Qbar - column sum of q (null: no correction)
   const R* Dqy;
   const R* gcor;   // [(e n_tri + t) 2 + g] face correction delta / tot (null: none)
+  // open-boundary forcing (null: none): exterior velocity at the two forcing times,
+  // the second time's E0/E1, and theta at the middle of the stage's 2D run
+  const R* Uxa;
+  const R* Vxa;
+  const R* Uxb;
+  const R* Vxb;
+  const R* E0b;
+  const R* E1b;
+  const R* th;
 };
 
 template <typename R>
@@ -160,17 +169,31 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
         }
       }
     } else {  // open boundary
+      // forced: the exterior transport (dz_rest/2) u_ext and exterior values at
+      // theta of the middle of the stage's 2D run; the face transport is then the
+      // mean of both sides as on interior faces
+      const R th = in.Uxa ? *in.th : (R)0;
+      has_nb = in.Uxa != nullptr;
 #pragma unroll
-      for (int j = 0; j < 2; ++j)
+      for (int j = 0; j < 2; ++j) {
+        const int la = j ? a1 : a0;
+        const R hr = in.Uxa ? (R)0.5 * dz_rest_r<R>(m, la * nt + t, k, N) : (R)0;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          qb[j][c] = qo[j][c];
+          const size_t idx = (size_t)(c * 3 + la) * P + p;
+          if (in.Uxa) {
+            const R ux = in.Uxa[idx] + th * (in.Uxb[idx] - in.Uxa[idx]);
+            const R vx = in.Vxa[idx] + th * (in.Vxb[idx] - in.Vxa[idx]);
+            qb[j][c] = hr * (ux * nxe + vx * nye);
+          } else {
+            qb[j][c] = qo[j][c];
+          }
           if (!UNIT) {
-            const size_t idx = (size_t)(c * 3 + (j ? a1 : a0)) * P + p;
-            fb0[j][c] = in.E0 ? in.E0[idx] : fo0[j][c];
-            fb1[j][c] = in.E1 ? in.E1[idx] : fo1[j][c];
+            fb0[j][c] = in.E0 ? (in.E0b ? in.E0[idx] + th * (in.E0b[idx] - in.E0[idx]) : in.E0[idx]) : fo0[j][c];
+            fb1[j][c] = in.E1 ? (in.E1b ? in.E1[idx] + th * (in.E1b[idx] - in.E1[idx]) : in.E1[idx]) : fo1[j][c];
           }
         }
+      }
     }
     R gc[2] = {0, 0};
     if (in.gcor) {

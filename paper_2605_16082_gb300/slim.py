@@ -18,8 +18,9 @@ LIB_PATH = os.path.join(HERE, "libslim.so")
 SLIM_FP64, SLIM_MIXED = 0, 1
 SLIM_SCHEME_TRACER, SLIM_SCHEME_SPLIT = 0, 1
 FIELD = dict(T=0, S=1, U=2, V=3, W=4, R_X=5, R_Y=6, T_EXT=7, S_EXT=8, ETA=16, QX=17, QY=18, ETA_NEXT=19,
-             QBAR_X=20, QBAR_Y=21, S3_X=22, S3_Y=23, F2D_X=24, F2D_Y=25)
-FIELD_IS_3D = {f: (v < 16) for f, v in FIELD.items()}
+             QBAR_X=20, QBAR_Y=21, S3_X=22, S3_Y=23, F2D_X=24, F2D_Y=25, U_EXT=26, V_EXT=27,
+             U_EXT_B=28, V_EXT_B=29, T_EXT_B=30, S_EXT_B=31)
+FIELD_IS_3D = {f: (v < 16 or v >= 26) for f, v in FIELD.items()}   # 16..25: 2D
 
 # every symbol declared in include/slim.h
 EXPORTED = ["slim_params_default", "slim_status_string", "slim_last_error", "slim_mesh_create",
@@ -39,7 +40,8 @@ class SlimParams(C.Structure):
         "nu_v", "kappa_h", "nu_h", "drag_cd", "flux_top", "flux_bot", "penalty_v", "penalty_h",
         "tide_amp", "tide_period")] + [(n, C.c_int) for n in (
         "scheme", "n_sub", "tile_prisms", "check_every", "blocks_per_sm", "use_graph",
-        "persistent_2d")]
+        "persistent_2d")] + [(n, C.c_double) for n in ("forcing_t_a", "forcing_t_b")] + [
+        ("forcing", C.c_int)]
 
 
 class SlimError(RuntimeError):

@@ -75,7 +75,8 @@ def oracle_params(p):
     return bc.Params(g=p.g, rho0=p.rho0, f=p.coriolis_f, alpha=p.eos_alpha, beta=p.eos_beta,
                      T0=p.eos_T0, S0=p.eos_S0, kappa_v=p.kappa_v, nu_v=p.nu_v, kappa_h=p.kappa_h,
                      nu_h=p.nu_h, cd=p.drag_cd, penalty_v=p.penalty_v, penalty_h=p.penalty_h,
-                     tide_amp=p.tide_amp, tide_period=p.tide_period, n_sub=p.n_sub)
+                     tide_amp=p.tide_amp, tide_period=p.tide_period, n_sub=p.n_sub,
+                     forcing=bool(p.forcing))
 
 
 def oracle_state(m, om, ini):
@@ -360,3 +361,92 @@ def test_grid_barrier_rounds_and_bounded_timeout(slim):
     assert (bits, arr) == (0, 8 * 50)
     bits, arr = slim.slim_selftest_barrier(8, 3, 5)
     assert bits & 4 and arr == 7
+
+
+def _forcing_fields(m, ini):
+    """Exterior velocity turning from inflow to outflow between the two forcing
+    times, exterior temperature warming by 0.5 (read at open-boundary nodes)."""
+    x, y, z, s_ = wl.fields.node_positions_sigma(m)
+    ua = (-0.05 * (1.2 - s_)).ravel(); va = (0.01 + 0 * s_).ravel()
+    ub = (0.03 * (0.5 + s_)).ravel(); vb = (-0.02 + 0 * s_).ravel()
+    return dict(U_EXT=ua, V_EXT=va, U_EXT_B=ub, V_EXT_B=vb, T_EXT_B=ini["T"] + 0.5, S_EXT_B=ini["S"])
+
+
+def _forced_oracle_state(m, om, ini, fx, p):
+    from oracle import baroclinic as bc
+    from oracle import tracer as tr
+    st = oracle_state(m, om, ini)
+    P = om.P
+    st.forcing = bc.Forcing(t_a=p.forcing_t_a, t_b=p.forcing_t_b, u_a=tr.to3(fx["U_EXT"], P),
+                            v_a=tr.to3(fx["V_EXT"], P), u_b=tr.to3(fx["U_EXT_B"], P),
+                            v_b=tr.to3(fx["V_EXT_B"], P), T_a=st.T.copy(), S_a=st.S.copy(),
+                            T_b=tr.to3(fx["T_EXT_B"], P), S_b=tr.to3(fx["S_EXT_B"], P))
+    return st
+
+
+@pytest.mark.parametrize("case", ["basin", "square"])
+def test_split_forcing_parity_fp64(slim, case):
+    """Open-boundary forcing linear in time (exterior velocity and temperature at two
+    times, interpolated inside the kernels; the 2D mode with the column sum of the
+    exterior transport): two steps against the oracle, every field."""
+    from oracle import baroclinic as bc
+    from oracle.mesh import OMesh
+    m = case_mesh(case)
+    ini = initial(m)
+    p = params(slim, forcing=1, forcing_t_a=-100.0, forcing_t_b=400.0)
+    om = OMesh(m)
+    fx = _forcing_fields(m, ini)
+    st = _forced_oracle_state(m, om, ini, fx, p)
+    par = oracle_params(p)
+    dt = 10.0 * wl.fields.dt_2d(m)
+    with model(slim, m, slim.SLIM_FP64, p, ini) as mod:
+        for k in ("U_EXT", "V_EXT", "U_EXT_B", "V_EXT_B", "T_EXT_B", "S_EXT_B"):
+            mod.upload(k, fx[k])
+        for n in range(2):
+            d1, d2 = {}, {}
+            st = bc.split_step(om, par, st, n * dt, dt, d1, d2)
+            slim.slim_step(mod.state, n * dt, dt)
+            slim.slim_state_check(mod.state)
+            for f, o in FIELDS3 + FIELDS2:
+                assert rel_l2(mod.download(f), getattr(st, o)) < TOL64, (n, f)
+            assert rel_l2(mod.download("W"), d2["W"]) < TOL_R, (n, "W")
+            assert rel_l2(mod.download("QBAR_X"), d2["Qbar"][0]) < TOL64, (n, "Qbar")
+    # the forcing changed the result (the exterior state enters)
+    st0 = bc.split_step(om, oracle_params(params(slim)), oracle_state(m, om, ini), 0.0, dt)
+    assert rel_l2(st0.u, bc.split_step(om, par, _forced_oracle_state(m, om, ini, fx, p), 0.0, dt).u) > 1e-6
+
+
+def test_split_forcing_mixed_and_constants(slim):
+    """Forced run in the mixed form against the oracle, and constant tracers with
+    constant exterior tracers stay constant under the time-varying exterior flow."""
+    from oracle import baroclinic as bc
+    from oracle.mesh import OMesh
+    m = case_mesh("basin")
+    ini = initial(m)
+    p = params(slim, forcing=1, forcing_t_a=-100.0, forcing_t_b=400.0)
+    om = OMesh(m)
+    fx = _forcing_fields(m, ini)
+    st = _forced_oracle_state(m, om, ini, fx, p)
+    par = oracle_params(p)
+    dt = 10.0 * wl.fields.dt_2d(m)
+    with model(slim, m, slim.SLIM_MIXED, p, ini) as mod:
+        for k in ("U_EXT", "V_EXT", "U_EXT_B", "V_EXT_B", "T_EXT_B", "S_EXT_B"):
+            mod.upload(k, fx[k])
+        for n in range(2):
+            st = bc.split_step(om, par, st, n * dt, dt)
+            slim.slim_step(mod.state, n * dt, dt)
+        errs = {f: rel_l2(mod.download(f), getattr(st, o)) for f, o in FIELDS3 + FIELDS2}
+    for f in ("T", "S"):
+        assert errs[f] < 1e-6, (f, errs[f])
+    for f in ("U", "V", "ETA", "QX", "QY"):
+        assert errs[f] < 1e-3, (f, errs[f])
+    const = dict(ini, T=np.full_like(ini["T"], 20.0), S=np.full_like(ini["S"], 35.0))
+    fxc = dict(fx, T_EXT_B=const["T"], S_EXT_B=const["S"])
+    for prec, tol in ((slim.SLIM_FP64, 1e-12), (slim.SLIM_MIXED, 1e-5)):
+        with model(slim, m, prec, p, const) as mod:
+            for k in ("U_EXT", "V_EXT", "U_EXT_B", "V_EXT_B", "T_EXT_B", "S_EXT_B"):
+                mod.upload(k, fxc[k])
+            for n in range(3):
+                slim.slim_step(mod.state, n * dt, dt)
+            assert np.abs(mod.download("T") - 20.0).max() < tol * 20.0
+            assert np.abs(mod.download("S") - 35.0).max() < tol * 35.0
