@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--occ", type=int, default=0, help="blocks per SM without the autotuner")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-accuracy", action="store_true", help="skip the 1000-step mixed-error run")
+    ap.add_argument("--layer-sweep", action="store_true",
+                    help="time per step against the number of sigma layers (1..64) instead")
     return ap.parse_args()
 
 
@@ -129,7 +131,8 @@ def workload_inputs(name: str):
             u, v = wl.basin_velocity(m)
             T = wl.c2_initial_state(m)["T"]
         return m, dict(kappa_v=W["kappa_v"]), dict(U=u, V=v, T=T, ETA=np.zeros(3 * m.n_tri)), W["dt"], 1
-    ini = wl.c2_initial_state(m) if name == "basin_baroclinic" else wl.c4_initial_state(m)
+    ini = {"basin_baroclinic": wl.c2_initial_state, "zlevel_baroclinic": wl.c4_initial_state,
+           "reef_baroclinic": wl.c5_initial_state}[name](m)
     fields = dict(U=ini["u"], V=ini["v"], T=ini["T"], S=ini["S"], ETA=ini["eta"], QX=ini["U"], QY=ini["V"])
     par = dict(scheme=1, n_sub=W["n_sub"], kappa_v=W["kappa_v"], nu_v=W["nu_v"],
                kappa_h=W.get("kappa_h", 0.0), nu_h=W.get("nu_h", 0.0))
@@ -342,6 +345,56 @@ def mixed_accuracy(steps: int = 1000) -> dict:
                 bar=1e-5, mass_drift_mixed=float(out["mixed"][1]), mass_drift_fp64=float(out["fp64"][1]))
 
 
+SWEEP_LAYERS = (1, 2, 3, 4, 6, 8, 10, 12, 16, 20, 24, 32, 40, 48, 56, 64)
+
+
+def layer_sweep(args) -> dict:
+    """Mixed split step against the number of uniform sigma layers on one horizontal
+    mesh (the basin generator at ~50k triangles, n_sub = 20): each layer count with
+    its autotuned tiling, timed with CUDA events after warm-up; reported per step and
+    per prism (the block structure of whole-column tiles shows in the latter)."""
+    import dataclasses
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2605_16082_gb300 import autotune, slim
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    base = wl.c2_mesh(50_000, 1, 0)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for N in SWEEP_LAYERS:
+        m = dataclasses.replace(base, n_layers=np.full(base.n_tri, N, np.int32))
+        ini = wl.c2_initial_state(m)
+        fields = dict(U=ini["u"], V=ini["v"], T=ini["T"], S=ini["S"], ETA=ini["eta"], QX=ini["U"],
+                      QY=ini["V"])
+        par = slim.slim_params_default(scheme=1, n_sub=20, kappa_v=1e-3, nu_v=1e-3, kappa_h=1.0,
+                                       nu_h=1.0)
+        dt = 20 * wl.fields.dt_2d(m)
+        tn = autotune.autotune(m, slim.SLIM_MIXED, par, fields, dt, use_cache=False)
+        par.tile_prisms, par.blocks_per_sm = tn["tile_prisms"], tn["blocks_per_sm"]
+        with slim.Model(m, slim.SLIM_MIXED, par) as mod:
+            for k, v in fields.items():
+                mod.upload(k, v)
+            t = 0.0
+            for _ in range(max(3, args.warmup)):
+                slim.slim_step(mod.state, t, dt, stream.cuda_stream); t += dt
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                slim.slim_step(mod.state, t, dt, stream.cuda_stream); t += dt
+            e1.record(stream)
+            torch.cuda.synchronize()
+            slim.slim_state_check(mod.state)
+            ms = e0.elapsed_time(e1) / args.steps
+        P = int(m.n_layers.sum())
+        rows.append(dict(layers=N, prisms=P, ms_per_step=ms, ns_per_prism_step=ms * 1e6 / P,
+                         dof_updates_per_s=6.0 * P * 4 / (ms / 1e3),
+                         prisms_per_block=tn["tile_prisms"], blocks_per_sm=tn["blocks_per_sm"]))
+    return dict(layer_sweep=rows, n_tri=base.n_tri, precision="mixed", scheme="split", n_sub=20,
+                steps=args.steps)
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -395,7 +448,8 @@ def oracle_sample(args, m, seconds: float):
             if el >= seconds:
                 break
     else:
-        ini = wl.c2_initial_state(sub) if args.workload == "basin_baroclinic" else wl.c4_initial_state(sub)
+        ini = {"basin_baroclinic": wl.c2_initial_state, "zlevel_baroclinic": wl.c4_initial_state,
+               "reef_baroclinic": wl.c5_initial_state}[args.workload](sub)
         st = obc.State(u=otr.to3(ini["u"], P), v=otr.to3(ini["v"], P), T=otr.to3(ini["T"], P),
                        S=otr.to3(ini["S"], P), eta=otr.to2(ini["eta"], sub.n_tri),
                        U=otr.to2(ini["U"], sub.n_tri), V=otr.to2(ini["V"], sub.n_tri))
@@ -443,6 +497,10 @@ def main():
                     data="synthetic", config=cfg, cpu_baseline=cb,
                     e2e=dict(value=cb["value"], unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
         print(json.dumps(line))
+        return
+    if args.layer_sweep:
+        if rank == 0:
+            print(json.dumps(layer_sweep(args)))
         return
     m, res, clocks = run_ours(args, rank, world)
     cfg.update(n_tri=m.n_tri, n_prisms=m.n_prisms, layers=int(m.n_layers.max()),

@@ -450,3 +450,74 @@ def test_split_forcing_mixed_and_constants(slim):
                 slim.slim_step(mod.state, n * dt, dt)
             assert np.abs(mod.download("T") - 20.0).max() < tol * 20.0
             assert np.abs(mod.download("S") - 35.0).max() < tol * 35.0
+
+
+@pytest.fixture(scope="module")
+def reef_full():
+    """The reef-scale stress workload at full size (~2.4M triangles around 400
+    islands, 1-30 z-levels, ~41M prisms; the mesh is cached after its first build)."""
+    W = wl.WORKLOADS["reef_baroclinic"]
+    m = W["mesh"]()
+    ini = wl.c5_initial_state(m)
+    fields = dict(U=ini["u"], V=ini["v"], T=ini["T"], S=ini["S"], ETA=ini["eta"], QX=ini["U"], QY=ini["V"])
+    par = dict(scheme=1, n_sub=W["n_sub"], kappa_v=W["kappa_v"], nu_v=W["nu_v"],
+               kappa_h=W.get("kappa_h", 0.0), nu_h=W.get("nu_h", 0.0))
+    return m, fields, par, W["n_sub"] * wl.fields.dt_2d(m)
+
+
+def test_split_reef_full_size(slim, reef_full):
+    """Largest configuration, bench launch shape (512-prism tiles): constant tracers
+    stay constant in the mixed form, the pressure gradient of the FP64 step matches
+    the oracle at sampled columns (coastline ones included), and the mixed step
+    agrees with the FP64 one."""
+    from oracle import baroclinic as bc
+    from oracle.mesh import OMesh
+    m, fields, par, dt = reef_full
+    assert m.n_tri > 2_000_000 and int(m.n_layers.sum()) > 40_000_000
+    pm = slim.slim_params_default(**par)
+    pm.tile_prisms, pm.blocks_per_sm = 512, 4
+    const = dict(fields, T=np.full_like(fields["T"], 20.0), S=np.full_like(fields["S"], 35.0))
+    with model(slim, m, slim.SLIM_MIXED, pm, const, tile=512) as mod:
+        for n in range(2):
+            slim.slim_step(mod.state, n * dt, dt)
+        slim.slim_state_check(mod.state)
+        assert np.abs(mod.download("T") - 20.0).max() < 1e-5 * 20.0
+    del const
+    res = {}
+    for prec in (slim.SLIM_FP64, slim.SLIM_MIXED):
+        p = slim.slim_params_default(**par)
+        p.tile_prisms, p.blocks_per_sm = 512, 2 if prec == slim.SLIM_FP64 else 4
+        with model(slim, m, prec, p, fields, tile=512) as mod:
+            slim.slim_step(mod.state, 0.0, dt)
+            slim.slim_state_check(mod.state)
+            res[prec] = {f: mod.download(f) for f in ("U", "T", "S", "ETA")}
+            if prec == slim.SLIM_MIXED:
+                for f in ("T", "S"):
+                    assert rel_l2(res[prec][f], res[slim.SLIM_FP64][f]) < 1e-6, f
+                for f in ("U", "ETA"):
+                    assert rel_l2(res[prec][f], res[slim.SLIM_FP64][f]) < 1e-3, f
+            if prec == slim.SLIM_FP64:
+                # the stepped state is still nearly z-only (its r is the rounding residue
+                # of cancelling terms, an absolute floor that grows down 30 z-levels): add
+                # a horizontal temperature variation large enough to dominate it
+                t_of = np.repeat(np.arange(m.n_tri), m.n_layers)
+                xv = m.xy[m.tri[t_of].T, 0]                                   # (3, P) node x
+                T_hpg = res[prec]["T"] + 4.0 * np.sin(2 * np.pi * np.broadcast_to(xv[None], (2,) + xv.shape).ravel() / 50e3)
+                mod.upload("T", T_hpg)
+                slim.slim_hpg(mod.state)
+                rx = mod.download("R_X")
+    st = res[slim.SLIM_FP64]
+    rng = np.random.default_rng(5)
+    coast = np.nonzero((m.bnd == 1).any(axis=1))[0]
+    seeds = np.unique(np.concatenate([rng.choice(m.n_tri, 6, replace=False), rng.choice(coast, 4, replace=False)]))
+    p = slim.slim_params_default(**par)
+    got, ref = [], []
+    for sd in seeds:
+        sub, tmap, pos = ring_submesh(m, np.array([sd]), 2)
+        om = OMesh(sub)
+        ox, _ = bc.hpg(om, oracle_params(p), restrict3(T_hpg, m, tmap), restrict3(st["S"], m, tmap),
+                       restrict2(st["ETA"], m, tmap))
+        pr = prisms_of(sub.n_layers, pos)
+        got.append(restrict3(rx, m, np.array([sd])).ravel())
+        ref.append(ox[:, :, pr].ravel())
+    assert rel_l2(np.concatenate(got), np.concatenate(ref)) < TOL_R

@@ -17,7 +17,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .meshes import Mesh, c1_mesh, c2_mesh, c4_mesh
+from .meshes import Mesh, c1_mesh, c2_mesh, c4_mesh, c5_mesh, cached_mesh
 
 
 def col_offsets(m: Mesh) -> np.ndarray:
@@ -143,4 +143,11 @@ WORKLOADS = {
                              kappa_v=1e-3, nu_v=1e-3, kappa_h=1.0, nu_h=1.0, scheme="split"),
     "zlevel_baroclinic": dict(mesh=lambda: c4_mesh(500_000, 0), steps=3, n_sub=20,
                               kappa_v=1e-3, nu_v=1e-3, kappa_h=1.0, nu_h=1.0, scheme="split"),
+    # reef-scale stress run: ~2.4M triangles around 400 islands, 1-30 z-levels (~41M prisms)
+    "reef_baroclinic": dict(mesh=lambda: cached_mesh("reef_c5_v1", c5_mesh), steps=2000, n_sub=20,
+                            kappa_v=1e-3, nu_v=1e-3, kappa_h=1.0, nu_h=1.0, scheme="split"),
 }
+
+
+def c5_initial_state(m: Mesh) -> dict:
+    return c2_initial_state(m, h_max=1000.0)

@@ -236,6 +236,15 @@ def basin_mesh(Lx: float, Ly: float, nx0: int, ny0: int, s_min: float, s_max: fl
                seed: int, jitter: float = 0.2, hilbert: bool = True) -> tuple[np.ndarray, np.ndarray]:
     """Graded conforming triangulation of [0,Lx] x [0,Ly], finest (edge ~ s_min) at x = 0,
     coarsening linearly to s_max at x = Lx.  Returns (xy, tri), tri CCW."""
+    target = lambda x, y: s_min + (s_max - s_min) * np.clip(x / Lx, 0.0, 1.0)
+    return graded_mesh(Lx, Ly, nx0, ny0, target, seed, jitter, hilbert)
+
+
+def graded_mesh(Lx: float, Ly: float, nx0: int, ny0: int, target, seed: int, jitter: float = 0.2,
+                hilbert: bool = True, keep=None) -> tuple[np.ndarray, np.ndarray]:
+    """Conforming newest-vertex-bisection triangulation of [0,Lx] x [0,Ly] refined until
+    every edge is below the size field target(x, y); ``keep(cx, cy)`` (optional) selects
+    the triangles to keep by their centroids (holes).  Returns (xy, tri), tri CCW."""
     i, j = np.meshgrid(np.arange(nx0 + 1), np.arange(ny0 + 1), indexing="xy")
     xy = [(float(ii * Lx / nx0), float(jj * Ly / ny0)) for ii, jj in zip(i.ravel(), j.ravel())]
     vid = lambda ii, jj: jj * (nx0 + 1) + ii
@@ -246,10 +255,16 @@ def basin_mesh(Lx: float, Ly: float, nx0: int, ny0: int, s_min: float, s_max: fl
             # newest vertex first; the shared diagonal (v00, v11) is both triangles' refinement edge
             tris.append((v10, v11, v00))
             tris.append((v01, v00, v11))
-    target = lambda x, y: s_min + (s_max - s_min) * np.clip(x / Lx, 0.0, 1.0)
     xy, tris = _nvb_refine(xy, tris, target)
     P = np.asarray(xy, dtype=np.float64)
     T = np.asarray(tris, dtype=np.int64)
+    if keep is not None:
+        c = P[T].mean(axis=1)
+        T = T[keep(c[:, 0], c[:, 1])]
+        used = np.unique(T)
+        remap = -np.ones(P.shape[0], np.int64)
+        remap[used] = np.arange(used.size)
+        P, T = P[used], remap[T]
     # orient counter-clockwise
     u = P[T[:, 1]] - P[T[:, 0]]
     v = P[T[:, 2]] - P[T[:, 0]]
@@ -343,3 +358,81 @@ def c4_mesh(target_tri: int = 500_000, seed: int = 0, n_max: int = 60,
     bnd = _tag_boundary(xy, tri, lambda x, y: x > Lx - 1e-3)
     return Mesh(xy=xy, tri=tri, h_tri=h_tri, n_layers=nt, bnd=bnd, levels=levels,
                 name=f"zlevel{tri.shape[0]}")
+
+
+# ----------------------------------------------------------------------------
+# reef-scale stress mesh: islands, multiscale coastline, uneven columns
+# ----------------------------------------------------------------------------
+def reef_islands(n: int, Lx: float, Ly: float, seed: int, r_min: float = 100.0, r_max: float = 2000.0):
+    """n circular islands (centres uniform, 5 km from the outer boundary; radii
+    log-uniform in [r_min, r_max])."""
+    rng = np.random.default_rng(seed + 7)
+    cx = rng.uniform(5e3, Lx - 5e3, n)
+    cy = rng.uniform(5e3, Ly - 5e3, n)
+    r = np.exp(rng.uniform(np.log(r_min), np.log(r_max), n))
+    return cx, cy, r
+
+
+def _coast_distance(x, y, isl, k: int = 16):
+    """Distance to the nearest island coastline (0 inside an island): the minimum of
+    |p - c_i| - r_i over the k nearest centres, exact whenever the nearest coast
+    belongs to one of them; a point whose k-th centre is nearer than its best
+    coast distance plus the largest radius is checked against all islands."""
+    from scipy.spatial import cKDTree
+    cx, cy, r = isl
+    x = np.asarray(x, np.float64).ravel(); y = np.asarray(y, np.float64).ravel()
+    pts = np.stack([x, y], axis=1)
+    tree = cKDTree(np.stack([cx, cy], axis=1))
+    kk = min(k, cx.size)
+    dist, idx = tree.query(pts, k=kk)
+    dist = dist.reshape(pts.shape[0], kk); idx = idx.reshape(pts.shape[0], kk)
+    d = np.maximum(dist - r[idx], 0.0).min(axis=1)
+    unsure = dist[:, -1] < d + r.max()
+    if unsure.any() and kk < cx.size:
+        q = pts[unsure]
+        dx = q[:, 0:1] - cx[None]; dy = q[:, 1:2] - cy[None]
+        d[unsure] = np.maximum(np.sqrt(dx * dx + dy * dy) - r[None], 0.0).min(axis=1)
+    return d
+
+
+def c5_mesh(n_islands: int = 400, Lx: float = 400e3, Ly: float = 200e3, seed: int = 0,
+            s_min: float = 50.0, s_max: float = 5000.0, ramp: float = 0.15, n_max: int = 30,
+            h_min: float = 1.0, h_max: float = 1000.0, h_scale: float = 6e3) -> Mesh:
+    """Reef-scale stress mesh: edge ~ s_min at the island coastlines growing by
+    ``ramp`` per metre of distance to s_max, triangles inside the islands removed
+    (their coastlines are walls), open boundary at x = Lx, walls elsewhere; depth
+    h = h_min + (h_max - h_min) tanh(d / h_scale) with d the distance to the nearest
+    coast; z-levels (geometric from 1 m) with at most n_max layers per column."""
+    isl = reef_islands(n_islands, Lx, Ly, seed)
+    target = lambda x, y: np.minimum(s_max, s_min + ramp * _coast_distance(x, y, isl))
+    cx, cy, r = isl
+    keep = lambda x, y: _coast_distance(x, y, isl) > 0.0
+    xy, tri = graded_mesh(Lx, Ly, 40, 20, target, seed, keep=keep)
+    d = _coast_distance(xy[:, 0], xy[:, 1], isl)
+    h_vert = h_min + (h_max - h_min) * np.tanh(d / h_scale)
+    levels = zlevels(n_max, 1.0, h_max)
+    nt, h_tri = zlevel_columns(h_vert, tri, levels)
+    bnd = _tag_boundary(xy, tri, lambda x, y: x > Lx - 1e-3)
+    return Mesh(xy=xy, tri=tri, h_tri=h_tri, n_layers=nt, bnd=bnd, levels=levels,
+                name=f"reef{tri.shape[0]}")
+
+
+def cached_mesh(name: str, build) -> Mesh:
+    """``build()`` once per machine: the mesh is kept as an .npz file in the system
+    temporary directory under ``name`` (large generated meshes take minutes)."""
+    import os
+    import tempfile
+    d = os.path.join(tempfile.gettempdir(), "slim_gb300_meshes")
+    path = os.path.join(d, name + ".npz")
+    if os.path.exists(path):
+        z = np.load(path, allow_pickle=False)
+        lv = z["levels"]
+        return Mesh(xy=z["xy"], tri=z["tri"], h_tri=z["h_tri"], n_layers=z["n_layers"], bnd=z["bnd"],
+                    levels=lv if lv.size else None, name=str(z["name"]))
+    m = build()
+    os.makedirs(d, exist_ok=True)
+    tmp = path + f".{os.getpid()}.tmp.npz"
+    np.savez(tmp, xy=m.xy, tri=m.tri, h_tri=m.h_tri, n_layers=m.n_layers, bnd=m.bnd,
+             levels=m.levels if m.levels is not None else np.zeros(0), name=m.name)
+    os.replace(tmp, path)
+    return m
