@@ -341,9 +341,11 @@ def zlevel_columns(h_vert: np.ndarray, tri: np.ndarray, levels: np.ndarray,
 def c4_mesh(target_tri: int = 500_000, seed: int = 0, n_max: int = 60,
             h_min: float = 2.0, h_max: float = 600.0) -> Mesh:
     """Basin generator at ~500k triangles with log-uniform smooth bathymetry in
-    [2, 600] m and z-level layering of 1..60 layers per column."""
+    [2, 600] m (a smooth seeded noise field, rank-mapped to a uniform variable so
+    that the depth is log-uniform) and z-level layering (geometric levels from 1 m)
+    of 1..60 layers per column: ~12M prisms at the default size."""
     Lx, Ly = 200e3, 100e3
-    s_min = 175.0 * (200_000 / target_tri)
+    s_min = 146.0 * (200_000 / target_tri)
     xy, tri = basin_mesh(Lx, Ly, 20, 10, s_min, 4000.0, seed)
     rng = np.random.default_rng(seed + 1)
     noise = np.zeros(xy.shape[0])
@@ -351,9 +353,9 @@ def c4_mesh(target_tri: int = 500_000, seed: int = 0, n_max: int = 60,
         kx, ky = rng.uniform(1, 6, size=2) * 2 * np.pi / np.array([Lx, Ly])
         ph = rng.uniform(0, 2 * np.pi)
         noise += np.sin(kx * xy[:, 0] + ky * xy[:, 1] + ph)
-    noise = (noise - noise.min()) / (noise.max() - noise.min())
-    h_vert = np.exp(np.log(h_min) + noise * (np.log(h_max) - np.log(h_min)))
-    levels = zlevels(n_max, 2.0, h_max)
+    u = (np.argsort(np.argsort(noise)) + 0.5) / noise.size      # uniform on (0, 1)
+    h_vert = np.exp(np.log(h_min) + u * (np.log(h_max) - np.log(h_min)))
+    levels = zlevels(n_max, 1.0, h_max)
     nt, h_tri = zlevel_columns(h_vert, tri, levels)
     bnd = _tag_boundary(xy, tri, lambda x, y: x > Lx - 1e-3)
     return Mesh(xy=xy, tri=tri, h_tri=h_tri, n_layers=nt, bnd=bnd, levels=levels,
