@@ -833,6 +833,11 @@ __global__ void __launch_bounds__(256) k_ext2d_run(DevMesh m, SplitBufs bf, Mx2d
 //   F2D = (Q1 - (Q0 + T S3/w))/T, Dq = Qbar - sum q, st_end = 1 + eta1/h,
 //   gcor = (Gbar - {Qbar}.n) / (paired layer thickness at the edge point)
 // ---------------------------------------------------------------------------
+// FP64 value in the compute type (the FP32 conversion on the integer pipe)
+template <typename R> __device__ __forceinline__ R to_r(double x);
+template <> __device__ __forceinline__ double to_r<double>(double x) { return x; }
+template <> __device__ __forceinline__ float to_r<float>(double x) { return d2f_bits(x); }
+
 template <typename R>
 __global__ void k_couple2d(DevMesh m, const double* __restrict__ e1, const double* __restrict__ U1,
                            const double* __restrict__ V1, const double* __restrict__ U0,
@@ -851,22 +856,25 @@ __global__ void k_couple2d(DevMesh m, const double* __restrict__ e1, const doubl
   if (t >= nt) return;
   const double iw = iw6[t];  // 1 / (J_h/6)
   const int N = m.col_off[t + 1] - m.col_off[t];
+  // the differences that cancel (F2D, Qbar - sum q, Gbar - {Qbar}.n) are FP64; in
+  // the mixed form the paired thickness and the division are FP32 and the
+  // conversions run on the integer pipe
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int ia = a * nt + t;
     const double fx = (U1[ia] - (U0[ia] + T * (S3x[ia] * iw))) * iT;
     const double fy = (V1[ia] - (V0[ia] + T * (S3y[ia] * iw))) * iT;
     F2x[ia] = fx; F2y[ia] = fy;
-    F2x_r[ia] = (R)fx; F2y_r[ia] = (R)fy;
-    Dqx_r[ia] = (R)(Qbx[ia] - Sqx[ia]);
-    Dqy_r[ia] = (R)(Qby[ia] - Sqy[ia]);
-    st_end[ia] = (R)(1.0 + e1[ia] * m.ih[ia]);
+    F2x_r[ia] = to_r<R>(fx); F2y_r[ia] = to_r<R>(fy);
+    Dqx_r[ia] = to_r<R>(Qbx[ia] - Sqx[ia]);
+    Dqy_r[ia] = to_r<R>(Qby[ia] - Sqy[ia]);
+    st_end[ia] = to_r<R>(1.0 + e1[ia] * m.ih[ia]);
   }
   // paired rest thickness of vertex i of a column of N layers over its first Np layers
-  auto paired = [&](int i, int Nc, int Np) -> double {
-    if (Np >= Nc) return m.h[i];
-    if (m.n_levels == 0) return m.hN[i] * Np;
-    return -m.levels[Np];
+  auto paired = [&](int i, int Nc, int Np) -> R {
+    if (Np >= Nc) return Geo<R>::h(m, i);
+    if (m.n_levels == 0) return Geo<R>::hN(m, i) * (R)Np;
+    return -Geo<R>::lev(m, Np);
   };
 #pragma unroll
   for (int ed = 0; ed < 3; ++ed) {
@@ -875,7 +883,8 @@ __global__ void k_couple2d(DevMesh m, const double* __restrict__ e1, const doubl
     const double nx = m.enx[ed * nt + t], ny = m.eny[ed * nt + t];
     for (int gs = 0; gs < 2; ++gs) {
       const double b0 = gs ? SLIM_GL2 : SLIM_GL1, b1 = gs ? SLIM_GL1 : SLIM_GL2;
-      double g = 0.0;
+      const R b0r = gs ? (R)SLIM_GL2 : (R)SLIM_GL1, b1r = gs ? (R)SLIM_GL1 : (R)SLIM_GL2;
+      R g = 0;
       if (ei.x != -1) {
         const int i0 = a0 * nt + t, i1 = a1 * nt + t;
         const double Qo = b0 * (Qbx[i0] * nx + Qby[i0] * ny) + b1 * (Qbx[i1] * nx + Qby[i1] * ny);
@@ -891,19 +900,17 @@ __global__ void k_couple2d(DevMesh m, const double* __restrict__ e1, const doubl
           Qavg = 0.5 * (Qo + b0 * qe(i0) + b1 * qe(i1));
         }
         const int Np = ei.x >= 0 ? min(N, ei.z) : N;
-        double tot = b0 * paired(i0, N, Np) * (double)st_ev[i0] + b1 * paired(i1, N, Np) * (double)st_ev[i1];
+        R tot = b0r * paired(i0, N, Np) * st_ev[i0] + b1r * paired(i1, N, Np) * st_ev[i1];
         if (ei.x >= 0) {
           const int l0 = ei.w & 3, l1 = (ei.w >> 2) & 3;
           const int j0 = l0 * nt + ei.x, j1 = l1 * nt + ei.x;
           const double Qn = b0 * (Qbx[j0] * nx + Qby[j0] * ny) + b1 * (Qbx[j1] * nx + Qby[j1] * ny);
           Qavg = 0.5 * (Qo + Qn);
-          tot += b0 * paired(j0, ei.z, Np) * (double)st_ev[j0] + b1 * paired(j1, ei.z, Np) * (double)st_ev[j1];
+          tot += b0r * paired(j0, ei.z, Np) * st_ev[j0] + b1r * paired(j1, ei.z, Np) * st_ev[j1];
         }
-        const double dG = Gb[(ed * nt + t) * 2 + gs] - Qavg;
-        // the result is stored in R: the mixed form divides in FP32
-        g = sizeof(R) == 8 ? dG / tot : (double)((float)dG / (float)tot);
+        g = to_r<R>(Gb[(ed * nt + t) * 2 + gs] - Qavg) / tot;
       }
-      gcor_r[(ed * nt + t) * 2 + gs] = (R)g;
+      gcor_r[(ed * nt + t) * 2 + gs] = g;
     }
   }
 }
