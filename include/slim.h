@@ -256,8 +256,10 @@ slim_status slim_vertical_solve(slim_state* s, int field, double beta_dt, const 
  * state's T, S and the horizontal baroclinic pressure gradient r of Eq. 8 at the
  * state's elevation: per column the system D_vu r = F of Eq. 16 (printed D_vu
  * pattern with the consistent M_h), solved top-down by Algorithm 1, with
- * F = int v g grad_h rho' dV in weak form (central density traces on lateral,
- * top and bottom faces) and the surface value g rho'(eta) grad(eta).  Writes
+ * F = -int v g grad_h rho' dV in weak form (central density traces on lateral,
+ * top and bottom faces) and the surface value g rho'(eta) grad(eta): r is the
+ * horizontal gradient of the baroclinic pressure g int_z^eta rho' dz', so
+ * dr/dz = -g grad_h rho' (Eq. 8's derivative taken downward).  Writes
  * SLIM_FIELD_R_X and SLIM_FIELD_R_Y.  SLIM_SCHEME_SPLIT only. */
 slim_status slim_hpg(slim_state* s, void* stream);
 

@@ -119,9 +119,12 @@ def _z_nodes(om: OMesh, eta: np.ndarray):
 
 
 def hpg_rhs(om: OMesh, par: Params, rho: np.ndarray, eta: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
-    """F = int_K v g grad_h rho' dV for v = phi_a psi_c (physical horizontal gradient at
-    constant z), in the weak form
-        -g int_K rho' grad_h v dV + g oint_dK v {rho'} n_h dS
+    """F = -int_K v g grad_h rho' dV for v = phi_a psi_c (physical horizontal gradient at
+    constant z), the right-hand side of dr/dz = -g grad_h rho': r is the horizontal
+    gradient of the baroclinic hydrostatic pressure p' = g int_z^eta rho' dz' (Eq. 7),
+    so it grows downward by g grad_h rho' per metre (Eq. 8 integrated from the top
+    down).  In the weak form
+        +g int_K rho' grad_h v dV - g oint_dK v {rho'} n_h dS
     with grad_h v|_z = grad(phi_a) psi_c - phi_a psi_c' grad_xy z / z_zeta and
     dV = J_h z_zeta dA dzeta.  Lateral faces: normal n_e, dS = z_zeta dl dzeta (own
     geometry), central {rho'} (own value on boundaries).  Top/bottom faces:
@@ -153,7 +156,7 @@ def hpg_rhs(om: OMesh, par: Params, rho: np.ndarray, eta: np.ndarray) -> tuple[n
                 for c in range(2):
                     # rho' (grad phi_a psi_c z_zeta - phi_a dpsi_c grad z)
                     for d, F in ((0, Fx), (1, Fy)):
-                        F[c, a] -= g * w * rp * (grad[:, a, d] * ps[c] * zz - ph[a] * ds[c] * gz[:, d])
+                        F[c, a] += g * w * rp * (grad[:, a, d] * ps[c] * zz - ph[a] * ds[c] * gz[:, d])
     # lateral faces
     for e in range(3):
         pn, ok = om.nbr_prism(e)
@@ -177,8 +180,8 @@ def hpg_rhs(om: OMesh, par: Params, rho: np.ndarray, eta: np.ndarray) -> tuple[n
                 w = 0.5 * L * ws * wz * zz
                 for j in range(2):
                     for c in range(2):
-                        Fx[c, own[j]] += g * w * rh * n[:, 0] * wv[j] * ps[c]
-                        Fy[c, own[j]] += g * w * rh * n[:, 1] * wv[j] * ps[c]
+                        Fx[c, own[j]] -= g * w * rh * n[:, 0] * wv[j] * ps[c]
+                        Fy[c, own[j]] -= g * w * rh * n[:, 1] * wv[j] * ps[c]
     # top and bottom faces (zeta = +1: psi_top = 1; zeta = -1: psi_bot = 1)
     above = np.where(om.k_of > 0, np.arange(om.P) - 1, -1)
     below = np.where(om.k_of + 1 < om.N[t], np.arange(om.P) + 1, -1)
@@ -193,8 +196,8 @@ def hpg_rhs(om: OMesh, par: Params, rho: np.ndarray, eta: np.ndarray) -> tuple[n
         r_bot = np.where(below >= 0, 0.5 * (r_bot_own + r_bot_dn), r_bot_own)
         for a in range(3):
             for d, F in ((0, Fx), (1, Fy)):
-                F[0, a] += g * w * ph[a] * r_top * (-gzt[:, d])
-                F[1, a] += g * w * ph[a] * r_bot * (+gzb[:, d])
+                F[0, a] -= g * w * ph[a] * r_top * (-gzt[:, d])
+                F[1, a] -= g * w * ph[a] * r_bot * (+gzb[:, d])
     # surface condition: r^ext on the top face of layer 0 = g rho'(top) grad eta
     Mh = om.mass2d()[t]                                    # (P, 3, 3)
     geta = np.stack([sum(eta[a, t] * grad[:, a, d] for a in range(3)) for d in range(2)], -1)

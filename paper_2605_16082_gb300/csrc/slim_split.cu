@@ -286,7 +286,9 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
     const R gzbx = zb[0] * gx[0] + zb[1] * gx[1] + zb[2] * gx[2];
     const R gzby = zb[0] * gy[0] + zb[1] * gy[1] + zb[2] * gy[2];
     R Fx[2][3], Fy[2][3];
-    // volume: -g int rho' grad(phi_a) psi_c z_zeta  +  g int rho' phi_a psi_c' grad z
+    // right-hand side of dr/dz = -g grad_h rho' (r is the horizontal gradient of the
+    // baroclinic hydrostatic pressure g int_z^eta rho', so it grows downward)
+    // volume: +g int rho' grad(phi_a) psi_c z_zeta  -  g int rho' phi_a psi_c' grad z
     {
       const R shz = hz[0] + hz[1] + hz[2];
       R A[2], Sr[2];
@@ -303,13 +305,13 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
       for (int a = 0; a < 3; ++a) {
         const R m0 = w24 * (Sr[0] + r[0][a]), m1 = w24 * (Sr[1] + r[1][a]);
         const R bx = m0 * Z0x + m1 * Z1x, by = m0 * Z0y + m1 * Z1y;
-        Fx[0][a] = g * (-gx[a] * tA0 + (R)0.5 * bx);
-        Fy[0][a] = g * (-gy[a] * tA0 + (R)0.5 * by);
-        Fx[1][a] = g * (-gx[a] * tA1 - (R)0.5 * bx);
-        Fy[1][a] = g * (-gy[a] * tA1 - (R)0.5 * by);
+        Fx[0][a] = g * (gx[a] * tA0 - (R)0.5 * bx);
+        Fy[0][a] = g * (gy[a] * tA0 - (R)0.5 * by);
+        Fx[1][a] = g * (gx[a] * tA1 + (R)0.5 * bx);
+        Fy[1][a] = g * (gy[a] * tA1 + (R)0.5 * by);
       }
     }
-    // lateral faces: + g oint v {rho'} n z_zeta dl dzeta
+    // lateral faces: - g oint v {rho'} n z_zeta dl dzeta
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
       const int4 ei = m.einfo[e * nt + t];
@@ -341,7 +343,7 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
           const R B00 = b0 * z0, B01 = b0 * z1, B10 = b1 * z0, B11 = b1 * z1;
           R rh = B00 * r[0][a0] + B01 * r[1][a0] + B10 * r[0][a1] + B11 * r[1][a1];
           if (has_nb) rh = (R)0.5 * (rh + (B00 * rb[0][0] + B01 * rb[0][1] + B10 * rb[1][0] + B11 * rb[1][1]));
-          const R wx = g * half_len * zz * rh * nxe, wy = g * half_len * zz * rh * nye;
+          const R wx = -g * half_len * zz * rh * nxe, wy = -g * half_len * zz * rh * nye;
           Fx[0][a0] += wx * B00; Fx[1][a0] += wx * B01; Fx[0][a1] += wx * B10; Fx[1][a1] += wx * B11;
           Fy[0][a0] += wy * B00; Fy[1][a0] += wy * B01; Fy[0][a1] += wy * B10; Fy[1][a1] += wy * B11;
         }
@@ -373,8 +375,8 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const R mt = w24 * (srt + rt[a]), mb = w24 * (srb + rbt[a]);
-        Fx[0][a] -= g * mt * gztx; Fy[0][a] -= g * mt * gzty;
-        Fx[1][a] += g * mb * gzbx; Fy[1][a] += g * mb * gzby;
+        Fx[0][a] += g * mt * gztx; Fy[0][a] += g * mt * gzty;
+        Fx[1][a] -= g * mb * gzbx; Fy[1][a] -= g * mb * gzby;
       }
     }
     // surface condition r = g rho'(eta) grad(eta): F_top -= M_h r_surface (layer 0)

@@ -49,7 +49,10 @@ def test_hpg_vanishes_for_density_depending_on_z_only(slope):
 
 @pytest.mark.parametrize("slope", [False, True])
 def test_hpg_linear_in_x_density_gives_exact_profile(slope):
-    # rho' = a x: dr/dz = g a, r = 0 at a flat surface -> r_x = g a z
+    # r is the horizontal gradient of the baroclinic hydrostatic pressure
+    # p' = g int_z^eta rho' dz' (Eq. 7).  rho' = a x under a flat surface:
+    # p' = -g a x z, so r_x = -g a z (denser water to the east pushes westward at
+    # depth, and r grows downward: dr/dz = -g grad rho')
     m = flat_or_shelf(slope=slope)
     om = OMesh(m)
     par = bc.Params()
@@ -59,8 +62,26 @@ def test_hpg_linear_in_x_density_gives_exact_profile(slope):
     a = 3e-4
     Fx, Fy = bc.hpg_rhs(om, par, a * x, eta)
     rx, ry = bc.hpg_solve(om, Fx, Fy)
-    assert np.allclose(rx, par.g * a * z, rtol=0, atol=1e-12 * par.g * a * 60)
+    assert np.allclose(rx, -par.g * a * z, rtol=0, atol=1e-12 * par.g * a * 60)
     assert np.abs(ry).max() < 1e-12
+
+
+@pytest.mark.parametrize("slope", [False, True])
+def test_hpg_tilted_surface_and_density_gradient_together(slope):
+    # rho' = a x and eta = b x: p' = g int_z^eta a x dz' = g a x (b x - z), so
+    # r_x = d p'/dx = 2 g a b x - g a z: the surface term g rho'(eta) grad(eta)
+    # (Eq. 8) and the interior integral enter with the same sign at the surface
+    m = flat_or_shelf(slope=slope)
+    om = OMesh(m)
+    par = bc.Params()
+    a, b = 3e-4, 2e-5
+    eta = b * np.stack([om.X[:, j, 0] for j in range(3)])
+    z = nodal_z(om, eta)
+    x, _ = nodal_xy(om)
+    rx, ry = bc.hpg_solve(om, *bc.hpg_rhs(om, par, a * x, eta))
+    ex = 2 * par.g * a * b * x - par.g * a * z
+    assert np.allclose(rx, ex, rtol=0, atol=1e-11 * np.abs(ex).max())
+    assert np.abs(ry).max() < 1e-11 * np.abs(ex).max()
 
 
 def test_hpg_surface_term_constant_density_tilted_surface():
