@@ -142,10 +142,11 @@ typedef struct slim_params {
                           open boundaries, interpolated in time inside the kernels: the
                           2D mode takes the exterior transport Q_ext(t) (the column sum
                           of (dz_rest/2) u_ext) at every stage time, the 3D open faces
-                          the mean of the interior and exterior transport and the
-                          exterior state at the middle of the stage's 2D run (Sec. 3
-                          forcing data, Sec. 2.5 consistency); 0: interior transport and
-                          static exterior tracer profiles. */
+                          the exterior transport and state at the middle of the stage's
+                          2D run plus their layer share of the averaged 2D face flux
+                          (Sec. 3 forcing data, Sec. 2.5 consistency); 0: zero exterior
+                          transport in both (a characteristic condition around the tide
+                          elevation) and static exterior tracer profiles. */
 } slim_params;
 
 /* Fill *p with the defaults: g 9.81, rho0 1025, f 1e-4, alpha 2e-4, beta 7.6e-4,

@@ -331,10 +331,13 @@ def momentum_horizontal(om: OMesh, par: Params, u, v, qx, qy, rx, ry, dz, face_c
     """F_3D^h(u, q, r) (Eq. 11): advection -div(q u) (upwind), horizontal viscosity,
     Coriolis -f e_z x u, baroclinic pressure gradient -r/rho0 (lumped mass), bottom
     drag.  dz: layer thickness of the transport geometry.  ext = (u_ext, v_ext,
-    qx_ext, qy_ext): prescribed exterior velocity and transport at open boundaries."""
+    qx_ext, qy_ext): exterior velocity (None: zero-gradient) and transport at open
+    boundaries (None: the own transport, as in the prediction with the uncorrected
+    transport q)."""
     ux = vx = qe = None
     if ext is not None:
-        ux, vx, qe = ext[0], ext[1], (ext[2], ext[3])
+        ux, vx = ext[0], ext[1]
+        qe = None if ext[2] is None else (ext[2], ext[3])
     Fx = tr.horizontal_residual(om, qx, qy, u, T_ext=ux, face_corr=face_corr, q_ext=qe)
     Fy = tr.horizontal_residual(om, qx, qy, v, T_ext=vx, face_corr=face_corr, q_ext=qe)
     Fx += horizontal_viscosity(om, dz, u, par.nu_h, par.penalty_h)
@@ -360,8 +363,13 @@ def mode2d_residual(om: OMesh, par: Params, eta, U, V, time: float, Q_ext=None):
     with H = h + eta, c = sqrt(g (h^- + h^+)/2) (rest depth) at each edge point,
       F_eta = {Q}.n + c/2 (eta^- - eta^+),   eta^ = {eta} + (q^- - q^+)/(2c)
     (upwind flux of the linear wave system).  Walls: eta^+ = eta^-, q^+ = -q^-.
-    Open boundary: eta^+ = A cos(2 pi t / T_M2), Q^+ = Q^- (or the prescribed
-    exterior transport Q_ext = (Qx, Qy) at this time, (3, n_tri))."""
+    Open boundary: the exterior state comes from data alone, eta^+ = A cos(2 pi t /
+    T_M2) and Q^+ = 0 (or the prescribed exterior transport Q_ext = (Qx, Qy) at
+    this time, (3, n_tri)): with the upwind flux this is a characteristic
+    (radiating) condition whose boundary energy flux g eta^ F_eta = (g/4c)
+    (q^- + c eta^-)^2 >= 0 for zero data, so the boundary only removes energy.
+    Q^+ = Q^- instead feeds the interior's incoming characteristic back and leaves
+    a weakly growing boundary mode."""
     nt = om.n_tri
     g = par.g
     h = om.h.T                                             # (3, n_tri)
@@ -402,7 +410,7 @@ def mode2d_residual(om: OMesh, par: Params, eta, U, V, time: float, Q_ext=None):
             qn = (wv[0] * (U[l0, nbs] * n[:, 0] + V[l0, nbs] * n[:, 1])
                   + wv[1] * (U[l1, nbs] * n[:, 0] + V[l1, nbs] * n[:, 1]))
             # exterior states
-            q_open = qo
+            q_open = np.zeros_like(qo)
             if Q_ext is not None:
                 q_open = (wv[0] * (Q_ext[0][own[0]] * n[:, 0] + Q_ext[1][own[0]] * n[:, 1])
                           + wv[1] * (Q_ext[0][own[1]] * n[:, 0] + Q_ext[1][own[1]] * n[:, 1]))
@@ -486,13 +494,15 @@ def corrected_transport(om: OMesh, dz, qx, qy, Qbx, Qby):
     return qx + 0.5 * (frac * Dx)[None], qy + 0.5 * (frac * Dy)[None]
 
 
-def face_correction(om: OMesh, dz, Qbx, Qby, Gb, Q_ext=None):
+def face_correction(om: OMesh, dz, Qbx, Qby, Gb, Q_ext):
     """Per prism and lateral-face quadrature point, the additive correction of the
     normal transport c_k (Gbar - {Qbar}.n)/2 (units of q.n) that makes the column sum
     of the 3D lateral fluxes equal the 2D averaged face flux Gbar.  c_k = layer
     fraction of the face: (dz_k^- + dz_k^+) / sum over paired layers (own only at an
-    open boundary).  {Qbar} on an open boundary is the interior Qbar, or with a
-    prescribed exterior transport Q_ext (3, n_tri) the mean of both.  Walls: 0.
+    open boundary).  {Qbar} on an open boundary is the exterior transport Q_ext
+    (3, n_tri) alone, matching the 3D open-face transport q_ext, so that the open
+    face carries q_ext + c_k (Gbar - Q_ext.n)/2 (zero data: the 2D face flux spread
+    over the layers by thickness).  Walls: 0.
     Returns (P, 3, 2) [p][edge][edge point]."""
     P = om.P
     t, k = om.t_of, om.k_of
@@ -523,11 +533,8 @@ def face_correction(om: OMesh, dz, Qbx, Qby, Gb, Q_ext=None):
             ln0, ln1 = np.where(has_nb, loc[:, 0], 0), np.where(has_nb, loc[:, 1], 0)
             Qn = (wv[0] * (Qbx[ln0, tn] * n[:, 0] + Qby[ln0, tn] * n[:, 1])
                   + wv[1] * (Qbx[ln1, tn] * n[:, 0] + Qby[ln1, tn] * n[:, 1]))
-            Q_open = Qo
-            if Q_ext is not None:
-                Qx = (wv[0] * (Q_ext[0][own[0], t] * n[:, 0] + Q_ext[1][own[0], t] * n[:, 1])
+            Q_open = (wv[0] * (Q_ext[0][own[0], t] * n[:, 0] + Q_ext[1][own[0], t] * n[:, 1])
                       + wv[1] * (Q_ext[0][own[1], t] * n[:, 0] + Q_ext[1][own[1], t] * n[:, 1]))
-                Q_open = 0.5 * (Qo + Qx)
             Qavg = np.where(has_nb, 0.5 * (Qo + Qn), Q_open)
             delta = Gb[t, e, gi] - Qavg
             ck = np.where(tot > 0, pair / np.where(tot > 0, tot, 1.0), 0.0)
@@ -569,9 +576,13 @@ def split_stage(om: OMesh, par: Params, st0: State, ev: State, t0: float, dt: fl
     # open-boundary forcing: the 2D run of this stage spans [t0, t0 + dt] and sees
     # Q_ext(t) linear in t; the 3D terms take the exterior state at the middle of
     # that run, whose column transport is the run's average of Q_ext
+    # (unforced: zero exterior transport, zero-gradient exterior velocity)
     Fo = st0.forcing if par.forcing else None
-    ext3 = qe = Q_mid = Q_ab = None
+    Q_ab = None
     T_x, S_x = st0.T_ext, st0.S_ext
+    qe = (np.zeros_like(st0.u), np.zeros_like(st0.v))
+    Q_mid = (np.zeros((3, om.n_tri)), np.zeros((3, om.n_tri)))
+    ext3 = (None, None, qe[0], qe[1])
     if Fo is not None:
         ux, vx, T_x, S_x = Fo.at(t0 + 0.5 * dt)
         qe = exterior_transport(om, ux, vx)
@@ -580,9 +591,10 @@ def split_stage(om: OMesh, par: Params, st0: State, ev: State, t0: float, dt: fl
         Q_ab = (exterior_column_transport(om, Fo.u_a, Fo.v_a), exterior_column_transport(om, Fo.u_b, Fo.v_b))
     # 1. density and horizontal pressure gradient
     rx, ry = hpg(om, par, ev.T, ev.S, ev.eta)
-    # 2. prediction of F_3D^h with the transport q of the evaluation state
+    # 2. prediction of F_3D^h with the uncorrected transport q of the evaluation
+    # state on every face (open faces: the own q, the estimate of the 2D flux there)
     qx, qy = tr.transport(dz_ev, ev.u, ev.v)
-    Fpx, Fpy = momentum_horizontal(om, par, ev.u, ev.v, qx, qy, rx, ry, dz_ev, ext=ext3)
+    Fpx, Fpy = momentum_horizontal(om, par, ev.u, ev.v, qx, qy, rx, ry, dz_ev, ext=(ext3[0], ext3[1], None, None))
     S3x, S3y = _col_sum3(om, Fpx), _col_sum3(om, Fpy)
     # 3. external mode from the state at t0
     eta1, U1, V1, Qbx, Qby, Gb = mode2d_run(om, par, st0.eta, st0.U, st0.V, S3x, S3y, t0, dt, n_sub,

@@ -54,8 +54,10 @@ def horizontal_residual(om: OMesh, qx: np.ndarray, qy: np.ndarray, T: np.ndarray
     Walls carry no flux.  Open boundaries use the interior transport and, for
     inflow, the exterior state ``T_ext`` (same layout as T; zero-gradient when None).
     With ``q_ext`` (an exterior transport at the own nodes, same layout as qx, qy)
-    the open-boundary face transport is the mean of the interior and exterior ones,
-    as on interior faces.
+    the open-boundary face transport is the exterior one alone: the exterior state
+    comes from data, as in the 2D mode's characteristic open condition, so that the
+    interior's baroclinic velocity does not feed the boundary flux (the split
+    scheme; the prescribed-velocity tracer scheme passes none).
     ``face_corr`` (P, 3, 2): an additive correction of the normal transport per
     lateral face and edge quadrature point (the same at both zeta points), used
     for the transport that matches the averaged 2D face flux.
@@ -110,7 +112,7 @@ def horizontal_residual(om: OMesh, qx: np.ndarray, qy: np.ndarray, T: np.ndarray
                     T_x = sum(wv[j] * ps[c] * T_ext[c, own[j]] for j in range(2) for c in range(2))
                 else:
                     T_x = T_own
-                qn_open = qn_own if q_ext is None else 0.5 * (qn_own + qn_x)
+                qn_open = qn_own if q_ext is None else qn_x
                 qn = np.where(ok, 0.5 * (qn_own + qn_nb), np.where(is_open, qn_open, 0.0))
                 if face_corr is not None:
                     qn = qn + np.where(ok | is_open, face_corr[:, e, gi], 0.0)

@@ -646,8 +646,10 @@ __device__ __forceinline__ void ext2d_residual(const DevMesh& m, const SplitBufs
         ex = b0 * en0 + b1 * en1;
         qx = b0 * qn0 + b1 * qn1;
       } else if (ei.x == -2) {
+        // open boundary: exterior state from data alone (tide, and the prescribed
+        // transport or none), a characteristic condition that only removes energy
         ex = tide;
-        qx = bf.forcing ? forced_qn<RC>(bf, nt, a0 * nt + t, a1 * nt + t, b0, b1, nx, ny, th) : qo;
+        qx = bf.forcing ? forced_qn<RC>(bf, nt, a0 * nt + t, a1 * nt + t, b0, b1, nx, ny, th) : (RC)0;
       } else {
         ex = eo_;
         qx = -qo;
@@ -890,8 +892,10 @@ __global__ void k_couple2d(DevMesh m, const double* __restrict__ e1, const doubl
       if (ei.x != -1) {
         const int i0 = a0 * nt + t, i1 = a1 * nt + t;
         const double Qo = b0 * (Qbx[i0] * nx + Qby[i0] * ny) + b1 * (Qbx[i1] * nx + Qby[i1] * ny);
-        double Qavg = Qo;
-        if (ei.x == -2 && Qext) {  // forced open boundary: mean with the exterior transport
+        // open boundary: the exterior transport alone (zero unforced), matching the
+        // 3D open-face transport, so the face carries its layer share of Gbar
+        double Qavg = 0;
+        if (ei.x == -2 && Qext) {
           const double th = *th_mid;
           const size_t n2 = (size_t)3 * nt;
           auto qe = [&](int i) {
@@ -899,7 +903,7 @@ __global__ void k_couple2d(DevMesh m, const double* __restrict__ e1, const doubl
             const double y = Qext[n2 + i] + th * (Qext[3 * n2 + i] - Qext[n2 + i]);
             return x * nx + y * ny;
           };
-          Qavg = 0.5 * (Qo + b0 * qe(i0) + b1 * qe(i1));
+          Qavg = b0 * qe(i0) + b1 * qe(i1);
         }
         const int Np = ei.x >= 0 ? min(N, ei.z) : N;
         R tot = b0r * paired(i0, N, Np) * st_ev[i0] + b1r * paired(i1, N, Np) * st_ev[i1];

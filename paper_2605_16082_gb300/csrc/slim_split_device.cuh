@@ -142,7 +142,7 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
         fo1[0][c] = own.f1[c][a0]; fo1[1][c] = own.f1[c][a1];
       }
     }
-    bool has_nb = false;
+    bool has_nb = false, is_open = false;
     if (nb >= 0) {
       const int Nn = ei.z;
       if (k >= Nn) continue;  // wall against a shallower neighbour column
@@ -169,11 +169,12 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
         }
       }
     } else {  // open boundary
-      // forced: the exterior transport (dz_rest/2) u_ext and exterior values at
-      // theta of the middle of the stage's 2D run; the face transport is then the
-      // mean of both sides as on interior faces
+      // the face transport is the exterior one alone (the exterior state comes
+      // from data): forced, (dz_rest/2) u_ext at theta of the middle of the
+      // stage's 2D run, else zero; the face correction adds the layer's share of
+      // the 2D flux.  Inflow values: the exterior profiles (lerped when forced).
       const R th = in.Uxa ? *in.th : (R)0;
-      has_nb = in.Uxa != nullptr;
+      is_open = true;
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int la = j ? a1 : a0;
@@ -186,7 +187,7 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
             const R vx = in.Vxa[idx] + th * (in.Vxb[idx] - in.Vxa[idx]);
             qb[j][c] = hr * (ux * nxe + vx * nye);
           } else {
-            qb[j][c] = qo[j][c];
+            qb[j][c] = (R)0;
           }
           if (!UNIT) {
             fb0[j][c] = in.E0 ? (in.E0b ? in.E0[idx] + th * (in.E0b[idx] - in.E0[idx]) : in.E0[idx]) : fo0[j][c];
@@ -211,8 +212,10 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
         const R z1 = gz ? (R)SLIM_GL1 : (R)SLIM_GL2;
         const R B00 = b0 * z0, B01 = b0 * z1, B10 = b1 * z0, B11 = b1 * z1;
         const R qno = B00 * qo[0][0] + B01 * qo[0][1] + B10 * qo[1][0] + B11 * qo[1][1];
-        R qn = qno;
-        if (has_nb) qn = (R)0.5 * (qno + (B00 * qb[0][0] + B01 * qb[0][1] + B10 * qb[1][0] + B11 * qb[1][1]));
+        const R qnb = B00 * qb[0][0] + B01 * qb[0][1] + B10 * qb[1][0] + B11 * qb[1][1];
+        // (the prediction, without a face correction, keeps the uncorrected own
+        // transport at open faces: its estimate of the 2D flux there)
+        R qn = (is_open && in.gcor) ? qnb : (has_nb ? (R)0.5 * (qno + qnb) : qno);
         qn += corr;
         if (UNIT) {
           const R f = half_len * qn;
