@@ -38,6 +38,16 @@ def test_ext2d_bytes_depend_on_the_form(bench):
     assert bench.phase_bytes("ext2d", m, 8, 20) == 50 * 736.0
 
 
+def test_persistent_2d_launch_counts_its_rk_stages(bench):
+    # one persistent launch per split stage runs all its RK stages: the 2D bytes
+    # follow the stage count, not the launch count
+    m = types.SimpleNamespace(n_prisms=1_000_000, n_tri=50_000)
+    r = dict(phases={"ext2d": (1.8, 2), "momentum": (2.0, 2)}, rk2d_stages=90)
+    _, allk = bench.rooflines(r, m, "split", "mixed", "w", 6657.6, "measured")
+    assert allk["k_ext2d"]["launches"] == 2
+    assert allk["k_ext2d"]["achieved"] == pytest.approx(90 * 50_000 * 492.0 / 1.8e-3 / 1e9, rel=1e-3)
+
+
 def test_traffic_needs_the_same_sources(bench, monkeypatch):
     m = types.SimpleNamespace(n_prisms=1000, n_tri=50)
     r = dict(phases={"momentum": (2.0, 2), "tracers": (2.0, 2)})
