@@ -240,6 +240,38 @@ def lumped_source(om: OMesh, dz: np.ndarray, fx: np.ndarray) -> np.ndarray:
     return tr.apply_mass(om, dz, fx)
 
 
+def tri_cubic_moments() -> np.ndarray:
+    """I[a, b, e] = (1/J_h) int_K phi_a phi_b phi_e dA for the P1 basis of a triangle:
+    1/20 when a = b = e, 1/60 when exactly two indices agree, 1/120 when all differ
+    (the barycentric moments 2A p! q! r! / (p + q + r + 2)! with J_h = 2A)."""
+    I = np.empty((3, 3, 3))
+    for a in range(3):
+        for b in range(3):
+            for e in range(3):
+                n_eq = len({a, b, e})
+                I[a, b, e] = {1: 1.0 / 20.0, 2: 1.0 / 60.0, 3: 1.0 / 120.0}[n_eq]
+    return I
+
+
+def pressure_source(om: OMesh, dz: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """int_K phi_a psi_c r dV for the nodal field r (2, 3, P), integrated exactly: r is
+    P1 x P1 and z_zeta = sum_e phi_e dz_e / 2 is linear over the triangle, so
+        S[c, a] = J_h sum_d G_cd sum_b (sum_e I_abe dz_e / 2) r[d, b].
+    With the consistent M_h of the r solve (Eq. 16) this makes the momentum source
+    the weak pressure gradient itself, the negative adjoint of the weak divergence of
+    the continuity; the horizontally lumped product instead leaves M_l M_c^-1 between
+    them, and a stratified rest state then grows a slow mode on irregular meshes."""
+    G = tr.int_psi_psi()
+    I = tri_cubic_moments()
+    hz = 0.5 * dz                                                  # (3, P)
+    K = om.Jh[om.t_of][:, None, None] * np.einsum("abe,ep->pab", I, hz)   # (P, 3, 3)
+    Kr = np.einsum("pab,dbp->dap", K, r)                           # (2, 3, P)
+    out = np.empty_like(r)
+    for c in range(2):
+        out[c] = G[c, 0] * Kr[0] + G[c, 1] * Kr[1]
+    return out
+
+
 def horizontal_viscosity(om: OMesh, dz: np.ndarray, u: np.ndarray, nu: float, penalty: float) -> np.ndarray:
     """SIPG for div_zeta(nu z_zeta grad_zeta u) on coordinate surfaces, tested with
     phi_a psi_c:
@@ -329,8 +361,9 @@ def bottom_drag(om: OMesh, par: Params, u: np.ndarray, v: np.ndarray) -> tuple[n
 
 def momentum_horizontal(om: OMesh, par: Params, u, v, qx, qy, rx, ry, dz, face_corr=None, ext=None):
     """F_3D^h(u, q, r) (Eq. 11): advection -div(q u) (upwind), horizontal viscosity,
-    Coriolis -f e_z x u, baroclinic pressure gradient -r/rho0 (lumped mass), bottom
-    drag.  dz: layer thickness of the transport geometry.  ext = (u_ext, v_ext,
+    Coriolis -f e_z x u, baroclinic pressure gradient -r/rho0, bottom
+    drag (Coriolis with the lumped mass, the pressure gradient integrated exactly:
+    pressure_source).  dz: layer thickness of the transport geometry.  ext = (u_ext, v_ext,
     qx_ext, qy_ext): exterior velocity (None: zero-gradient) and transport at open
     boundaries (None: the own transport, as in the prediction with the uncorrected
     transport q)."""
@@ -342,8 +375,8 @@ def momentum_horizontal(om: OMesh, par: Params, u, v, qx, qy, rx, ry, dz, face_c
     Fy = tr.horizontal_residual(om, qx, qy, v, T_ext=vx, face_corr=face_corr, q_ext=qe)
     Fx += horizontal_viscosity(om, dz, u, par.nu_h, par.penalty_h)
     Fy += horizontal_viscosity(om, dz, v, par.nu_h, par.penalty_h)
-    Fx += lumped_source(om, dz, par.f * v - rx / par.rho0)
-    Fy += lumped_source(om, dz, -par.f * u - ry / par.rho0)
+    Fx += lumped_source(om, dz, par.f * v) - pressure_source(om, dz, rx) / par.rho0
+    Fy += lumped_source(om, dz, -par.f * u) - pressure_source(om, dz, ry) / par.rho0
     Dx, Dy = bottom_drag(om, par, u, v)
     return Fx + Dx, Fy + Dy
 

@@ -450,22 +450,44 @@ __device__ __forceinline__ void momentum_extras(const DevMesh& m, int t, int k, 
   const int nt = m.n_tri, P = m.P;
   if (pp.nu_h > (R)0) prism_sipg2<R>(m, t, k, N, own.u, own.v, U, V, st, pp.nu_h, pp.pen_h, Fx, Fy);
   const R f = pp.f, irho = pp.irho0;
-  const R w6 = Geo<R>::jh(m, t) * (R)(1.0 / 6.0);
+  const R jh = Geo<R>::jh(m, t);
+  const R w6 = jh * (R)(1.0 / 6.0);
+  R hz[3], rx[2][3], ry[2][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const int ia = a * nt + t;
-    const R hz = (R)0.5 * dz_rest_r<R>(m, ia, k, N) * st[ia];
-    R sx[2], sy[2];
+    hz[a] = (R)0.5 * dz_rest_r<R>(m, a * nt + t, k, N) * st[a * nt + t];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      sx[c] = f * own.v[c][a] - Rx[(size_t)(c * 3 + a) * P + p] * irho;
-      sy[c] = -f * own.u[c][a] - Ry[(size_t)(c * 3 + a) * P + p] * irho;
+      rx[c][a] = Rx[(size_t)(c * 3 + a) * P + p];
+      ry[c][a] = Ry[(size_t)(c * 3 + a) * P + p];
     }
+  }
+  // pressure gradient integrated exactly: (1/J_h) int phi_a phi_b z_zeta dA =
+  // hz_a/30 + sum/60 on the diagonal, (hz_a + hz_b + sum)/120 off it (the cubic
+  // moments 1/20, 1/60, 1/120 of the P1 basis against the linear z_zeta)
+  const R sh = hz[0] + hz[1] + hz[2];
+  const R pj = -irho * jh;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R kx[2] = {0, 0}, ky[2] = {0, 0};
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const R kab = (a == b) ? hz[a] * (R)(1.0 / 30.0) + sh * (R)(1.0 / 60.0)
+                             : (hz[a] + hz[b] + sh) * (R)(1.0 / 120.0);
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        kx[d] += kab * rx[d][b];
+        ky[d] += kab * ry[d][b];
+      }
+    }
+    const R G2 = (R)(2.0 / 3.0), G1 = (R)(1.0 / 3.0);
     R ox0, ox1, oy0, oy1;
-    lumped<R>(w6 * hz, sx[0], sx[1], ox0, ox1);
-    lumped<R>(w6 * hz, sy[0], sy[1], oy0, oy1);
-    Fx[0][a] += ox0; Fx[1][a] += ox1;
-    Fy[0][a] += oy0; Fy[1][a] += oy1;
+    lumped<R>(w6 * hz[a], f * own.v[0][a], f * own.v[1][a], ox0, ox1);
+    lumped<R>(w6 * hz[a], -f * own.u[0][a], -f * own.u[1][a], oy0, oy1);
+    Fx[0][a] += ox0 + pj * (G2 * kx[0] + G1 * kx[1]);
+    Fx[1][a] += ox1 + pj * (G1 * kx[0] + G2 * kx[1]);
+    Fy[0][a] += oy0 + pj * (G2 * ky[0] + G1 * ky[1]);
+    Fy[1][a] += oy1 + pj * (G1 * ky[0] + G2 * ky[1]);
     if (k == N - 1) {
       const R ub = own.u[1][a], vb = own.v[1][a];
       const R sp = sqrt(ub * ub + vb * vb);

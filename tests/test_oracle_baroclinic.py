@@ -98,6 +98,65 @@ def test_hpg_surface_term_constant_density_tilted_surface():
     assert np.abs(ry).max() < 1e-12
 
 
+def test_tri_cubic_moments_are_the_exact_integrals():
+    sympy = pytest.importorskip("sympy")
+    x, y = sympy.symbols("x y")
+    lam = (1 - x - y, x, y)                       # reference triangle, J_h = 1
+    I = bc.tri_cubic_moments()
+    for a in range(3):
+        for b in range(3):
+            for e in range(3):
+                v = sympy.integrate(sympy.integrate(lam[a] * lam[b] * lam[e], (y, 0, 1 - x)), (x, 0, 1))
+                assert I[a, b, e] == pytest.approx(float(v), rel=1e-14)
+
+
+def _prism_quadrature(X, hz, r):
+    # int_K phi_a psi_c r z_zeta dA dzeta by a collapsed (Duffy) Gauss rule, 4 x 4
+    # points on the triangle and 3 in zeta: exact for the quartic integrand
+    g, w = np.polynomial.legendre.leggauss(4)
+    gz, wz = np.polynomial.legendre.leggauss(3)
+    Jh = abs((X[1, 0] - X[0, 0]) * (X[2, 1] - X[0, 1]) - (X[1, 1] - X[0, 1]) * (X[2, 0] - X[0, 0]))
+    out = np.zeros((2, 3))
+    for i, (s_, ws) in enumerate(zip(g, w)):
+        for j, (t_, wt) in enumerate(zip(g, w)):
+            u = 0.5 * (1 + s_); v = 0.5 * (1 + t_) * (1 - u)
+            wt2 = ws * wt * 0.25 * (1 - u)             # d(u, v) of the unit triangle
+            ph = np.array([1 - u - v, u, v])
+            zz = ph @ hz
+            for zq, wq in zip(gz, wz):
+                ps = np.array([0.5 * (1 + zq), 0.5 * (1 - zq)])     # psi_top, psi_bot
+                rv = sum(ph[b] * ps[d] * r[d, b] for b in range(3) for d in range(2))
+                for c in range(2):
+                    out[c] += Jh * wt2 * wq * ph * ps[c] * rv * zz
+    return out
+
+
+def test_pressure_source_is_the_exact_integral():
+    m = flat_or_shelf(n=3, N=2, slope=True)
+    om = OMesh(m)
+    rng = np.random.default_rng(3)
+    eta = 0.3 * rng.standard_normal((3, m.n_tri))
+    dz = om.thickness(eta)
+    r = rng.standard_normal((2, 3, om.P))
+    S = bc.pressure_source(om, dz, r)
+    for p in (0, 5, om.P - 1):
+        X = om.X[om.t_of[p]]
+        ex = _prism_quadrature(X, 0.5 * dz[:, p], r[:, :, p])
+        assert np.allclose(S[:, :, p], ex, rtol=1e-12, atol=1e-12 * np.abs(ex).max())
+
+
+def test_pressure_source_reduces_to_the_lumped_mass_for_flat_layers():
+    # uniform thickness and r constant over each node level: exact and lumped agree;
+    # otherwise the horizontal coupling shows
+    m = flat_or_shelf(n=3, N=2, slope=False)
+    om = OMesh(m)
+    dz = om.thickness(np.zeros((3, m.n_tri)))
+    r = np.broadcast_to(np.array([1.7, -0.4])[:, None, None], (2, 3, om.P)).copy()
+    assert np.allclose(bc.pressure_source(om, dz, r), tr.apply_mass(om, dz, r), rtol=1e-13)
+    r[:, 0] += 1.0
+    assert not np.allclose(bc.pressure_source(om, dz, r), tr.apply_mass(om, dz, r), rtol=1e-6)
+
+
 def test_equation_of_state():
     par = bc.Params()
     assert bc.density_anomaly(par, np.array(par.T0), np.array(par.S0)) == 0.0
