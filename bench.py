@@ -175,8 +175,8 @@ KERNEL_OF = {"split": {"continuity": "k_cont_split", "hpg": "k_hpg", "mom_pred":
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
 # capture, valid only while the kernel sources hash to ``src``; see profiles/.
 TRAFFIC = {
-    ("k_update", "mixed", "basin_baroclinic"): dict(bytes=745.4e6, src="f9370ed0fe43191e"),
-    ("k_update", "fp64", "basin_baroclinic"): dict(bytes=1400.8e6, src="f9370ed0fe43191e"),
+    ("k_update", "mixed", "basin_baroclinic"): dict(bytes=745.8e6, src="b776c25d0ef34a00"),
+    ("k_update", "fp64", "basin_baroclinic"): dict(bytes=1399.8e6, src="b776c25d0ef34a00"),
 }
 KSRC = ["paper_2605_16082_gb300/csrc/slim_split.cu", "paper_2605_16082_gb300/csrc/slim_split_device.cuh",
         "paper_2605_16082_gb300/csrc/slim_device.cuh", "paper_2605_16082_gb300/csrc/slim_tracer.cu",

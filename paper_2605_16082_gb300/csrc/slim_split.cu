@@ -854,6 +854,24 @@ __global__ void __launch_bounds__(256) k_ext2d_run(DevMesh m, SplitBufs bf, Mx2d
   }
 }
 
+// Start of a split stage's external run in one pass over the 2D nodes: the FP64
+// working copies of the state (eta, Qx, Qy), their FP32 shadows (mixed form; null
+// in FP64) and the zeroed time-averaged transport.
+__global__ void __launch_bounds__(256)
+    k_ext2d_begin(const double* __restrict__ e, const double* __restrict__ U, const double* __restrict__ V,
+                  double* __restrict__ Ae, double* __restrict__ AU, double* __restrict__ AV,
+                  float* __restrict__ Aer, float* __restrict__ AUr, float* __restrict__ AVr,
+                  double* __restrict__ Qbx, double* __restrict__ Qby, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double ei = e[i], ui = U[i], vi = V[i];
+    Ae[i] = ei; AU[i] = ui; AV[i] = vi;
+    if (Aer) {
+      Aer[i] = (float)ei; AUr[i] = (float)ui; AVr[i] = (float)vi;
+    }
+    Qbx[i] = 0.0; Qby[i] = 0.0;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // coupling after the external run (FP64, thread per triangle):
 //   F2D = (Q1 - (Q0 + T S3/w))/T, Dq = Qbar - sum q, st_end = 1 + eta1/h,
@@ -1326,18 +1344,17 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, int tide_base,
     SLIM_CU(launch_mompred<R>(m, TP, occ, pin, Rx, Ry, pp, b, stm));
   }
   b->has_s3 = true;
-  // external mode from the state at t0
-  SLIM_CU(cudaMemcpyAsync(b->Ae, s->eta, n2 * 8, cudaMemcpyDeviceToDevice, stm));
-  SLIM_CU(cudaMemcpyAsync(b->AU, s->Qx, n2 * 8, cudaMemcpyDeviceToDevice, stm));
-  SLIM_CU(cudaMemcpyAsync(b->AV, s->Qy, n2 * 8, cudaMemcpyDeviceToDevice, stm));
+  // external mode from the state at t0: working copies, FP32 shadows, zero averages
   const bool shadow = sizeof(R) != 8;
-  if (shadow) {
-    SLIM_CU(launch_convert_d2f(b->Ae, (float*)b->Ae_r, n2, stm));
-    SLIM_CU(launch_convert_d2f(b->AU, (float*)b->AU_r, n2, stm));
-    SLIM_CU(launch_convert_d2f(b->AV, (float*)b->AV_r, n2, stm));
+  {
+    ProfScope ps(s, SLIM_PHASE_MISC, stm);
+    const int blocks = (int)std::min<size_t>((n2 + 255) / 256, 4096);
+    k_ext2d_begin<<<blocks, 256, 0, stm>>>(s->eta, s->Qx, s->Qy, b->Ae, b->AU, b->AV,
+                                           shadow ? (float*)b->Ae_r : nullptr,
+                                           shadow ? (float*)b->AU_r : nullptr,
+                                           shadow ? (float*)b->AV_r : nullptr, s->Qbx, s->Qby, n2);
+    SLIM_CU(cudaGetLastError());
   }
-  SLIM_CU(cudaMemsetAsync(s->Qbx, 0, n2 * 8, stm));
-  SLIM_CU(cudaMemsetAsync(s->Qby, 0, n2 * 8, stm));
   SLIM_CU(cudaMemsetAsync(b->Gb, 0, n2 * 2 * 8, stm));
   const double dts = dt / n_sub;
   const double A_[3] = {0.0, 0.75, 1.0 / 3.0}, B_[3] = {1.0, 0.25, 2.0 / 3.0};
@@ -1685,12 +1702,12 @@ slim_status split_step(slim_state* s, double t, double dt, cudaStream_t st) {
 }
 
 int split_kernel_count(const slim_state* s) {
-  // time kernel; per stage: hpg, mompred, 3 n_sub_stage external stages, couple,
-  // continuity, momentum, tracers; the mixed form's 2D shadow conversions (3 per stage)
-  // (the persistent mixed run is one launch per stage)
+  // time kernel; per stage: hpg, mompred, the start of the external run, 3 n_sub_stage
+  // external stages, couple, continuity, momentum, tracers (the persistent mixed run
+  // is one launch per stage)
   const int n = s->par.n_sub;
   const int ext = (s->prec == SLIM_MIXED && s->par.persistent_2d) ? 2 : 3 * (n / 2 + n);
-  return 1 + 2 * 6 + ext + (s->prec == SLIM_MIXED ? 6 : 0);
+  return 1 + 2 * 7 + ext;
 }
 
 }  // namespace slim
