@@ -249,6 +249,7 @@ def run_ours(args, rank: int, world: int):
             tn = autotune.autotune(m, prec, par, fields, dt, use_cache=False)
             par.tile_prisms = tn["tile_prisms"]
             par.blocks_per_sm = tn["blocks_per_sm"]
+            par.persistent_2d = tn.get("persistent_2d", par.persistent_2d)
             tuned[pname] = tn
         else:
             if args.tile:
@@ -298,7 +299,8 @@ def run_ours(args, rank: int, world: int):
         rk2d = 3 * (par.n_sub // 2 + par.n_sub) * args.steps if W["scheme"] == "split" else 0
         r = dict(value=world * dofs / (ms_step / 1e3), ms_per_step=ms_step, phases=phases,
                  gpu_launches=n_k * args.steps, rk2d_stages=rk2d,
-                 tile_prisms=par.tile_prisms, blocks_per_sm=par.blocks_per_sm, device_bytes=dev_bytes,
+                 tile_prisms=par.tile_prisms, blocks_per_sm=par.blocks_per_sm,
+                 persistent_2d=int(par.persistent_2d), device_bytes=dev_bytes,
                  autotune=tuned.get(pname, {}).get("all"))
         # end to end through the public API with pinned host buffers
         if not args.no_e2e:
@@ -406,6 +408,7 @@ def layer_sweep(args) -> dict:
         dt = 20 * wl.fields.dt_2d(m)
         tn = autotune.autotune(m, slim.SLIM_MIXED, par, fields, dt, use_cache=False)
         par.tile_prisms, par.blocks_per_sm = tn["tile_prisms"], tn["blocks_per_sm"]
+        par.persistent_2d = tn.get("persistent_2d", par.persistent_2d)
         with slim.Model(m, slim.SLIM_MIXED, par) as mod:
             for k, v in fields.items():
                 mod.upload(k, v)
@@ -424,7 +427,8 @@ def layer_sweep(args) -> dict:
         P = int(m.n_layers.sum())
         rows.append(dict(layers=N, prisms=P, ms_per_step=ms, ns_per_prism_step=ms * 1e6 / P,
                          dof_updates_per_s=6.0 * P * 4 / (ms / 1e3),
-                         prisms_per_block=tn["tile_prisms"], blocks_per_sm=tn["blocks_per_sm"]))
+                         prisms_per_block=tn["tile_prisms"], blocks_per_sm=tn["blocks_per_sm"],
+                         persistent_2d=int(par.persistent_2d)))
     return dict(layer_sweep=rows, n_tri=base.n_tri, precision="mixed", scheme="split", n_sub=20,
                 steps=args.steps)
 
@@ -556,7 +560,8 @@ def main():
                 gpu_launches=head["gpu_launches"], phases_ms={k: v[0] for k, v in head["phases"].items()},
                 device_bytes=head["device_bytes"],
                 tiling=dict(prisms_per_block=head["tile_prisms"], blocks_per_sm=head["blocks_per_sm"],
-                            autotune_ms=head["autotune"]), cuda_graph=True)
+                            persistent_2d=head["persistent_2d"], autotune_ms=head["autotune"]),
+                cuda_graph=True)
     if "e2e" in head:
         line["e2e"] = head["e2e"]
     if "fp64" in res and hname != "fp64":

@@ -1,7 +1,8 @@
 """Autotuner of the launch tiling: prisms per thread block (the tile of whole
 columns each block owns: 128, 256 or 512) and the register budget of the heavy
 split-step kernels (2, 3 or 4 resident blocks of 256 threads per SM in the mixed
-form; the FP64 form has one budget).
+form; the FP64 form has one budget), and, in the mixed split scheme, whether the 2D
+run is one cooperative launch per split stage or one launch per RK stage.
 
 Every candidate is a separate mesh tiling and state; each runs a few warm-up
 steps and is timed over a few steps with CUDA events on the current stream.  The
@@ -54,12 +55,14 @@ def _store(d):
 
 
 def time_config(mesh, precision: int, params, fields: dict, dt: float, tile: int, occ: int,
-                warmup: int = 2, steps: int = 3) -> float:
+                warmup: int = 2, steps: int = 3, persistent: int | None = None) -> float:
     """Milliseconds per step of one configuration."""
     import torch
     p = slim.SlimParams.from_buffer_copy(params)
     p.tile_prisms = tile
     p.blocks_per_sm = occ
+    if persistent is not None:
+        p.persistent_2d = persistent
     stream = torch.cuda.current_stream()
     with slim.Model(mesh, precision, p, tile_prisms=tile) as mod:
         for k, v in fields.items():
@@ -104,7 +107,18 @@ def autotune(mesh, precision: int, params, fields: dict, dt: float, use_cache: b
                 print(f"autotune tile={tile} blocks_per_sm={occ}: {ms:.3f} ms/step", flush=True)
     best = min(results, key=results.get)
     tile, occ = (int(x) for x in best.split("/"))
-    out = dict(tile_prisms=tile, blocks_per_sm=occ, ms_per_step=results[best], all=results)
+    out = dict(tile_prisms=tile, blocks_per_sm=occ, ms_per_step=results[best], all=results,
+               persistent_2d=int(params.persistent_2d))
+    if params.scheme == slim.SLIM_SCHEME_SPLIT and precision == slim.SLIM_MIXED:
+        # the mixed 2D run as one cooperative launch per split stage or one launch per
+        # RK stage: the grid barrier pays on large meshes, the launches on small ones
+        other = 0 if params.persistent_2d else 1
+        ms = time_config(mesh, precision, params, fields, dt, tile, occ, persistent=other)
+        results[f"{tile}/{occ}/persistent{other}"] = ms
+        if verbose:
+            print(f"autotune tile={tile} blocks_per_sm={occ} persistent_2d={other}: {ms:.3f} ms/step", flush=True)
+        if ms < out["ms_per_step"]:
+            out.update(persistent_2d=other, ms_per_step=ms)
     cache[key] = out
     if use_cache:
         _store(cache)

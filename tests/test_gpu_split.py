@@ -246,9 +246,12 @@ def test_autotune_returns_a_measured_configuration(slim):
     p = params(slim)
     res = autotune.autotune(m, slim.SLIM_MIXED, p, ini, 20.0, use_cache=False)
     assert res["tile_prisms"] in autotune.TILES and res["blocks_per_sm"] in autotune.OCCS
-    # every (tile, budget) pair except the 3-block budget of 512-prism tiles
-    assert len(res["all"]) == len(autotune.TILES) * len(autotune.OCCS) - 1
+    # every (tile, budget) pair except the 3-block budget of 512-prism tiles, and the
+    # best of them with the other 2D launch form
+    assert len(res["all"]) == len(autotune.TILES) * len(autotune.OCCS)
     assert "512/3" not in res["all"]
+    assert sum(k.endswith("persistent0") for k in res["all"]) == 1
+    assert res["persistent_2d"] in (0, 1)
     assert res["ms_per_step"] == min(res["all"].values()) > 0
 
 
