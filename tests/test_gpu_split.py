@@ -167,6 +167,33 @@ def test_split_step_parity_fp64(slim, case):
             assert rel_l2(mod.download("F2D_Y"), d2["F2D"][1]) < TOL64, (n, "F2D")
 
 
+def test_split_long_run_parity_fp64(slim):
+    """100 steps (1.3 h, 1 m tide of period 1 h: currents up to 0.4 m/s, upwind
+    directions switching) from the stratified rest state of a small basin
+    (550 triangles x 3 layers, n_sub = 20, the workload's step 20 dt_2d): the FP64
+    path follows the oracle step after step.  Rounding accumulates over the steps,
+    so the bar is 1e-10 instead of the per-step 1e-12."""
+    from oracle import baroclinic as bc
+    from oracle.mesh import OMesh
+    m = wl.c2_mesh(300, 3, 0)
+    c2 = wl.c2_initial_state(m)
+    ini = dict(U=c2["u"], V=c2["v"], T=c2["T"], S=c2["S"], ETA=c2["eta"], QX=c2["U"], QY=c2["V"])
+    p = params(slim, n_sub=20, kappa_v=1e-3, nu_v=1e-3, kappa_h=1.0, nu_h=1.0, tide_amp=1.0)
+    om = OMesh(m)
+    st = oracle_state(m, om, ini)
+    par = oracle_params(p)
+    dt = 20.0 * wl.fields.dt_2d(m)
+    with model(slim, m, slim.SLIM_FP64, p, ini) as mod:
+        for n in range(100):
+            st = bc.split_step(om, par, st, n * dt, dt)
+            slim.slim_step(mod.state, n * dt, dt)
+            if n + 1 in (50, 100):
+                slim.slim_state_check(mod.state)
+                for f, o in FIELDS3 + FIELDS2:
+                    assert rel_l2(mod.download(f), getattr(st, o)) < 1e-10, (n + 1, f)
+        assert np.abs(st.u).max() > 0.2
+
+
 def test_split_step_parity_tiles(slim):
     """Same step with every tile size gives the oracle's result."""
     from oracle import baroclinic as bc
