@@ -274,20 +274,23 @@ slim_status slim_step(slim_state* s, double t, double dt, void* stream);
  * order (deterministic).  Writes one double to *mass_host; synchronises. */
 slim_status slim_tracer_mass(slim_state* s, int field, double* mass_host, void* stream);
 
-/* slim_tracer_mass_noalloc: the same sum as slim_tracer_mass (same order, same
- * result), for callers that must not allocate device memory during the call: a
- * pool or caching allocator that forbids direct cudaMalloc/cudaFree, code that
- * must not block or synchronize the host, or a fixed device-memory budget.  The
- * paper has no counterpart; this is a library convenience.
+/* slim_tracer_mass_noalloc: the same sum as slim_tracer_mass (the same two
+ * reduction kernels, so the same bits), for callers that must not allocate device
+ * memory during the call: a pool or caching allocator that forbids direct
+ * cudaMalloc/cudaFree, code that must not block or synchronize the host, or a
+ * fixed device-memory budget.  The paper has no counterpart; this is a library
+ * convenience.
  *   mass_dev: caller-owned device address of one double, written when the
- *             stream reaches the call (nothing is copied to the host; the call
- *             does not wait for the GPU).
+ *             stream reaches the call (nothing is copied to the host; after the
+ *             first call on a device the call does not wait for the GPU).
  * Scratch: the block partials live in a fixed 1 MiB device array inside the
  * library (2 doubles per thread-block tile, at most 65536 tiles), held by every
  * GPU that loads the library until the process exits; a mesh with more tiles is
  * rejected with SLIM_ERR_ARG.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress) with the device current; make that first
- * call before any stream capture.  The array is shared by all calls and keeps
+ * device address (cudaGetSymbolAddress) with the device current, and the first
+ * call per device, precision and tile size may load the kernels' module (lazy
+ * loading): such a call can block the host while that happens.  Make that first
+ * call before any stream capture and outside code that must not block.  The array is shared by all calls and keeps
  * the last call's partials: calls whose work overlaps on the GPU (other streams,
  * other states, other threads) race on it.  No cudaMalloc, cudaFree or
  * allocating library routine is called.  field: SLIM_FIELD_T or _S. */

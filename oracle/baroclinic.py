@@ -641,7 +641,7 @@ def split_stage(om: OMesh, par: Params, st0: State, ev: State, t0: float, dt: fl
     corr = face_correction(om, dz_ev, Qbx, Qby, Gb, Q_ext=Q_mid)
     dz1 = om.thickness(eta1)
     R1 = tr.horizontal_residual(om, qbx, qby, np.ones_like(qbx), face_corr=corr, q_ext=qe)
-    F = R1 - ((om.Jh[om.t_of] / 12.0)[None] * (dz1 - dz0) / dt)[None]
+    F = R1 - ((om.Jh[om.t_of] / 12.0)[None] * om.thickness_change(st0.eta, eta1) / dt)[None]
     W = tr.solve_continuity(om, F)
     # 6. momentum: M1 u1 = M0 u0 + dt (F_3D^h(u_ev, qbar, r) + M1 F2D/H1 + [A u1 | A u_ev])
     Fx, Fy = momentum_horizontal(om, par, ev.u, ev.v, qbx, qby, rx, ry, dz_ev, face_corr=corr, ext=ext3)

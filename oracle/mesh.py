@@ -111,6 +111,15 @@ class OMesh:
         zt, zb = self.interfaces(eta)
         return zt - zb
 
+    def thickness_change(self, eta0: np.ndarray, eta1: np.ndarray) -> np.ndarray:
+        """dz(eta1) - dz(eta0) (3, P), written as dz_rest (eta1 - eta0)/h: the
+        interfaces stretch linearly with eta, so this is the same quantity without
+        the cancellation of subtracting two thicknesses (whose rounding, relative to
+        the small change, is eps h / |eta1 - eta0|)."""
+        zt0, zb0 = self.rest_interfaces()
+        h = self.h[self.t_of].T
+        return (zt0 - zb0) * (eta1 - eta0)[:, self.t_of] / h
+
     def nbr_prism(self, e: int) -> tuple[np.ndarray, np.ndarray]:
         """For edge e of every prism: the lateral neighbour prism (or -1) and a mask."""
         t, k = self.t_of, self.k_of

@@ -328,9 +328,8 @@ def continuity(om: OMesh, eta_n: np.ndarray, u: np.ndarray, v: np.ndarray, dt: f
     R1 = horizontal_residual(om, qx, qy, np.ones_like(u))
     D = column_sum(om, R1)
     eta_np1 = eta_n + dt * D / vertex_weight(om)
-    dz_np1 = om.thickness(eta_np1)
     w12 = (om.Jh[om.t_of] / 12.0)[None]
-    F = R1 - (w12 * (dz_np1 - dz_n) / dt)[None]
+    F = R1 - (w12 * om.thickness_change(eta_n, eta_np1) / dt)[None]
     W = solve_continuity(om, F)
     return eta_np1, W, (qx, qy)
 

@@ -96,3 +96,50 @@ def restrict2(f: np.ndarray, m: Mesh, tmap: np.ndarray) -> np.ndarray:
 def prisms_of(n_layers: np.ndarray, tris: np.ndarray) -> np.ndarray:
     off = col_offsets(n_layers)
     return np.concatenate([np.arange(off[t], off[t + 1]) for t in tris])
+
+
+def assert_close(got, ref, tol: float, what=None) -> None:
+    """Parity bar: relative L2 over the field AND every node within tol of the
+    field's largest magnitude (a single wrong node -- a wall face, a ragged last
+    tile, the last layer of a short column -- fails the second even when the norm
+    hides it)."""
+    g = np.asarray(got, np.float64).ravel()
+    r = np.asarray(ref, np.float64).ravel()
+    assert g.shape == r.shape, (what, g.shape, r.shape)
+    e2 = rel_l2(g, r)
+    d = np.abs(g - r)
+    scale = float(np.abs(r).max()) or 1.0
+    emax = float(d.max()) / scale if d.size else 0.0
+    assert e2 < tol and emax <= tol, dict(what=what, rel_l2=e2, max_rel=emax, at=int(np.argmax(d)) if d.size else -1,
+                                          tol=tol)
+
+
+def split_case_mesh(name):
+    """Meshes of the split-scheme parity cases: a graded basin with an open tidal
+    boundary, a square basin with an open side, a z-level basin with uneven columns."""
+    if name == "basin":
+        return wl.c2_mesh(2500, 5, 0)
+    if name == "square":
+        return wl.meshes.square_mesh(10, 4000.0, 4, lambda x, y: 15.0 + 20.0 * x / 4000.0,
+                                     lambda x, y: x > 4000.0 - 1e-6)
+    if name == "zlevel":
+        return wl.c4_mesh(3000, 0, n_max=12, h_max=60.0)
+    raise KeyError(name)
+
+
+def split_initial(m, seed=0):
+    """Seeded smooth state of the split-scheme parity cases (velocity with depth
+    shear, T and S varying in x, y and z, sloped elevation and transport)."""
+    rng = np.random.default_rng(seed)
+    x, y, z, s = wl.fields.node_positions_sigma(m)
+    Lx = max(m.xy[:, 0].max(), 1.0)
+    Ly = max(m.xy[:, 1].max(), 1.0)
+    u = 0.2 * np.sin(np.pi * x / Lx) * np.cos(np.pi * y / Ly) * (1.2 - s)
+    v = 0.1 * np.cos(np.pi * x / Lx) * (0.4 + s)
+    T = 15.0 + 10.0 * np.exp(z / 40.0) + 0.5 * np.sin(3 * x / Lx)
+    S = 34.0 - 2.0 * z / 60.0 + 0.3 * np.cos(2 * y / Ly)
+    xt, yt = m.xy[m.tri][:, :, 0].T, m.xy[m.tri][:, :, 1].T
+    eta = 0.05 * np.cos(np.pi * xt / Lx) + 0.02 * np.sin(2 * np.pi * yt / Ly)
+    U = 1.0 * np.sin(np.pi * xt / Lx)
+    V = 0.3 * np.cos(np.pi * yt / Ly) * np.sin(np.pi * xt / Lx)
+    return dict(U=u.ravel(), V=v.ravel(), T=T.ravel(), S=S.ravel(), ETA=eta.ravel(), QX=U.ravel(), QY=V.ravel())

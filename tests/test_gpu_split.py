@@ -1,8 +1,9 @@
 """GPU parity of the baroclinic split-IMEX path (C ABI) against the FP64 oracle.
 
-FP64 bar: relative L2 <= 1e-12 per field per step (3D u, v, T, S; 2D eta, U, V;
-the stage-2 intermediates Qbar, S3 and F2D; 1e-11 for the pressure gradient r
-and the vertical flux W, see TOL_R).  Cases: a graded basin with an
+FP64 bar: relative L2 <= 1e-12 per field per step, and every node within 1e-12
+of the field's largest magnitude (3D u, v, T, S; 2D eta, U, V; the stage-2
+intermediates Qbar, S3, F2D and the vertical flux W; 1e-11 for the pressure
+gradient r, see TOL_R).  Cases: a graded basin with an
 open tidal boundary (several tiles, ragged last tile), a square basin, and a
 z-level basin with uneven columns (1..N layers, walls against shallower
 neighbours)."""
@@ -12,17 +13,16 @@ import numpy as np
 import pytest
 
 import workloads as wl
-from helpers import prisms_of, rel_l2, restrict2, restrict3, ring_submesh
+from helpers import (assert_close, prisms_of, rel_l2, restrict2, restrict3, ring_submesh,
+                     split_case_mesh as case_mesh, split_initial as initial)
 
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
-# Two intermediates are small differences of much larger terms: the pressure
-# gradient r (terms of size g rho' H: coordinate-surface slopes times the full
-# density anomaly) and the vertical flux W (partial column sums of the horizontal
-# divergence and the mass change, which cancel over the column).  Their FP64
-# rounding floor relative to their own norm is about 1e-12, so they are compared
-# at 1e-11.  Every prognostic field is held to 1e-12.
+# The pressure gradient r is a gradient along sloping coordinate surfaces: nodal
+# depths of O(100 m) enter through their differences across a triangle.  One
+# rounding of its inputs moves r by 1.8e-12 of its norm on the graded basin
+# (test_oracle_rounding.py), so r is compared at 1e-11; every other field at 1e-12.
 TOL_R = 1e-11
 
 
@@ -34,33 +34,6 @@ def slim():
     from paper_2605_16082_gb300 import slim as s
     torch.cuda.init()
     return s
-
-
-def case_mesh(name):
-    if name == "basin":
-        return wl.c2_mesh(2500, 5, 0)
-    if name == "square":
-        return wl.meshes.square_mesh(10, 4000.0, 4, lambda x, y: 15.0 + 20.0 * x / 4000.0,
-                                     lambda x, y: x > 4000.0 - 1e-6)
-    if name == "zlevel":
-        return wl.c4_mesh(3000, 0, n_max=12, h_max=60.0)
-    raise KeyError(name)
-
-
-def initial(m, seed=0):
-    rng = np.random.default_rng(seed)
-    x, y, z, s = wl.fields.node_positions_sigma(m)
-    Lx = max(m.xy[:, 0].max(), 1.0)
-    Ly = max(m.xy[:, 1].max(), 1.0)
-    u = 0.2 * np.sin(np.pi * x / Lx) * np.cos(np.pi * y / Ly) * (1.2 - s)
-    v = 0.1 * np.cos(np.pi * x / Lx) * (0.4 + s)
-    T = 15.0 + 10.0 * np.exp(z / 40.0) + 0.5 * np.sin(3 * x / Lx)
-    S = 34.0 - 2.0 * z / 60.0 + 0.3 * np.cos(2 * y / Ly)
-    xt, yt = m.xy[m.tri][:, :, 0].T, m.xy[m.tri][:, :, 1].T
-    eta = 0.05 * np.cos(np.pi * xt / Lx) + 0.02 * np.sin(2 * np.pi * yt / Ly)
-    U = 1.0 * np.sin(np.pi * xt / Lx)
-    V = 0.3 * np.cos(np.pi * yt / Ly) * np.sin(np.pi * xt / Lx)
-    return dict(U=u.ravel(), V=v.ravel(), T=T.ravel(), S=S.ravel(), ETA=eta.ravel(), QX=U.ravel(), QY=V.ravel())
 
 
 def params(slim, **kw):
@@ -112,8 +85,8 @@ def test_hpg_parity(slim, case):
         slim.slim_hpg(mod.state)
         rx, ry = mod.download("R_X"), mod.download("R_Y")
     ox, oy = bc.hpg(om, oracle_params(p), st.T, st.S, st.eta)
-    assert rel_l2(rx, ox) < TOL_R
-    assert rel_l2(ry, oy) < TOL_R
+    assert_close(rx, ox, TOL_R)
+    assert_close(ry, oy, TOL_R)
 
 
 @pytest.mark.parametrize("case", ["basin", "square"])
@@ -132,9 +105,9 @@ def test_rhs2d_parity(slim, case):
         torch.cuda.synchronize()
         got = out.cpu().numpy().reshape(3, 3, m.n_tri)
     Re, RU, RV, _ = bc.mode2d_residual(om, oracle_params(p), st.eta, st.U, st.V, 1234.5)
-    assert rel_l2(got[0], Re) < TOL64
-    assert rel_l2(got[1], RU) < TOL64
-    assert rel_l2(got[2], RV) < TOL64
+    assert_close(got[0], Re, TOL64)
+    assert_close(got[1], RU, TOL64)
+    assert_close(got[2], RV, TOL64)
 
 
 FIELDS3 = [("U", "u"), ("V", "v"), ("T", "T"), ("S", "S")]
@@ -159,12 +132,12 @@ def test_split_step_parity_fp64(slim, case):
             slim.slim_step(mod.state, n * dt, dt)
             slim.slim_state_check(mod.state)
             for f, o in FIELDS3 + FIELDS2:
-                assert rel_l2(mod.download(f), getattr(st, o)) < TOL64, (n, f)
-            assert rel_l2(mod.download("R_X"), d2["r"][0]) < TOL_R, (n, "r")
-            assert rel_l2(mod.download("W"), d2["W"]) < TOL_R, (n, "W")
-            assert rel_l2(mod.download("QBAR_X"), d2["Qbar"][0]) < TOL64, (n, "Qbar")
-            assert rel_l2(mod.download("S3_X"), d2["S3"][0]) < TOL64, (n, "S3")
-            assert rel_l2(mod.download("F2D_Y"), d2["F2D"][1]) < TOL64, (n, "F2D")
+                assert_close(mod.download(f), getattr(st, o), TOL64, (n, f))
+            assert_close(mod.download("R_X"), d2["r"][0], TOL_R, (n, "r"))
+            assert_close(mod.download("W"), d2["W"], TOL64, (n, "W"))
+            assert_close(mod.download("QBAR_X"), d2["Qbar"][0], TOL64, (n, "Qbar"))
+            assert_close(mod.download("S3_X"), d2["S3"][0], TOL64, (n, "S3"))
+            assert_close(mod.download("F2D_Y"), d2["F2D"][1], TOL64, (n, "F2D"))
 
 
 def test_split_long_run_parity_fp64(slim):
@@ -190,7 +163,7 @@ def test_split_long_run_parity_fp64(slim):
             if n + 1 in (50, 100):
                 slim.slim_state_check(mod.state)
                 for f, o in FIELDS3 + FIELDS2:
-                    assert rel_l2(mod.download(f), getattr(st, o)) < 1e-10, (n + 1, f)
+                    assert_close(mod.download(f), getattr(st, o), 1e-10, (n + 1, f))
         assert np.abs(st.u).max() > 0.2
 
 
@@ -207,7 +180,7 @@ def test_split_step_parity_tiles(slim):
         with model(slim, m, slim.SLIM_FP64, p, ini, tile=tile) as mod:
             slim.slim_step(mod.state, 0.0, 30.0)
             for f, o in FIELDS3 + FIELDS2:
-                assert rel_l2(mod.download(f), getattr(st, o)) < TOL64, (tile, f)
+                assert_close(mod.download(f), getattr(st, o), TOL64, (tile, f))
 
 
 def test_split_lake_at_rest_gpu(slim):
@@ -359,7 +332,7 @@ def test_split_full_size_in_the_bench_configuration(slim, basin_full):
         got.append(np.concatenate([restrict3(rx, m, np.array([sd])).ravel(),
                                    restrict3(ry, m, np.array([sd])).ravel()]))
         ref.append(np.concatenate([ox[:, :, pr].ravel(), oy[:, :, pr].ravel()]))
-    assert rel_l2(np.concatenate(got), np.concatenate(ref)) < TOL_R
+    assert_close(np.concatenate(got), np.concatenate(ref), TOL_R)
 
 
 @pytest.mark.parametrize("mesh", ["basin", "wide"])
@@ -438,9 +411,9 @@ def test_split_forcing_parity_fp64(slim, case):
             slim.slim_step(mod.state, n * dt, dt)
             slim.slim_state_check(mod.state)
             for f, o in FIELDS3 + FIELDS2:
-                assert rel_l2(mod.download(f), getattr(st, o)) < TOL64, (n, f)
-            assert rel_l2(mod.download("W"), d2["W"]) < TOL_R, (n, "W")
-            assert rel_l2(mod.download("QBAR_X"), d2["Qbar"][0]) < TOL64, (n, "Qbar")
+                assert_close(mod.download(f), getattr(st, o), TOL64, (n, f))
+            assert_close(mod.download("W"), d2["W"], TOL64, (n, "W"))
+            assert_close(mod.download("QBAR_X"), d2["Qbar"][0], TOL64, (n, "Qbar"))
     # the forcing changed the result (the exterior state enters)
     st0 = bc.split_step(om, oracle_params(params(slim)), oracle_state(m, om, ini), 0.0, dt)
     assert rel_l2(st0.u, bc.split_step(om, par, _forced_oracle_state(m, om, ini, fx, p), 0.0, dt).u) > 1e-6
@@ -550,4 +523,4 @@ def test_split_reef_full_size(slim, reef_full):
         pr = prisms_of(sub.n_layers, pos)
         got.append(restrict3(rx, m, np.array([sd])).ravel())
         ref.append(ox[:, :, pr].ravel())
-    assert rel_l2(np.concatenate(got), np.concatenate(ref)) < TOL_R
+    assert_close(np.concatenate(got), np.concatenate(ref), TOL_R)

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import workloads as wl
-from helpers import (rel_l2, sheared_velocity, random_uneven_mesh, ring_submesh, restrict3,
+from helpers import (assert_close, rel_l2, sheared_velocity, random_uneven_mesh, ring_submesh, restrict3,
                      restrict2, prisms_of)
 
 pytestmark = pytest.mark.gpu
@@ -74,7 +74,7 @@ def test_rhs3d_parity(slim, case, tile):
     dz = om.thickness(eta.reshape(3, -1))
     qx, qy = otr.transport(dz, otr.to3(u, om.P), otr.to3(v, om.P))
     ref = otr.horizontal_residual(om, qx, qy, otr.to3(T, om.P))
-    assert rel_l2(got, ref) < TOL64
+    assert_close(got, ref, TOL64)
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -89,8 +89,8 @@ def test_continuity_parity(slim, case):
         W = mod.download("W")
         e1 = mod.download("ETA_NEXT")
     eo, Wo, _ = otr.continuity(om, np.zeros((3, m.n_tri)), otr.to3(u, om.P), otr.to3(v, om.P), 20.0)
-    assert rel_l2(W, Wo) < TOL64
-    assert rel_l2(e1, eo) < TOL64
+    assert_close(W, Wo, TOL64)
+    assert_close(e1, eo, TOL64)
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -118,7 +118,7 @@ def test_vertical_solve_parity(slim, case):
         got_inplace = r.cpu().numpy()
     ref = otr.stage_solve(om, otr.to3(W, om.P), om.thickness(np.zeros((3, m.n_tri))),
                           otr.to3(rhs, om.P), bdt, kappa, 1e-4, -2e-4)
-    assert rel_l2(got, ref) < TOL64
+    assert_close(got, ref, TOL64)
     assert np.array_equal(got, got_inplace)
 
 
@@ -137,8 +137,8 @@ def test_step_parity_fp64(slim, case):
             slim.slim_step(mod.state, n * dt, dt)
             slim.slim_state_check(mod.state)
             eo, To, _ = otr.tracer_step(om, eo, To, uo, vo, dt, kappa)
-            assert rel_l2(mod.download("T"), To) < TOL64, n
-            assert rel_l2(mod.download("ETA"), eo) < TOL64, n
+            assert_close(mod.download("T"), To, TOL64, n)
+            assert_close(mod.download("ETA"), eo, TOL64, n)
 
 
 def test_square_basin_workload_parity(slim):
@@ -155,9 +155,9 @@ def test_square_basin_workload_parity(slim):
             slim.slim_step(mod.state, n * W["dt"], W["dt"])
             eo, To, _ = otr.tracer_step(om, eo, To, otr.to3(u, om.P), otr.to3(v, om.P), W["dt"], W["kappa_v"])
             got = mod.download("T")
-            assert rel_l2(got, To) < TOL64
+            assert_close(got, To, TOL64)
             assert np.abs(got - To.ravel()).max() < 1e-12
-            assert rel_l2(mod.download("ETA"), eo) < TOL64
+            assert_close(mod.download("ETA"), eo, TOL64)
 
 
 def test_open_boundary_inflow_uses_exterior_profile(slim):
@@ -182,7 +182,7 @@ def test_open_boundary_inflow_uses_exterior_profile(slim):
     ref = otr.horizontal_residual(om, qx, qy, otr.to3(T, om.P), otr.to3(Text, om.P))
     ref_same = otr.horizontal_residual(om, qx, qy, otr.to3(T, om.P), otr.to3(T, om.P))
     assert rel_l2(ref, ref_same) > 1e-6           # the exterior state matters
-    assert rel_l2(got, ref) < TOL64
+    assert_close(got, ref, TOL64)
 
 
 def test_mass_conservation_and_parity(slim):
@@ -274,8 +274,8 @@ def test_sampled_parity_at_basin_size(slim):
         gT.append(restrict3(T1, m, np.array([sd])).ravel()); rT.append(To[:, :, pr].ravel())
         ge.append(restrict2(e1, m, np.array([sd])).ravel()); re.append(eo[:, pos].ravel())
     # the per-field bar over the sampled outputs
-    assert rel_l2(np.concatenate(gT), np.concatenate(rT)) < TOL64
-    assert rel_l2(np.concatenate(ge), np.concatenate(re)) < TOL64
+    assert_close(np.concatenate(gT), np.concatenate(rT), TOL64)
+    assert_close(np.concatenate(ge), np.concatenate(re), TOL64)
 
 
 def test_tracer_graph_replay_matches_launches(slim):
