@@ -451,63 +451,129 @@ def allmax(x: float, world: int) -> float:
 
 
 # ---------------------------------------------------------------------------
-def oracle_sample(args, m, seconds: float):
-    """The oracle as it stands on a bounded sample of the workload: a compact patch
-    of consecutive (Hilbert-ordered) columns, stepped until ``seconds`` elapse."""
-    from oracle import tracer as otr
-    from oracle import baroclinic as obc
-    from oracle.mesh import OMesh
+def host_cpu() -> dict:
+    """Host cores and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return dict(nproc=os.cpu_count() or 1, model=model or "unknown")
+
+
+def _patch(workload: str, m, n_patch: int, first: int):
+    """Sub-mesh of n_patch consecutive (Hilbert-ordered) columns starting at first;
+    cut edges become walls, open-boundary edges stay open."""
     from workloads.meshes import Mesh
-    W = wl.WORKLOADS[args.workload]
-    n_patch = min(m.n_tri, 1200 if W["scheme"] == "tracer" else 400)
-    idx = np.arange(n_patch)
+    idx = np.arange(first, min(first + n_patch, m.n_tri))
     bnd = m.bnd[idx].copy()
     sub = Mesh(xy=m.xy, tri=m.tri[idx], h_tri=m.h_tri[idx], n_layers=m.n_layers[idx], bnd=bnd,
                levels=m.levels)
-    # cut edges become walls; open-boundary edges stay open
     topo = wl.meshes._tag_boundary(sub.xy, sub.tri, None)
     sub.bnd = np.where((topo == 1) & (bnd == 2), 2, topo).astype(np.int8)
+    return sub
+
+
+def _oracle_worker(job):
+    """One oracle process: its own patch of the workload, `warm` untimed steps, then
+    steps until `seconds` elapse (at least `min_steps`).  Returns (prisms, fields,
+    timed steps, timed seconds)."""
+    workload, m, n_patch, first, seconds, warm, min_steps, dt_full = job
+    from oracle import tracer as otr
+    from oracle import baroclinic as obc
+    from oracle.mesh import OMesh
+    W = wl.WORKLOADS[workload]
+    sub = _patch(workload, m, n_patch, first)
     om = OMesh(sub)
     P = om.P
-    steps = 0
-    t0 = time.perf_counter()
     if W["scheme"] == "tracer":
-        if args.workload == "square_tracer":
+        if workload == "square_tracer":
             u, v = wl.c1_velocity(sub); T = wl.c1_tracer(sub)
         else:
             u, v = wl.basin_velocity(sub); T = wl.c2_initial_state(sub)["T"]
-        u, v, T = otr.to3(u, P), otr.to3(v, P), otr.to3(T, P)
-        eta = np.zeros((3, sub.n_tri))
+        state = [np.zeros((3, sub.n_tri)), otr.to3(T, P)]
+        u, v = otr.to3(u, P), otr.to3(v, P)
         nf = 1
-        while True:
-            eta, T, _ = otr.tracer_step(om, eta, T, u, v, W["dt"], W["kappa_v"])
-            steps += 1
-            el = time.perf_counter() - t0
-            if el >= seconds:
-                break
+
+        def step(k):
+            state[0], state[1], _ = otr.tracer_step(om, state[0], state[1], u, v, W["dt"], W["kappa_v"])
     else:
         ini = {"basin_baroclinic": wl.c2_initial_state, "zlevel_baroclinic": wl.c4_initial_state,
-               "reef_baroclinic": wl.c5_initial_state}[args.workload](sub)
+               "reef_baroclinic": wl.c5_initial_state}[workload](sub)
         st = obc.State(u=otr.to3(ini["u"], P), v=otr.to3(ini["v"], P), T=otr.to3(ini["T"], P),
                        S=otr.to3(ini["S"], P), eta=otr.to2(ini["eta"], sub.n_tri),
                        U=otr.to2(ini["U"], sub.n_tri), V=otr.to2(ini["V"], sub.n_tri))
         st.T_ext, st.S_ext = st.T.copy(), st.S.copy()
         par = obc.Params(n_sub=W["n_sub"], kappa_v=W["kappa_v"], nu_v=W["nu_v"],
                          kappa_h=W.get("kappa_h", 0.0), nu_h=W.get("nu_h", 0.0))
-        dt = W["n_sub"] * wl.fields.dt_2d(m)
+        state = [st]
         nf = 4
-        tt = 0.0
-        while True:
-            st = obc.split_step(om, par, st, tt, dt)
-            tt += dt
-            steps += 1
-            el = time.perf_counter() - t0
-            if el >= seconds:
-                break
-    per_step = el / steps
-    return dict(value=6.0 * P * nf / per_step, unit=UNIT, cores=1, kind="oracle",
-                sample=f"{sub.n_tri} columns x {int(sub.n_layers.max())} layers ({P} prisms) of "
-                       f"{args.workload}, {steps} steps in {el:.1f} s, numpy FP64, 1 thread")
+
+        def step(k):
+            state[0] = obc.split_step(om, par, state[0], k * dt_full, dt_full)
+    for k in range(warm):
+        step(k)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        step(warm + n)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and n >= min_steps:
+            break
+    return P, nf, n, el
+
+
+def oracle_run(workload: str, m, seconds: float, cores: int, warm: int = 0, min_steps: int = 1) -> dict:
+    """The oracle as it stands on bounded samples of the workload: `cores` processes
+    (spawned: this process may hold a CUDA context), each stepping its own patch of
+    consecutive columns.  Throughput is the sum over the processes."""
+    import multiprocessing as mp
+    W = wl.WORKLOADS[workload]
+    n_patch = min(m.n_tri, 1200 if W["scheme"] == "tracer" else 400)
+    dt_full = W["n_sub"] * wl.fields.dt_2d(m) if W["scheme"] == "split" else W["dt"]
+    n_avail = max(1, m.n_tri // n_patch)
+    jobs = [(workload, m, n_patch, (j % n_avail) * n_patch, seconds, warm, min_steps, dt_full)
+            for j in range(cores)]
+    if cores == 1:
+        res = [_oracle_worker(jobs[0])]
+    else:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_worker, jobs)
+    value = sum(6.0 * P * nf * n / el for P, nf, n, el in res)
+    steps = [n for _, _, n, _ in res]
+    el = max(e for _, _, _, e in res)
+    P0 = res[0][0]
+    return dict(value=value, unit=UNIT, cores=cores, kind="oracle", steps_per_process=steps,
+                prisms_per_process=P0,
+                seconds=el, ms_per_step=1e3 * sum(e / n for _, _, n, e in res) / len(res),
+                sample=f"{cores} process(es) x {n_patch} columns ({P0} prisms) of {workload}, "
+                       f"{min(steps)}-{max(steps)} timed steps each in {el:.1f} s, numpy FP64, "
+                       f"1 thread per process")
+
+
+def cpu_baseline(workload: str, m, seconds: float) -> dict:
+    """The oracle at every host core (one process per core) and at one core."""
+    cpu = host_cpu()
+    one = oracle_run(workload, m, 0.4 * seconds, 1)
+    allc = oracle_run(workload, m, 0.6 * seconds, cpu["nproc"])
+    out = dict(allc)
+    out.update(cpu_model=cpu["model"], nproc=cpu["nproc"], value_1core=one["value"],
+               sample_1core=one["sample"])
+    return out
 
 
 def main():
@@ -526,11 +592,16 @@ def main():
         if rank != 0:
             return
         m = W["mesh"]()
-        cfg.update(n_tri=m.n_tri, n_prisms=m.n_prisms, layers=int(m.n_layers.max()))
-        cb = oracle_sample(args, m, max(2.0, args.cpu_seconds * args.steps / 20.0))
-        nf = 1 if W["scheme"] == "tracer" else 4
+        cpu = host_cpu()
+        # every process steps its own bounded patch of the workload: W untimed steps,
+        # then at least K timed ones (about --cpu-seconds of CPU work per process)
+        cb = oracle_run(args.workload, m, args.cpu_seconds, cpu["nproc"], warm=args.warmup,
+                        min_steps=args.steps)
+        cb.update(cpu_model=cpu["model"], nproc=cpu["nproc"])
+        cfg.update(n_tri=m.n_tri, n_prisms=m.n_prisms, layers=int(m.n_layers.max()),
+                   sample=cb["sample"], sample_prisms_per_process=cb["prisms_per_process"])
         line = dict(impl="reference", metric=METRIC, value=cb["value"], unit=UNIT, n_gpus=args.gpus,
-                    steps=args.steps, warmup=args.warmup, ms_per_step=6.0 * nf * m.n_prisms / cb["value"] * 1e3,
+                    steps=args.steps, warmup=args.warmup, ms_per_step=cb["ms_per_step"],
                     higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
                     data="synthetic", config=cfg, cpu_baseline=cb,
                     e2e=dict(value=cb["value"], unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
@@ -574,7 +645,7 @@ def main():
     if not args.no_accuracy and "mixed" in res:
         line["mixed_accuracy"] = mixed_accuracy()
     if not args.no_cpu:
-        line["cpu_baseline"] = oracle_sample(args, m, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.workload, m, args.cpu_seconds)
     print(json.dumps(line))
 
 

@@ -147,13 +147,25 @@ typedef struct slim_params {
                           (Sec. 3 forcing data, Sec. 2.5 consistency); 0: zero exterior
                           transport in both (a characteristic condition around the tide
                           elevation) and static exterior tracer profiles. */
+  int vertical;        /* column system of the implicit vertical terms (Sec. 2.4):
+                          0: lumped onto the vertex columns, one 2x2-block tridiagonal
+                             system per vertex column (both schemes);
+                          1: coupled, the consistent-mass system with one 6x6 block per
+                             prism (the paper's fully-assembled column solver): mass,
+                             vertical advection and diffusion keep the consistent M_h,
+                             the continuity solves the printed D_vd with M_h blocks for
+                             the nodal vertical flux (SLIM_FIELD_W then holds Omega) and
+                             the elevation takes the consistent 2D mass.  Tracer scheme
+                             only (SLIM_ERR_UNSUPPORTED with the split scheme); its
+                             shared-memory tile must fit 227 KB (FP64 with 512-prism
+                             tiles does not: SLIM_ERR_UNSUPPORTED). */
 } slim_params;
 
 /* Fill *p with the defaults: g 9.81, rho0 1025, f 1e-4, alpha 2e-4, beta 7.6e-4,
    T0 10, S0 35, kappa_v = nu_v = 1e-3, kappa_h = nu_h = 0, Cd 2.5e-3, no boundary
    fluxes, penalty_v 4, penalty_h 6, tide 1 m / 44712 s, SLIM_SCHEME_TRACER,
    n_sub 20, tile 256, check_every 0, blocks_per_sm 0, use_graph 1, persistent_2d 1,
-   forcing 0 (forcing_t_a 0, forcing_t_b 1).  Returns
+   forcing 0 (forcing_t_a 0, forcing_t_b 1), vertical 0.  Returns
    SLIM_ERR_ARG for a null pointer. */
 slim_status slim_params_default(slim_params* p);
 
@@ -234,6 +246,8 @@ slim_status slim_rhs3d(slim_state* s, int field, void* out_dev, void* stream);
  *     in double (FP64 in both precisions);
  * (ii) the vertical flux of every vertex column from the bottom-up column system
  *     of Eq. 17 (printed D_vd pattern), written to SLIM_FIELD_W.
+ * With slim_params.vertical = 1 the 2D mass is the consistent M_h (M_h (eta' -
+ * eta)/dt = the column sum) and (ii) solves D_vd (x) M_h for the nodal flux Omega.
  * The state's eta is not modified. */
 slim_status slim_continuity(slim_state* s, double dt, void* stream);
 
@@ -249,7 +263,9 @@ slim_status slim_rhs2d(slim_state* s, double t, double* out_dev, void* stream);
  * M the lumped 2x2-per-layer mass at the state's elevation, A the vertical
  * upwind advection by the state's W plus SIPG diffusion (kappa_v for T/S, nu_v
  * for U/V), b the prescribed boundary fluxes (Sec. 2.4 system, 2x2 blocks per
- * layer).  rhs_dev, out_dev: 6P elements of the compute type; they may alias. */
+ * layer).  With slim_params.vertical = 1: one solve per prism column of the
+ * coupled system (consistent mass, 6x6 blocks, W read as the nodal Omega).
+ * rhs_dev, out_dev: 6P elements of the compute type; they may alias. */
 slim_status slim_vertical_solve(slim_state* s, int field, double beta_dt, const void* rhs_dev,
                                 void* out_dev, void* stream);
 
@@ -270,8 +286,10 @@ slim_status slim_hpg(slim_state* s, void* stream);
 slim_status slim_step(slim_state* s, double t, double dt, void* stream);
 
 /* slim_tracer_mass: sum over all nodes of (M T) for field T or S at the state's
- * elevation, accumulated in double with compensated (Neumaier) sums in a fixed
- * order (deterministic).  Writes one double to *mass_host; synchronises. */
+ * elevation (M the lumped mass, or the consistent one with slim_params.vertical =
+ * 1: the quantity each step conserves), accumulated in double with compensated
+ * (Neumaier) sums in a fixed order (deterministic).  Writes one double to
+ * *mass_host; synchronises. */
 slim_status slim_tracer_mass(slim_state* s, int field, double* mass_host, void* stream);
 
 /* slim_tracer_mass_noalloc: the same sum as slim_tracer_mass (the same two
@@ -313,6 +331,16 @@ slim_status slim_selftest_conversions(long long n, unsigned long long seed, long
  * arrivals to host memory; synchronises. */
 slim_status slim_selftest_barrier(int n_blocks, int skip_block, int rounds, int* err_bits,
                                   int* arrivals);
+
+/* slim_selftest_fma_peak: diagnostic (no counterpart in the paper).  Measures the
+ * GPU's fused multiply-add throughput in the precision's compute type (FP64 for
+ * SLIM_FP64, FP32 for SLIM_MIXED): 8 blocks of 256 threads per SM, each thread
+ * running 8 independent FMA chains of `iters` steps, timed with CUDA events on the
+ * legacy default stream after one warm-up launch.  Writes FLOP/s (2 per FMA) and
+ * the timed launch's milliseconds to host memory; synchronises.  The roofline of
+ * an arithmetic-bound kernel takes its denominator from this and from the unit
+ * counts and clocks. */
+slim_status slim_selftest_fma_peak(int precision, long long iters, double* flops_per_s, double* ms);
 
 /* Number of kernels slim_step launches per call (for launch accounting). */
 int slim_step_kernel_count(const slim_state* s);

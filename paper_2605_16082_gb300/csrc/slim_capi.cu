@@ -42,6 +42,7 @@ extern "C" slim_status slim_params_default(slim_params* p) {
   p->forcing_t_a = 0.0;
   p->forcing_t_b = 1.0;
   p->forcing = 0;
+  p->vertical = 0;
   return SLIM_OK;
 }
 
@@ -69,6 +70,11 @@ slim_status check_params(const slim_params* par) {
   if (par->forcing && !(par->forcing_t_b > par->forcing_t_a)) {
     set_error("forcing_t_b must be later than forcing_t_a");
     return SLIM_ERR_ARG;
+  }
+  if (par->vertical != 0 && par->vertical != 1) { set_error("vertical must be 0 or 1"); return SLIM_ERR_ARG; }
+  if (par->vertical == 1 && par->scheme != SLIM_SCHEME_TRACER) {
+    set_error("the coupled column system (vertical = 1) is built for the tracer scheme only");
+    return SLIM_ERR_UNSUPPORTED;
   }
   return SLIM_OK;
 }
@@ -187,24 +193,31 @@ slim_status tracer_step(slim_state* s, double dt, cudaStream_t st) {
   const R* st1 = (const R*)s->st_next;
   {
     ProfScope ps(s, SLIM_PHASE_CONTINUITY, st);
-    SLIM_LAUNCH(launch_continuity<R>(m, TP, U, V, s->eta, st0, s->eta_next, (R*)s->st_next, W, dt, st));
+      if (s->par.vertical)
+      SLIM_LAUNCH(launch_continuity_cpl<R>(m, TP, U, V, s->eta, st0, s->eta_next, (R*)s->st_next, W, dt, st));
+    else
+      SLIM_LAUNCH(launch_continuity<R>(m, TP, U, V, s->eta, st0, s->eta_next, (R*)s->st_next, W, dt, st));
   }
   // Shu-Osher SSP-RK3: (alpha, beta) = (0, 1), (3/4, 1/4), (1/3, 2/3);
   // stage elevations eta^{n+1}, (eta^n + eta^{n+1})/2, eta^{n+1}
+  const bool cpl = s->par.vertical != 0;
+  auto stage = [&](const R* Tp, R* To, double th_p, double th_s, double al, double be) {
+    return cpl ? launch_tracer_stage_cpl<R>(m, TP, U, V, T, Tp, Text, W, To, st0, st1, th_p, th_s, al, be, dt,
+                                            sp, s->err, st)
+               : launch_tracer_stage<R>(m, TP, U, V, T, Tp, Text, W, To, st0, st1, th_p, th_s, al, be, dt, sp,
+                                        s->err, st);
+  };
   {
     ProfScope ps(s, SLIM_PHASE_TRACER_STAGE, st);
-    SLIM_LAUNCH(launch_tracer_stage<R>(m, TP, U, V, T, T, Text, W, T1, st0, st1, 0.0,
-                                       1.0, 0.0, 1.0, dt, sp, s->err, st));
+    SLIM_LAUNCH(stage(T, T1, 0.0, 1.0, 0.0, 1.0));
   }
   {
     ProfScope ps(s, SLIM_PHASE_TRACER_STAGE, st);
-    SLIM_LAUNCH(launch_tracer_stage<R>(m, TP, U, V, T, T1, Text, W, T2, st0, st1, 1.0,
-                                       0.5, 0.75, 0.25, dt, sp, s->err, st));
+    SLIM_LAUNCH(stage(T1, T2, 1.0, 0.5, 0.75, 0.25));
   }
   {
     ProfScope ps(s, SLIM_PHASE_TRACER_STAGE, st);
-    SLIM_LAUNCH(launch_tracer_stage<R>(m, TP, U, V, T, T2, Text, W, T, st0, st1, 0.5,
-                                       1.0, 1.0 / 3.0, 2.0 / 3.0, dt, sp, s->err, st));
+    SLIM_LAUNCH(stage(T2, T, 0.5, 1.0, 1.0 / 3.0, 2.0 / 3.0));
   }
   SLIM_CUDA_TRY(cudaMemcpyAsync(s->eta, s->eta_next, sizeof(double) * 3 * m.n_tri,
                                 cudaMemcpyDeviceToDevice, st));
@@ -232,6 +245,13 @@ extern "C" slim_status slim_state_alloc(const slim_mesh* m, slim_precision prec,
   if (prec != SLIM_FP64 && prec != SLIM_MIXED) { set_error("unknown precision"); return SLIM_ERR_ARG; }
   slim_status st = check_params(par);
   if (st != SLIM_OK) return st;
+  if (par->vertical == 1) {
+    const size_t esz = prec == SLIM_FP64 ? sizeof(double) : sizeof(float);
+    if (coupled_smem_bytes(m->d, m->tile_prisms, esz) > (size_t)227 * 1024) {
+      set_error("coupled column system: the tile's shared memory exceeds 227 KB (use smaller tiles)");
+      return SLIM_ERR_UNSUPPORTED;
+    }
+  }
   slim_state* s = new slim_state();
   s->mesh = m;
   s->prec = prec;
@@ -279,6 +299,7 @@ extern "C" slim_status slim_state_set_params(slim_state* s, const slim_params* p
   slim_status st = check_params(par);
   if (st != SLIM_OK) return st;
   if (par->scheme != s->par.scheme) { set_error("scheme cannot change"); return SLIM_ERR_ARG; }
+  if (par->vertical != s->par.vertical) { set_error("vertical cannot change"); return SLIM_ERR_ARG; }
   if (par->scheme == SLIM_SCHEME_SPLIT && par->n_sub != s->par.n_sub) {
     set_error("n_sub cannot change");
     return SLIM_ERR_ARG;
@@ -388,14 +409,16 @@ extern "C" slim_status slim_continuity(slim_state* s, double dt, void* stream) {
   if (!s) { set_error("state is null"); return SLIM_ERR_ARG; }
   if (!(dt > 0)) { set_error("dt must be positive"); return SLIM_ERR_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
-  if (s->prec == SLIM_FP64)
-    SLIM_LAUNCH(launch_continuity<double>(s->mesh->d, tile_of(s), (const double*)s->U, (const double*)s->V,
-                                          s->eta, (const double*)s->st_cur, s->eta_next,
-                                          (double*)s->st_next, (double*)s->W, dt, st));
-  else
-    SLIM_LAUNCH(launch_continuity<float>(s->mesh->d, tile_of(s), (const float*)s->U, (const float*)s->V,
-                                         s->eta, (const float*)s->st_cur, s->eta_next,
-                                         (float*)s->st_next, (float*)s->W, dt, st));
+  const bool cpl = s->par.vertical != 0;
+  if (s->prec == SLIM_FP64) {
+    auto f = cpl ? launch_continuity_cpl<double> : launch_continuity<double>;
+    SLIM_LAUNCH(f(s->mesh->d, tile_of(s), (const double*)s->U, (const double*)s->V, s->eta,
+                  (const double*)s->st_cur, s->eta_next, (double*)s->st_next, (double*)s->W, dt, st));
+  } else {
+    auto f = cpl ? launch_continuity_cpl<float> : launch_continuity<float>;
+    SLIM_LAUNCH(f(s->mesh->d, tile_of(s), (const float*)s->U, (const float*)s->V, s->eta,
+                  (const float*)s->st_cur, s->eta_next, (float*)s->st_next, (float*)s->W, dt, st));
+  }
   return SLIM_OK;
 }
 
@@ -425,14 +448,16 @@ extern "C" slim_status slim_vertical_solve(slim_state* s, int field, double beta
     sp.flux_top = sp.flux_bot = 0.0;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  if (s->prec == SLIM_FP64)
-    SLIM_LAUNCH(launch_vertical_solve<double>(s->mesh->d, tile_of(s), (const double*)s->W, (const double*)s->st_cur,
-                                              (const double*)rhs_dev, (double*)out_dev, beta_dt, sp,
-                                              s->err, st));
-  else
-    SLIM_LAUNCH(launch_vertical_solve<float>(s->mesh->d, tile_of(s), (const float*)s->W, (const float*)s->st_cur,
-                                             (const float*)rhs_dev, (float*)out_dev, beta_dt, sp,
-                                             s->err, st));
+  const bool cpl = s->par.vertical != 0;
+  if (s->prec == SLIM_FP64) {
+    auto f = cpl ? launch_vertical_solve_cpl<double> : launch_vertical_solve<double>;
+    SLIM_LAUNCH(f(s->mesh->d, tile_of(s), (const double*)s->W, (const double*)s->st_cur,
+                  (const double*)rhs_dev, (double*)out_dev, beta_dt, sp, s->err, st));
+  } else {
+    auto f = cpl ? launch_vertical_solve_cpl<float> : launch_vertical_solve<float>;
+    SLIM_LAUNCH(f(s->mesh->d, tile_of(s), (const float*)s->W, (const float*)s->st_cur,
+                  (const float*)rhs_dev, (float*)out_dev, beta_dt, sp, s->err, st));
+  }
   return SLIM_OK;
 }
 
@@ -546,10 +571,11 @@ extern "C" slim_status slim_tracer_mass(slim_state* s, int field, double* mass_h
   if (field != SLIM_FIELD_T && field != SLIM_FIELD_S) { set_error("field must be T or S"); return SLIM_ERR_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
   void* T = field == SLIM_FIELD_T ? s->T : s->S;
+  const bool cpl = s->par.vertical != 0;
   if (s->prec == SLIM_FP64)
-    SLIM_LAUNCH(launch_mass<double>(s->mesh->d, tile_of(s), (const double*)T, s->eta, s->red, s->red_out, st));
+    SLIM_LAUNCH(launch_mass<double>(s->mesh->d, tile_of(s), (const double*)T, s->eta, s->red, s->red_out, st, cpl));
   else
-    SLIM_LAUNCH(launch_mass<float>(s->mesh->d, tile_of(s), (const float*)T, s->eta, s->red, s->red_out, st));
+    SLIM_LAUNCH(launch_mass<float>(s->mesh->d, tile_of(s), (const float*)T, s->eta, s->red, s->red_out, st, cpl));
   SLIM_CUDA_TRY(cudaMemcpyAsync(mass_host, s->red_out, sizeof(double), cudaMemcpyDeviceToHost, st));
   SLIM_CUDA_TRY(cudaStreamSynchronize(st));
   return SLIM_OK;

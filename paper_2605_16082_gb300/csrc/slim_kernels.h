@@ -48,10 +48,28 @@ template <typename R>
 cudaError_t launch_column_divergence(const DevMesh& m, int TP, const R* U, const R* V,
                                      const R* st_cur, double* out, cudaStream_t st);
 
-// mass: block partials (2 doubles per tile: sum, compensation) then one final block
+// mass: block partials (2 doubles per tile: sum, compensation) then one final block;
+// consistent: the consistent mass of the coupled column system instead of the lumped one
 template <typename R>
 cudaError_t launch_mass(const DevMesh& m, int TP, const R* T, const double* eta, double* partials,
-                        double* result, cudaStream_t st);
+                        double* result, cudaStream_t st, bool consistent);
+
+// coupled (consistent-mass, 6x6 blocks per prism) column system of the tracer scheme
+size_t coupled_smem_bytes(const DevMesh& m, int TP, size_t esz);
+template <typename R>
+cudaError_t launch_continuity_cpl(const DevMesh& m, int TP, const R* U, const R* V, const double* eta,
+                                  const R* st_cur, double* eta_out, R* st_out, R* W, double dt,
+                                  cudaStream_t st);
+template <typename R>
+cudaError_t launch_tracer_stage_cpl(const DevMesh& m, int TP, const R* U, const R* V, const R* Tn,
+                                    const R* Tp, const R* Text, const R* W, R* Tout, const R* st_n,
+                                    const R* st_np1, double th_p, double th_s, double alpha,
+                                    double beta, double dt, const StageParams& sp, int* err,
+                                    cudaStream_t st);
+template <typename R>
+cudaError_t launch_vertical_solve_cpl(const DevMesh& m, int TP, const R* W, const R* st, const R* rhs,
+                                      R* out, double bdt, const StageParams& sp, int* err,
+                                      cudaStream_t stm);
 
 // float <-> double conversion
 cudaError_t launch_convert_d2f(const double* in, float* out, size_t n, cudaStream_t st);

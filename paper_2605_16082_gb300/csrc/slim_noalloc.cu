@@ -73,8 +73,10 @@ extern "C" slim_status slim_tracer_mass_noalloc(slim_state* s, int field, double
   // partials in the library array and the result at the caller's address
   const cudaError_t e =
       s->prec == SLIM_FP64
-          ? launch_mass<double>(m, s->mesh->tile_prisms, (const double*)T, s->eta, part, mass_dev, st)
-          : launch_mass<float>(m, s->mesh->tile_prisms, (const float*)T, s->eta, part, mass_dev, st);
+          ? launch_mass<double>(m, s->mesh->tile_prisms, (const double*)T, s->eta, part, mass_dev, st,
+                                s->par.vertical != 0)
+          : launch_mass<float>(m, s->mesh->tile_prisms, (const float*)T, s->eta, part, mass_dev, st,
+                               s->par.vertical != 0);
   if (e != cudaSuccess) { set_error(std::string("tracer mass: ") + cudaGetErrorString(e)); return SLIM_ERR_CUDA; }
   return SLIM_OK;
 }

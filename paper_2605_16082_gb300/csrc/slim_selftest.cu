@@ -47,10 +47,65 @@ __global__ void k_barrier_check(unsigned* bar, int* err, int skip_block, int rou
   }
 }
 
+// Arithmetic peak: every thread runs 8 independent FMA chains (enough independent
+// work to keep the pipe busy at full occupancy); a result is stored only when it
+// is NaN, which never happens, so that the chains are not removed.
+template <typename R>
+__global__ void __launch_bounds__(256) k_fma_peak(long long iters, R b, R c, R* out) {
+  R a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = (R)(threadIdx.x + j) * (R)1e-3;
+  for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = fma(a[j], b, c);
+  }
+  R s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += a[j];
+  if (s != s) out[blockIdx.x] = s;
+}
+
 }  // namespace
 }  // namespace slim
 
 using namespace slim;
+
+extern "C" slim_status slim_selftest_fma_peak(int precision, long long iters, double* flops_per_s,
+                                              double* ms) {
+  clear_error();
+  if ((precision != SLIM_FP64 && precision != SLIM_MIXED) || iters < 1 || !flops_per_s || !ms) {
+    set_error("bad argument");
+    return SLIM_ERR_ARG;
+  }
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = 8 * sms, threads = 256;
+  void* d = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&d, (size_t)blocks * sizeof(double));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float t = 0.f;
+  for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first launch warms up
+    e = cudaEventRecord(e0);
+    if (precision == SLIM_FP64)
+      k_fma_peak<double><<<blocks, threads>>>(iters, 0.999999, 1e-7, (double*)d);
+    else
+      k_fma_peak<float><<<blocks, threads>>>(iters, 0.9999f, 1e-4f, (float*)d);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(e1);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (d) cudaFree(d);
+  if (e != cudaSuccess) { set_error(std::string("selftest: ") + cudaGetErrorString(e)); return SLIM_ERR_CUDA; }
+  *ms = t;
+  *flops_per_s = 2.0 * 8.0 * (double)iters * blocks * threads / (t * 1e-3);
+  return SLIM_OK;
+}
 
 extern "C" slim_status slim_selftest_barrier(int n_blocks, int skip_block, int rounds, int* err_bits,
                                              int* arrivals) {

@@ -425,7 +425,9 @@ __device__ __forceinline__ CSum block_csum(CSum v, double* s_s, double* s_c) {
   return {s_s[0], s_c[0]};
 }
 
-template <typename R, int TP>
+// CPL: the consistent mass of the coupled column system, whose node weights are
+// sum_a K(dz/2)_ab = (J_h/48)(dz_b + sum dz) instead of the lumped (J_h/12) dz_b
+template <typename R, int TP, bool CPL>
 __global__ void __launch_bounds__(TP) k_mass_partial(DevMesh m, const R* __restrict__ T,
                                                      const double* __restrict__ eta,
                                                      double* __restrict__ part) {
@@ -438,10 +440,13 @@ __global__ void __launch_bounds__(TP) k_mass_partial(DevMesh m, const R* __restr
     const int lt = tile_tri_of(s_off, tl.nt, i);
     const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
     const int p = tl.p0 + i, nt = m.n_tri;
-    const double w12 = m.jh[t] * (1.0 / 12.0);
+    double dz[3];
+    for (int a = 0; a < 3; ++a) dz[a] = dz_r<double>(m, a * nt + t, eta[a * nt + t], k, N);
+    const double w12 = m.jh[t] * (1.0 / 12.0), w48 = m.jh[t] * (1.0 / 48.0);
+    const double sdz = dz[0] + dz[1] + dz[2];
     for (int a = 0; a < 3; ++a) {
-      const double dz = dz_r<double>(m, a * nt + t, eta[a * nt + t], k, N);
-      const double x = w12 * dz * ((double)T[(size_t)a * m.P + p] + (double)T[(size_t)(3 + a) * m.P + p]);
+      const double wa = CPL ? w48 * (dz[a] + sdz) : w12 * dz[a];
+      const double x = wa * ((double)T[(size_t)a * m.P + p] + (double)T[(size_t)(3 + a) * m.P + p]);
       v = csum_add(v, {x, 0.0});
     }
   }
@@ -573,8 +578,11 @@ cudaError_t launch_rhs3d(const DevMesh& m, int TP, const R* U, const R* V, const
 
 template <typename R>
 cudaError_t launch_mass(const DevMesh& m, int TP, const R* T, const double* eta, double* partials,
-                        double* result, cudaStream_t stm) {
-  SLIM_TP_SWITCH(TP, (k_mass_partial<R, TPc><<<m.n_tiles, TPc, 0, stm>>>(m, T, eta, partials)));
+                        double* result, cudaStream_t stm, bool consistent) {
+  if (consistent)
+    SLIM_TP_SWITCH(TP, (k_mass_partial<R, TPc, true><<<m.n_tiles, TPc, 0, stm>>>(m, T, eta, partials)))
+  else
+    SLIM_TP_SWITCH(TP, (k_mass_partial<R, TPc, false><<<m.n_tiles, TPc, 0, stm>>>(m, T, eta, partials)))
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_mass_final<256><<<1, 256, 0, stm>>>(partials, m.n_tiles, result);
@@ -609,7 +617,7 @@ cudaError_t launch_convert_f2d(const float* in, double* out, size_t n, cudaStrea
   template cudaError_t launch_rhs3d<R>(const DevMesh&, int, const R*, const R*, const R*, const R*,  \
                                        const R*, R*, cudaStream_t);                                  \
   template cudaError_t launch_mass<R>(const DevMesh&, int, const R*, const double*, double*,         \
-                                      double*, cudaStream_t);
+                                      double*, cudaStream_t, bool);
 
 SLIM_INSTANTIATE(double)
 SLIM_INSTANTIATE(float)

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libslim.so")
 
 SLIM_FP64, SLIM_MIXED = 0, 1
 SLIM_SCHEME_TRACER, SLIM_SCHEME_SPLIT = 0, 1
+SLIM_VERTICAL_LUMPED, SLIM_VERTICAL_COUPLED = 0, 1
 FIELD = dict(T=0, S=1, U=2, V=3, W=4, R_X=5, R_Y=6, T_EXT=7, S_EXT=8, ETA=16, QX=17, QY=18, ETA_NEXT=19,
              QBAR_X=20, QBAR_Y=21, S3_X=22, S3_Y=23, F2D_X=24, F2D_Y=25, U_EXT=26, V_EXT=27,
              U_EXT_B=28, V_EXT_B=29, T_EXT_B=30, S_EXT_B=31)
@@ -30,7 +31,7 @@ EXPORTED = ["slim_params_default", "slim_status_string", "slim_last_error", "sli
             "slim_rhs2d", "slim_vertical_solve", "slim_hpg", "slim_step", "slim_tracer_mass",
             "slim_step_kernel_count", "slim_profile_begin", "slim_profile_end",
             "slim_phase_name", "slim_tracer_mass_noalloc", "slim_selftest_conversions",
-            "slim_selftest_barrier"]
+            "slim_selftest_barrier", "slim_selftest_fma_peak"]
 PHASES = ["continuity", "tracer_stage", "hpg", "mom_pred", "ext2d", "momentum", "tracers", "misc"]
 
 
@@ -41,7 +42,7 @@ class SlimParams(C.Structure):
         "tide_amp", "tide_period")] + [(n, C.c_int) for n in (
         "scheme", "n_sub", "tile_prisms", "check_every", "blocks_per_sm", "use_graph",
         "persistent_2d")] + [(n, C.c_double) for n in ("forcing_t_a", "forcing_t_b")] + [
-        ("forcing", C.c_int)]
+        ("forcing", C.c_int), ("vertical", C.c_int)]
 
 
 class SlimError(RuntimeError):
@@ -89,6 +90,7 @@ def lib() -> C.CDLL:
             "slim_selftest_conversions": ([C.c_longlong, C.c_ulonglong, C.POINTER(C.c_longlong),
                                            C.POINTER(C.c_longlong)], _i),
             "slim_selftest_barrier": ([_i, _i, _i, C.POINTER(_i), C.POINTER(_i)], _i),
+            "slim_selftest_fma_peak": ([_i, C.c_longlong, _dp, _dp], _i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -246,6 +248,13 @@ def slim_selftest_barrier(n_blocks: int, skip_block: int, rounds: int) -> tuple[
     _check(lib().slim_selftest_barrier(int(n_blocks), int(skip_block), int(rounds), C.byref(a),
                                        C.byref(b)))
     return a.value, b.value
+
+
+def slim_selftest_fma_peak(precision: int, iters: int = 1 << 16) -> tuple[float, float]:
+    """(FLOP/s, milliseconds) of the library's FMA-throughput kernel."""
+    f, ms = C.c_double(), C.c_double()
+    _check(lib().slim_selftest_fma_peak(precision, C.c_longlong(iters), C.byref(f), C.byref(ms)))
+    return f.value, ms.value
 
 
 def slim_step_kernel_count(state: int) -> int:
