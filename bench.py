@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true", help="skip the 1000-step mixed-error run")
     ap.add_argument("--layer-sweep", action="store_true",
                     help="time per step against the number of sigma layers (1..64) instead")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the z-level and reef workloads and the tracer-scheme timings")
     return ap.parse_args()
 
 
@@ -131,8 +133,8 @@ def workload_inputs(name: str):
             u, v = wl.basin_velocity(m)
             T = wl.c2_initial_state(m)["T"]
         return m, dict(kappa_v=W["kappa_v"]), dict(U=u, V=v, T=T, ETA=np.zeros(3 * m.n_tri)), W["dt"], 1
-    ini = {"basin_baroclinic": wl.c2_initial_state, "zlevel_baroclinic": wl.c4_initial_state,
-           "reef_baroclinic": wl.c5_initial_state}[name](m)
+    ini = {"basin_baroclinic": wl.c2_initial_state, "basin_baroclinic_small": wl.c2_initial_state,
+           "zlevel_baroclinic": wl.c4_initial_state, "reef_baroclinic": wl.c5_initial_state}[name](m)
     fields = dict(U=ini["u"], V=ini["v"], T=ini["T"], S=ini["S"], ETA=ini["eta"], QX=ini["U"], QY=ini["V"])
     par = dict(scheme=1, n_sub=W["n_sub"], kappa_v=W["kappa_v"], nu_v=W["nu_v"],
                kappa_h=W.get("kappa_h", 0.0), nu_h=W.get("nu_h", 0.0))
@@ -224,6 +226,125 @@ def rooflines(r: dict, m, scheme: str, pname: str, workload: str, hbm: float, pe
                   for k, v in out.items()}
 
 
+# FP64 arithmetic of the dominant FP64 kernel per launch, counted by ncu on the same
+# sources (2 x DFMA + DADD + DMUL executed, sm__sass_thread_inst_executed_op_d*),
+# valid only while the kernel sources hash to ``src``; see profiles/.
+FP64_FLOPS = {}
+
+
+def alu_peaks(slim, sms: int) -> dict:
+    """Measured FMA throughput of the library's FMA-loop kernel in FP64 and FP32 with
+    the SM clock sampled meanwhile, and the FP64 peak derived from the unit count
+    (GB300: 2 FP64 FMA per SM per clock) at that clock."""
+    samp = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    samp.start()
+    f64, ms64 = slim.slim_selftest_fma_peak(slim.SLIM_FP64, 1 << 15)
+    f32, ms32 = slim.slim_selftest_fma_peak(slim.SLIM_MIXED, 1 << 20)
+    clk = samp.stop()
+    mhz = clk.get("sm_mhz") or 2070.0
+    return dict(fp64_measured_tflops=f64 / 1e12, fp32_measured_tflops=f32 / 1e12,
+                fp64_derived_tflops=sms * 2 * 2 * mhz * 1e6 / 1e12, sms=sms, sm_mhz=mhz,
+                derivation="SMs x 2 FP64 FMA/clock x 2 FLOP x median SM clock under load",
+                kernel="8 blocks of 256 threads per SM, 8 independent FMA chains per thread",
+                clocks=clk)
+
+
+def time_workload(slim, torch, name: str, prec: int, steps: int, warmup: int, tile: int, occ: int = 4,
+                  profile: bool = True, **extra) -> dict:
+    """One workload at a fixed tiling (no autotuner): CUDA-event time of `steps`
+    graph-replayed steps after `warmup`, clocks sampled meanwhile, and (profile)
+    the per-kernel phase times of as many more launched steps."""
+    W = wl.WORKLOADS[name]
+    m, over, fields, dt, nf = workload_inputs(name)
+    over = dict(over, **extra)
+    par = slim.slim_params_default(**over)
+    par.tile_prisms, par.blocks_per_sm = tile, occ
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    with slim.Model(m, prec, par) as mod:
+        torch.cuda.synchronize()
+        dev_bytes = free0 - torch.cuda.mem_get_info()[0]
+        for k, v in fields.items():
+            mod.upload(k, v)
+        t = 0.0
+        for _ in range(warmup):
+            slim.slim_step(mod.state, t, dt, sh); t += dt
+        samp = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+        samp.start()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            slim.slim_step(mod.state, t, dt, sh); t += dt
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = samp.stop()
+        ms = e0.elapsed_time(e1) / steps
+        r = dict(n_tri=m.n_tri, n_prisms=m.n_prisms, layers=int(m.n_layers.max()),
+                 min_layers=int(m.n_layers.min()), ms_per_step=ms, value=6.0 * m.n_prisms * nf / (ms / 1e3),
+                 steps=steps, warmup=warmup, clocks=clk, device_bytes=dev_bytes,
+                 tiling=dict(prisms_per_block=tile, blocks_per_sm=occ))
+        if profile:
+            n_k = slim.slim_step_kernel_count(mod.state)
+            slim.slim_profile_begin(mod.state, n_k * steps + 8)
+            for _ in range(steps):
+                slim.slim_step(mod.state, t, dt, sh); t += dt
+            torch.cuda.synchronize()
+            r["phases"] = slim.slim_profile_end(mod.state)
+            r["rk2d_stages"] = 3 * (par.n_sub // 2 + par.n_sub) * steps if W["scheme"] == "split" else 0
+        slim.slim_state_check(mod.state, sh)
+    return r
+
+
+def _build_mesh(name: str) -> None:
+    wl.WORKLOADS[name]["mesh"]()
+
+
+def start_mesh_build(name: str):
+    """Build (and cache on disk) a slow-to-generate mesh in a spawned process while
+    this one times the GPU."""
+    import multiprocessing as mp
+    p = mp.get_context("spawn").Process(target=_build_mesh, args=(name,))
+    p.start()
+    return p
+
+
+def extra_workloads(slim, torch, args, hbm: float, peak_src: str, reef_proc) -> dict:
+    """The z-level basin (uneven columns, 11.4M prisms) and the reef stress mesh
+    (41.4M prisms) in the mixed form, each with its roofline and clocks."""
+    out = {}
+    for name, tile, steps in (("zlevel_baroclinic", 256, 5), ("reef_baroclinic", 512, 3)):
+        if name == "reef_baroclinic" and reef_proc is not None:
+            reef_proc.join()
+        r = time_workload(slim, torch, name, slim.SLIM_MIXED, steps, 2, tile)
+        m = types_ns(r)
+        head, allk = rooflines(r, m, "split", "mixed", name, hbm, peak_src)
+        r.pop("phases"); r.pop("rk2d_stages")
+        r.update(roofline=head, roofline_all=allk, precision="mixed")
+        out[name] = r
+    return out
+
+
+def types_ns(r: dict):
+    import types
+    return types.SimpleNamespace(n_prisms=r["n_prisms"], n_tri=r["n_tri"])
+
+
+def tracer_scheme_times(slim, torch, steps: int = 50) -> dict:
+    """Square-basin tracer workload (2048 triangles x 10 layers, dt = 5 s) with the
+    lumped 2x2-block and the coupled 6x6-block column systems, both precisions:
+    CUDA-event ms per step and DoF-updates/s (one 3D field)."""
+    out = {}
+    for vname, v in (("lumped", slim.SLIM_VERTICAL_LUMPED), ("coupled", slim.SLIM_VERTICAL_COUPLED)):
+        for pname, prec in (("fp64", slim.SLIM_FP64), ("mixed", slim.SLIM_MIXED)):
+            r = time_workload(slim, torch, "square_tracer", prec, steps, 5, 256, profile=False, vertical=v)
+            out.setdefault(vname, {})[pname] = dict(ms_per_step=r["ms_per_step"], value=r["value"])
+    out.update(workload="square_tracer", n_prisms=20480, unit=UNIT, steps=steps)
+    return out
+
+
 def run_ours(args, rank: int, world: int):
     import torch
     import __graft_entry__ as g
@@ -241,6 +362,8 @@ def run_ours(args, rank: int, world: int):
     res = {}
     clocks = None
     tuned = {}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    res["alu_peaks"] = alu_peaks(slim, sms)
     for pname in precs:
         prec = slim.SLIM_MIXED if pname == "mixed" else slim.SLIM_FP64
         par = slim.slim_params_default(**over)
@@ -511,8 +634,8 @@ def _oracle_worker(job):
         def step(k):
             state[0], state[1], _ = otr.tracer_step(om, state[0], state[1], u, v, W["dt"], W["kappa_v"])
     else:
-        ini = {"basin_baroclinic": wl.c2_initial_state, "zlevel_baroclinic": wl.c4_initial_state,
-               "reef_baroclinic": wl.c5_initial_state}[workload](sub)
+        ini = {"basin_baroclinic": wl.c2_initial_state, "basin_baroclinic_small": wl.c2_initial_state,
+               "zlevel_baroclinic": wl.c4_initial_state, "reef_baroclinic": wl.c5_initial_state}[workload](sub)
         st = obc.State(u=otr.to3(ini["u"], P), v=otr.to3(ini["v"], P), T=otr.to3(ini["T"], P),
                        S=otr.to3(ini["S"], P), eta=otr.to2(ini["eta"], sub.n_tri),
                        U=otr.to2(ini["U"], sub.n_tri), V=otr.to2(ini["V"], sub.n_tri))
@@ -611,7 +734,11 @@ def main():
         if rank == 0:
             print(json.dumps(layer_sweep(args)))
         return
+    reef_proc = None
+    if rank == 0 and not args.no_extra and args.workload == "basin_baroclinic":
+        reef_proc = start_mesh_build("reef_baroclinic")
     m, res, clocks = run_ours(args, rank, world)
+    alu = res.pop("alu_peaks")
     cfg.update(n_tri=m.n_tri, n_prisms=m.n_prisms, layers=int(m.n_layers.max()),
                parallelism=f"replicas{world}")
     if rank != 0:
@@ -642,8 +769,24 @@ def main():
                             e2e=f.get("e2e"), phases_ms={k: v[0] for k, v in f["phases"].items()},
                             device_bytes=f["device_bytes"],
                             tiling=dict(prisms_per_block=f["tile_prisms"], blocks_per_sm=f["blocks_per_sm"]))
+        fl = FP64_FLOPS.get((line["fp64"]["roofline"]["kernel"], args.workload))
+        flops = fl["flops_per_launch"] if fl and fl["src"] == kernel_src_hash() else None
+        lm = line["fp64"]["roofline"]["launch_ms"]
+        ach = flops / (lm / 1e3) / 1e12 if flops else None
+        line["fp64"]["roofline_alu"] = dict(
+            kernel=line["fp64"]["roofline"]["kernel"], bound="alu", unit="TFLOP/s", achieved=ach,
+            peak=alu["fp64_derived_tflops"], peak_src="derived (unit count x sampled clock)",
+            peak_measured=alu["fp64_measured_tflops"],
+            frac=(ach / alu["fp64_derived_tflops"]) if ach else None,
+            flops_per_launch=flops, flops_src="ncu executed FP64 instructions (2 DFMA + DADD + DMUL)")
+    line["alu_peaks"] = alu
     if not args.no_accuracy and "mixed" in res:
         line["mixed_accuracy"] = mixed_accuracy()
+    if not args.no_extra and args.workload == "basin_baroclinic":
+        import torch
+        from paper_2605_16082_gb300 import slim
+        line["extra_workloads"] = extra_workloads(slim, torch, args, pk["hbm_gbs"], pk["src"], reef_proc)
+        line["tracer_scheme"] = tracer_scheme_times(slim, torch)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.workload, m, args.cpu_seconds)
     print(json.dumps(line))

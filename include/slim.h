@@ -232,11 +232,20 @@ slim_status slim_state_check(slim_state* s, void* stream);
  * Hot-path operations
  * ------------------------------------------------------------------------- */
 
-/* slim_rhs3d: horizontal residual of a 3D tracer field (Eq. 6, horizontal part):
+/* slim_rhs3d: horizontal residual of a 3D field at the state's elevation, with the
+ * layer transport q = (dz/2) u of the state's velocity.
+ * field SLIM_FIELD_T or _S: the tracer residual (Eq. 6, horizontal part)
  *   out[c,a,p] = int_K q T . grad(phi_a) psi_c  -  sum_faces int phi_a psi_c (q.n)^ T^
- * with the layer transport q = (dz/2) u of the state's velocity at the state's
- * elevation, face transport averaged over both sides, T^ upwind at the face
- * quadrature points, no flux through walls.  field: SLIM_FIELD_T or _S.
+ *   face transport averaged over both sides, T^ upwind at the face quadrature
+ *   points, no flux through walls.
+ * field SLIM_FIELD_U or _V (SLIM_SCHEME_SPLIT, forcing 0): one component of the
+ *   3D horizontal momentum term F_3D^h of Sec. 2.2 (Eq. 11): upwind advection
+ *   -div(q u), horizontal SIPG viscosity nu_h, Coriolis, the baroclinic pressure
+ *   gradient -r/rho0 (integrated exactly) and the quadratic bed drag, open faces
+ *   with the own transport and zero-gradient velocity (the prediction of the
+ *   split step).  r is recomputed first from the state's T, S (as slim_hpg:
+ *   SLIM_FIELD_R_X/Y are overwritten), and the FP64 column sums of both components
+ *   (the 3D-to-2D coupling S3) are left in SLIM_FIELD_S3_X / _S3_Y.
  * out_dev: 6P elements of the compute type. */
 slim_status slim_rhs3d(slim_state* s, int field, void* out_dev, void* stream);
 

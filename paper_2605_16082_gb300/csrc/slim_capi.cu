@@ -399,7 +399,14 @@ slim_status rhs3d_t(slim_state* s, int field, void* out, cudaStream_t st) {
 extern "C" slim_status slim_rhs3d(slim_state* s, int field, void* out_dev, void* stream) {
   clear_error();
   if (!s || !out_dev) { set_error("null argument"); return SLIM_ERR_ARG; }
-  if (field != SLIM_FIELD_T && field != SLIM_FIELD_S) { set_error("field must be T or S"); return SLIM_ERR_ARG; }
+  if (field == SLIM_FIELD_U || field == SLIM_FIELD_V) {
+    if (s->par.scheme != SLIM_SCHEME_SPLIT) {
+      set_error("the momentum residual needs SLIM_SCHEME_SPLIT");
+      return SLIM_ERR_UNSUPPORTED;
+    }
+    return split_rhs3d_momentum(s, field, out_dev, (cudaStream_t)stream);
+  }
+  if (field != SLIM_FIELD_T && field != SLIM_FIELD_S) { set_error("field must be T, S, U or V"); return SLIM_ERR_ARG; }
   return s->prec == SLIM_FP64 ? rhs3d_t<double>(s, field, out_dev, (cudaStream_t)stream)
                               : rhs3d_t<float>(s, field, out_dev, (cudaStream_t)stream);
 }

@@ -505,7 +505,8 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
     k_mompred(DevMesh m, AdvIn<R> in, const R* __restrict__ Rx, const R* __restrict__ Ry,
               PP<R> pp, double* __restrict__ S3x, double* __restrict__ S3y,
               double* __restrict__ Sqx, double* __restrict__ Sqy, R* __restrict__ S3x_r,
-              R* __restrict__ S3y_r, R* __restrict__ Ex, R* __restrict__ Ey) {
+              R* __restrict__ S3y_r, R* __restrict__ Ex, R* __restrict__ Ey,
+              R* __restrict__ Fx_out, R* __restrict__ Fy_out) {
   extern __shared__ __align__(16) unsigned char smem[];
   int* s_off = reinterpret_cast<int*>(smem);
   const int TPX = TP + m.max_tile_tris;
@@ -532,6 +533,9 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
         Fy[c][a] += ey[c][a];
         Ex[(size_t)(c * 3 + a) * m.P + p] = ex[c][a];
         Ey[(size_t)(c * 3 + a) * m.P + p] = ey[c][a];
+        // the whole F_3D^h per node when asked for (slim_rhs3d of a velocity)
+        if (Fx_out) Fx_out[(size_t)(c * 3 + a) * m.P + p] = Fx[c][a];
+        if (Fy_out) Fy_out[(size_t)(c * 3 + a) * m.P + p] = Fy[c][a];
       }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -1269,13 +1273,15 @@ cudaError_t launch_hpg(const DevMesh& m, int TP, int occ, const R* T, const R* S
 
 template <typename R>
 cudaError_t launch_mompred(const DevMesh& m, int TP, int occ, const AdvIn<R>& in, const R* Rx,
-                           const R* Ry, const PP<R>& pp, SplitBufs* b, cudaStream_t s) {
+                           const R* Ry, const PP<R>& pp, SplitBufs* b, cudaStream_t s,
+                           R* Fx_out = nullptr, R* Fy_out = nullptr) {
   SLIM_TPO_SWITCH(R, TP, occ, {
     const size_t sm = tile_smem(m, TPc, sizeof(R), 12);
     cudaError_t e = set_smem2(k_mompred<R, TPc, OCc>, sm);
     if (e != cudaSuccess) return e;
     k_mompred<R, TPc, OCc><<<m.n_tiles, TPc, sm, s>>>(m, in, Rx, Ry, pp, b->S3x, b->S3y, b->Sqx, b->Sqy,
-                                                 (R*)b->S3x_r, (R*)b->S3y_r, (R*)b->Ex, (R*)b->Ey);
+                                                 (R*)b->S3x_r, (R*)b->S3y_r, (R*)b->Ex, (R*)b->Ey,
+                                                 Fx_out, Fy_out);
   });
   return cudaGetLastError();
 }
@@ -1651,6 +1657,34 @@ slim_status split_hpg(slim_state* s, cudaStream_t st) {
                               (const float*)s->st_cur, phys<float>(s->par), (float*)s->Rx,
                               (float*)s->Ry, st));
   return SLIM_OK;
+}
+
+// F_3D^h of the state (a velocity component into out) with r recomputed from the
+// state's T, S; the column sums S3 go to the split buffers (SLIM_FIELD_S3_X/Y)
+template <typename R>
+slim_status rhs3d_momentum_t(slim_state* s, int field, R* out, cudaStream_t st) {
+  const DevMesh& m = s->mesh->d;
+  const int TP = s->mesh->tile_prisms;
+  const int occ = sizeof(R) == 8 ? 2 : occ_of(s->par, TP);
+  const PP<R> pp = phys<R>(s->par);
+  SLIM_CU(launch_hpg<R>(m, TP, occ, (const R*)s->T, (const R*)s->S, (const R*)s->st_cur, pp, (R*)s->Rx,
+                        (R*)s->Ry, st));
+  AdvIn<R> pin{(const R*)s->U, (const R*)s->V, nullptr, nullptr, nullptr, nullptr, (const R*)s->st_cur,
+               nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  SLIM_CU(launch_mompred<R>(m, TP, occ, pin, (const R*)s->Rx, (const R*)s->Ry, pp, s->sp, st,
+                            field == SLIM_FIELD_U ? out : nullptr, field == SLIM_FIELD_V ? out : nullptr));
+  s->sp->has_s3 = true;
+  return SLIM_OK;
+}
+
+slim_status split_rhs3d_momentum(slim_state* s, int field, void* out, cudaStream_t st) {
+  if (!s->sp) { set_error("split buffers missing"); return SLIM_ERR_UNSUPPORTED; }
+  if (s->par.forcing) {
+    set_error("slim_rhs3d of a velocity needs forcing = 0 (the forced exterior state depends on a stage time)");
+    return SLIM_ERR_UNSUPPORTED;
+  }
+  return s->prec == SLIM_FP64 ? rhs3d_momentum_t<double>(s, field, (double*)out, st)
+                              : rhs3d_momentum_t<float>(s, field, (float*)out, st);
 }
 
 slim_status split_rhs2d(slim_state* s, double t, double* out, cudaStream_t st) {

@@ -11,6 +11,7 @@ void split_free(slim_state* s);
 void* split_field(slim_state* s, int field);  // 2D double buffers of the last stage, or null
 slim_status split_hpg(slim_state* s, cudaStream_t st);
 slim_status split_rhs2d(slim_state* s, double t, double* out, cudaStream_t st);
+slim_status split_rhs3d_momentum(slim_state* s, int field, void* out, cudaStream_t st);
 slim_status split_step(slim_state* s, double t, double dt, cudaStream_t st);
 int split_kernel_count(const slim_state* s);
 // the step's time kernel (its first argument is the step's start time)

@@ -110,6 +110,42 @@ def test_rhs2d_parity(slim, case):
     assert_close(got[2], RV, TOL64)
 
 
+@pytest.mark.parametrize("case", ["basin", "square", "zlevel"])
+def test_rhs3d_momentum_parity(slim, case):
+    """slim_rhs3d of U and V: F_3D^h of the state (advection by the uncorrected
+    transport, SIPG viscosity, Coriolis, -r/rho0 with r from the state's T and S,
+    bed drag) and its FP64 column sums S3, element by element against the oracle;
+    the basin and square cases have an open boundary, the z-level case walls
+    against shallower columns."""
+    import torch
+    from oracle import baroclinic as bc
+    from oracle import tracer as tr
+    from oracle.mesh import OMesh
+    m = case_mesh(case)
+    ini = initial(m, 2)
+    p = params(slim)
+    om = OMesh(m)
+    st = oracle_state(m, om, ini)
+    par = oracle_params(p)
+    with model(slim, m, slim.SLIM_FP64, p, ini) as mod:
+        assert mod.info["n_tiles"] > 1
+        got = []
+        for f in (slim.FIELD["U"], slim.FIELD["V"]):
+            out = torch.zeros(6 * mod.P, dtype=torch.float64, device="cuda")
+            slim.slim_rhs3d(mod.state, f, out.data_ptr())
+            torch.cuda.synchronize()
+            got.append(out.cpu().numpy())
+        s3 = (mod.download("S3_X"), mod.download("S3_Y"))
+    dz = om.thickness(st.eta)
+    rx, ry = bc.hpg(om, par, st.T, st.S, st.eta)
+    qx, qy = tr.transport(dz, st.u, st.v)
+    Fx, Fy = bc.momentum_horizontal(om, par, st.u, st.v, qx, qy, rx, ry, dz, ext=(None, None, None, None))
+    assert_close(got[0], Fx, TOL64, "Fx")
+    assert_close(got[1], Fy, TOL64, "Fy")
+    assert_close(s3[0], tr.column_sum(om, Fx), TOL64, "S3x")
+    assert_close(s3[1], tr.column_sum(om, Fy), TOL64, "S3y")
+
+
 FIELDS3 = [("U", "u"), ("V", "v"), ("T", "T"), ("S", "S")]
 FIELDS2 = [("ETA", "eta"), ("QX", "U"), ("QY", "V")]
 

@@ -141,6 +141,9 @@ WORKLOADS = {
                           kappa_v=1e-3, scheme="tracer"),
     "basin_baroclinic": dict(mesh=lambda: c2_mesh(200_000, 20, 0), steps=1000, n_sub=20,
                              kappa_v=1e-3, nu_v=1e-3, kappa_h=1.0, nu_h=1.0, scheme="split"),
+    # the same basin at a quarter of the triangles (~1M prisms): profiler captures
+    "basin_baroclinic_small": dict(mesh=lambda: c2_mesh(50_000, 20, 0), steps=1000, n_sub=20,
+                                   kappa_v=1e-3, nu_v=1e-3, kappa_h=1.0, nu_h=1.0, scheme="split"),
     "zlevel_baroclinic": dict(mesh=lambda: c4_mesh(500_000, 0), steps=3, n_sub=20,
                               kappa_v=1e-3, nu_v=1e-3, kappa_h=1.0, nu_h=1.0, scheme="split"),
     # reef-scale stress run: ~2.4M triangles around 400 islands, 1-30 z-levels (~41M prisms)
