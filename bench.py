@@ -345,6 +345,49 @@ def tracer_scheme_times(slim, torch, steps: int = 50) -> dict:
     return out
 
 
+def halo_times(slim, torch, steps: int = 10, warmup: int = 3) -> dict:
+    """The partitioned tracer step on one device (basin tracer workload: 197,480
+    triangles x 20 layers, mixed form): one state launching every kernel, and 2
+    and 4 partitions with one ghost layer, boundary tiles first and the halo
+    exchange of every stage output overlapping the interior tiles.  CUDA-event ms
+    per step; the differences to the single state are the cost of the partitioned
+    path (the split launches and the exchanges)."""
+    name = "basin_tracer"
+    m, over, fields, dt, nf = workload_inputs(name)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    out = dict(workload=name, n_tri=m.n_tri, n_prisms=m.n_prisms, precision="mixed", steps=steps)
+
+    def timed(step):
+        for i in range(warmup):
+            step(i)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(steps):
+            step(warmup + i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    par = slim.slim_params_default(**over)
+    par.use_graph = 0
+    with slim.Model(m, slim.SLIM_MIXED, par, tile_prisms=256) as mod:
+        for k, v in fields.items():
+            mod.upload(k, v)
+        out["one_state_ms"] = timed(lambda i: slim.slim_step(mod.state, i * dt, dt, sh))
+    for K in (2, 4):
+        with slim.PartitionedModel(m, K, slim.SLIM_MIXED, par, tile_prisms=256) as pm:
+            for k, v in fields.items():
+                pm.upload(k, v)
+            ms = timed(lambda i: pm.step(i * dt, dt, sh))
+            ghosts = int(sum(p.n_tri - p.n_owned for p in pm.pt.parts))
+        out[f"parts{K}_ms"] = ms
+        out[f"parts{K}_ghost_triangles"] = ghosts
+        out[f"parts{K}_overhead"] = ms / out["one_state_ms"] - 1.0
+    return out
+
+
 def run_ours(args, rank: int, world: int):
     import torch
     import __graft_entry__ as g
@@ -787,6 +830,7 @@ def main():
         from paper_2605_16082_gb300 import slim
         line["extra_workloads"] = extra_workloads(slim, torch, args, pk["hbm_gbs"], pk["src"], reef_proc)
         line["tracer_scheme"] = tracer_scheme_times(slim, torch)
+        line["partitioned"] = halo_times(slim, torch)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.workload, m, args.cpu_seconds)
     print(json.dumps(line))

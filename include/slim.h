@@ -200,6 +200,20 @@ slim_status slim_mesh_create(const double* xy, int n_vert, const int* tri, int n
                              int n_levels, const signed char* bnd, int tile_prisms,
                              slim_mesh** out);
 void slim_mesh_destroy(slim_mesh* m);
+/* slim_mesh_create_part: a partition's mesh for the partitioned step (Sec. 3,
+ * "Multi-GPU": horizontal partitions with one layer of ghost triangles).  Same
+ * arguments as slim_mesh_create plus
+ *   tri_class [n_tri]  non-decreasing: 0 an owned triangle with a ghost neighbour,
+ *                      1 an owned triangle without, 2 a ghost triangle (a copy of
+ *                      another partition's triangle; its edges that leave the
+ *                      partition are walls)
+ * Thread-block tiles never mix classes, so the kernels can run over the boundary
+ * tiles, the interior tiles or both.  Errors as slim_mesh_create, SLIM_ERR_ARG for
+ * a missing or unordered tri_class. */
+slim_status slim_mesh_create_part(const double* xy, int n_vert, const int* tri, int n_tri,
+                                  const double* h_tri, const int* n_layers, const double* levels,
+                                  int n_levels, const signed char* bnd, int tile_prisms,
+                                  const signed char* tri_class, slim_mesh** out);
 /* Sizes of a mesh (any pointer may be NULL). */
 slim_status slim_mesh_info(const slim_mesh* m, int64_t* n_prisms, int* n_tri, int* max_layers,
                            int* n_tiles);
@@ -322,6 +336,42 @@ slim_status slim_tracer_mass(slim_state* s, int field, double* mass_host, void* 
  * other states, other threads) race on it.  No cudaMalloc, cudaFree or
  * allocating library routine is called.  field: SLIM_FIELD_T or _S. */
 slim_status slim_tracer_mass_noalloc(slim_state* s, int field, double* mass_dev, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Partitioned step on one device (Sec. 3, "Multi-GPU": horizontal domain
+ * decomposition with one ghost-triangle layer, halo exchanges after every phase
+ * that reads lateral neighbours, boundary kernels ahead of the interior ones).
+ * Each partition is a state (SLIM_SCHEME_TRACER, equal precision and column
+ * system) on a slim_mesh_create_part mesh; the states and meshes stay owned by
+ * the caller and must outlive the halo.
+ * ------------------------------------------------------------------------- */
+typedef struct slim_halo slim_halo;
+/* pair_count [n_parts * n_parts]: triangles partition i sends to partition j
+ *   (row i, column j; 0 on the diagonal).
+ * send_tris, recv_tris: the pairs' lists concatenated in row-major (i, j) order;
+ *   entry q of pair (i, j) is an owned triangle of i (its local id) and the local
+ *   id of its ghost copy in j.  Columns must have equal layer counts.
+ * Allocates per pair a send and a receive buffer of one 3D field's columns, two
+ * streams (the boundary stream at the highest priority) and events.
+ * Errors: SLIM_ERR_ARG (null, counts, ids out of range), SLIM_ERR_MESH (layer
+ * counts differ), SLIM_ERR_UNSUPPORTED (not the tracer scheme), SLIM_ERR_OOM. */
+slim_status slim_halo_create(slim_state* const* parts, int n_parts, const int* pair_count,
+                             const int* send_tris, const int* recv_tris, slim_halo** out);
+void slim_halo_destroy(slim_halo* h);
+/* Copy the owners' values of one field into every ghost column: a pack kernel per
+ * pair into its send buffer, one device-to-device cudaMemcpyAsync per pair into
+ * the receive buffer, an unpack kernel per pair.  field: SLIM_FIELD_T, _S, _U, _V,
+ * _W (3D) or SLIM_FIELD_ETA (2D).  Enqueued on stream. */
+slim_status slim_halo_exchange(slim_halo* h, int field, void* stream);
+/* One tracer-scheme step t -> t + dt of every partition (the same arithmetic per
+ * prism as slim_step): continuity over the owned tiles; three SSP-RK3 stages, each
+ * with the boundary tiles on the high-priority stream, then the exchange of the
+ * stage output on that stream while the interior tiles run on the second one;
+ * then eta' -> eta, its exchange and the stretch of every column.  The ghost
+ * columns' velocity and exterior profile are the caller's (uploaded or
+ * exchanged once).  Ordered after the work already on `stream`, which waits for
+ * the step's end; the host does not wait. */
+slim_status slim_halo_step(slim_halo* h, double t, double dt, void* stream);
 
 /* slim_selftest_conversions: diagnostic (no counterpart in the paper).  Runs the
  * library's integer-pipe binary32 <-> binary64 conversions (used by the mixed

@@ -90,6 +90,9 @@ struct slim_mesh {
   std::vector<int> col_off_h;
   std::vector<int> tile_t0_h;
   std::vector<int> nbr_h;
+  // first tile of each triangle class of a partition mesh (0 owned next to a ghost,
+  // 1 owned interior, 2 ghost) and the tile count; 0, 0, 0, n_tiles otherwise
+  int class_tile[4] = {0, 0, 0, 0};
 };
 
 struct slim_state {

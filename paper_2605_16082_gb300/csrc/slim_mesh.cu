@@ -57,12 +57,43 @@ extern "C" const char* slim_status_string(slim_status s) {
   return "unknown status";
 }
 
+namespace {
+slim_status mesh_create(const double* xy, int n_vert, const int* tri, int n_tri, const double* h_tri,
+                        const int* n_layers, const double* levels, int n_levels, const signed char* bnd,
+                        int tile_prisms, const signed char* tri_class, slim_mesh** out);
+}
+
 extern "C" slim_status slim_mesh_create(const double* xy, int n_vert, const int* tri, int n_tri,
                                         const double* h_tri, const int* n_layers,
                                         const double* levels, int n_levels,
                                         const signed char* bnd, int tile_prisms,
                                         slim_mesh** out) {
   clear_error();
+  return mesh_create(xy, n_vert, tri, n_tri, h_tri, n_layers, levels, n_levels, bnd, tile_prisms, nullptr,
+                     out);
+}
+
+extern "C" slim_status slim_mesh_create_part(const double* xy, int n_vert, const int* tri, int n_tri,
+                                             const double* h_tri, const int* n_layers,
+                                             const double* levels, int n_levels,
+                                             const signed char* bnd, int tile_prisms,
+                                             const signed char* tri_class, slim_mesh** out) {
+  clear_error();
+  if (!tri_class) { set_error("tri_class is null"); return SLIM_ERR_ARG; }
+  for (int t = 0; t < n_tri; ++t) {
+    if (tri_class[t] < 0 || tri_class[t] > 2 || (t > 0 && tri_class[t] < tri_class[t - 1])) {
+      set_error("tri_class must be non-decreasing in {0, 1, 2}");
+      return SLIM_ERR_ARG;
+    }
+  }
+  return mesh_create(xy, n_vert, tri, n_tri, h_tri, n_layers, levels, n_levels, bnd, tile_prisms, tri_class,
+                     out);
+}
+
+namespace {
+slim_status mesh_create(const double* xy, int n_vert, const int* tri, int n_tri, const double* h_tri,
+                        const int* n_layers, const double* levels, int n_levels, const signed char* bnd,
+                        int tile_prisms, const signed char* tri_class, slim_mesh** out) {
   if (!out) { set_error("out is null"); return SLIM_ERR_ARG; }
   *out = nullptr;
   if (!xy || !tri || !h_tri || !n_layers || !bnd || n_vert < 3 || n_tri < 1) {
@@ -172,19 +203,31 @@ extern "C" slim_status slim_mesh_create(const double* xy, int n_vert, const int*
     }
     i = j;
   }
-  // tiling: consecutive triangles, at most tile_prisms prisms per tile
+  // tiling: consecutive triangles, at most tile_prisms prisms per tile; a new tile
+  // also starts where the triangle class changes (partition meshes)
   std::vector<int> tile_t0;
   tile_t0.push_back(0);
+  int class_tile[4] = {0, 0, 0, 0};  // first tile of classes 0, 1, 2 and the end
   int cur = 0;
   for (int t = 0; t < nt; ++t) {
     int N = n_layers[t];
-    if (cur + N > tile_prisms) {
+    const bool new_class = tri_class && t > 0 && tri_class[t] != tri_class[t - 1];
+    if (cur + N > tile_prisms || (new_class && cur > 0)) {
       tile_t0.push_back(t);
       cur = 0;
     }
+    if (tri_class && (t == 0 || tri_class[t] != tri_class[t - 1]))
+      for (int c = (t == 0 ? 0 : tri_class[t - 1] + 1); c <= tri_class[t]; ++c)
+        class_tile[c] = (int)tile_t0.size() - 1;
     cur += N;
   }
   tile_t0.push_back(nt);
+  {
+    const int n_tiles = (int)tile_t0.size() - 1;
+    const int last = tri_class ? tri_class[nt - 1] : 2;
+    for (int c = last + 1; c <= 3; ++c) class_tile[c] = n_tiles;
+    if (!tri_class) { class_tile[0] = class_tile[1] = class_tile[2] = 0; class_tile[3] = n_tiles; }
+  }
   int max_tile_tris = 0;
   std::vector<int4> tile_info(tile_t0.size() - 1);
   for (size_t i = 0; i + 1 < tile_t0.size(); ++i) {
@@ -271,9 +314,11 @@ extern "C" slim_status slim_mesh_create(const double* xy, int n_vert, const int*
   m->col_off_h = col_off;
   m->tile_t0_h = tile_t0;
   m->nbr_h = nbr;
+  for (int c = 0; c < 4; ++c) m->class_tile[c] = class_tile[c];
   *out = m;
   return SLIM_OK;
 }
+}  // namespace
 
 extern "C" void slim_mesh_destroy(slim_mesh* m) { free_mesh(m); }
 

@@ -31,7 +31,8 @@ EXPORTED = ["slim_params_default", "slim_status_string", "slim_last_error", "sli
             "slim_rhs2d", "slim_vertical_solve", "slim_hpg", "slim_step", "slim_tracer_mass",
             "slim_step_kernel_count", "slim_profile_begin", "slim_profile_end",
             "slim_phase_name", "slim_tracer_mass_noalloc", "slim_selftest_conversions",
-            "slim_selftest_barrier", "slim_selftest_fma_peak"]
+            "slim_selftest_barrier", "slim_selftest_fma_peak", "slim_mesh_create_part",
+            "slim_halo_create", "slim_halo_destroy", "slim_halo_exchange", "slim_halo_step"]
 PHASES = ["continuity", "tracer_stage", "hpg", "mom_pred", "ext2d", "momentum", "tracers", "misc"]
 
 
@@ -91,6 +92,11 @@ def lib() -> C.CDLL:
                                            C.POINTER(C.c_longlong)], _i),
             "slim_selftest_barrier": ([_i, _i, _i, C.POINTER(_i), C.POINTER(_i)], _i),
             "slim_selftest_fma_peak": ([_i, C.c_longlong, _dp, _dp], _i),
+            "slim_mesh_create_part": ([_vp, _i, _vp, _i, _vp, _vp, _vp, _i, _vp, _i, _vp, C.POINTER(_vp)], _i),
+            "slim_halo_create": ([_vp, _i, _vp, _vp, _vp, C.POINTER(_vp)], _i),
+            "slim_halo_destroy": ([_vp], None),
+            "slim_halo_exchange": ([_vp, _i, _vp], _i),
+            "slim_halo_step": ([_vp, _d, _d, _vp], _i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -140,6 +146,45 @@ def slim_mesh_create(xy, tri, h_tri, n_layers, bnd, levels=None, tile_prisms: in
                                   0 if lev is None else int(lev.shape[0]), _ptr(bnd),
                                   int(tile_prisms), C.byref(out)))
     return out.value
+
+
+def slim_mesh_create_part(xy, tri, h_tri, n_layers, bnd, tri_class, levels=None, tile_prisms: int = 256) -> int:
+    xy = np.ascontiguousarray(xy, np.float64)
+    tri = np.ascontiguousarray(tri, np.int32)
+    h_tri = np.ascontiguousarray(h_tri, np.float64)
+    n_layers = np.ascontiguousarray(n_layers, np.int32)
+    bnd = np.ascontiguousarray(bnd, np.int8)
+    cls = np.ascontiguousarray(tri_class, np.int8)
+    lev = None if levels is None else np.ascontiguousarray(levels, np.float64)
+    out = _vp()
+    _check(lib().slim_mesh_create_part(_ptr(xy), int(xy.shape[0]), _ptr(tri), int(tri.shape[0]),
+                                       _ptr(h_tri), _ptr(n_layers), None if lev is None else _ptr(lev),
+                                       0 if lev is None else int(lev.shape[0]), _ptr(bnd),
+                                       int(tile_prisms), _ptr(cls), C.byref(out)))
+    return out.value
+
+
+def slim_halo_create(states, pair_count, send_tris, recv_tris) -> int:
+    arr = (_vp * len(states))(*states)
+    pc = np.ascontiguousarray(pair_count, np.int32)
+    st = np.ascontiguousarray(send_tris, np.int32)
+    rt = np.ascontiguousarray(recv_tris, np.int32)
+    out = _vp()
+    _check(lib().slim_halo_create(arr, len(states), _ptr(pc), _ptr(st) if st.size else None,
+                                  _ptr(rt) if rt.size else None, C.byref(out)))
+    return out.value
+
+
+def slim_halo_destroy(halo: int) -> None:
+    lib().slim_halo_destroy(halo)
+
+
+def slim_halo_exchange(halo: int, field: int, stream: int = 0) -> None:
+    _check(lib().slim_halo_exchange(halo, field, stream))
+
+
+def slim_halo_step(halo: int, t: float, dt: float, stream: int = 0) -> None:
+    _check(lib().slim_halo_step(halo, t, dt, stream))
 
 
 def slim_mesh_destroy(mesh: int) -> None:
@@ -336,3 +381,61 @@ class Model:
             self.close()
         except Exception:
             pass
+
+
+class PartitionedModel:
+    """The partitioned tracer step on one device: one state per partition of
+    ``partition.partition(mesh, n_parts)`` and the halo that connects them.  Fields
+    are uploaded and downloaded as global arrays (the partitions' owned values)."""
+
+    def __init__(self, mesh, n_parts: int, precision: int = SLIM_FP64, params: SlimParams | None = None,
+                 tile_prisms: int = 256):
+        from . import partition as pa
+        self.mesh = mesh
+        self.pt = pa.partition(mesh, n_parts)
+        self.params = params if params is not None else slim_params_default()
+        self.meshes, self.states, self.halo = [], [], None
+        self._pmap = [pa.prism_map(mesh, p) for p in self.pt.parts]
+        try:
+            for p in self.pt.parts:
+                self.meshes.append(slim_mesh_create_part(p.xy, p.tri, p.h_tri, p.n_layers, p.bnd, p.tri_class,
+                                                         p.levels, tile_prisms))
+                self.states.append(slim_state_alloc(self.meshes[-1], precision, self.params))
+            self.halo = slim_halo_create(self.states, self.pt.pair_count, self.pt.send_tris, self.pt.recv_tris)
+        except Exception:
+            self.close()
+            raise
+
+    def upload(self, field: str, values, stream: int = 0) -> None:
+        from . import partition as pa
+        is3d = FIELD_IS_3D[field]
+        for part, st, pm in zip(self.pt.parts, self.states, self._pmap):
+            slim_state_upload(st, FIELD[field], pa.to_local(self.mesh, part, values, is3d, pm), stream)
+
+    def download(self, field: str, stream: int = 0) -> np.ndarray:
+        from . import partition as pa
+        is3d = FIELD_IS_3D[field]
+        loc = []
+        for part, st, pm in zip(self.pt.parts, self.states, self._pmap):
+            n = 6 * len(pm) if is3d else 3 * part.n_tri
+            loc.append(slim_state_download(st, FIELD[field], n, stream))
+        return pa.owned_to_global(self.mesh, self.pt, loc, is3d)
+
+    def step(self, t: float, dt: float, stream: int = 0) -> None:
+        slim_halo_step(self.halo, t, dt, stream)
+
+    def close(self) -> None:
+        if getattr(self, "halo", None):
+            slim_halo_destroy(self.halo)
+            self.halo = None
+        for st in getattr(self, "states", []):
+            slim_state_free(st)
+        for m in getattr(self, "meshes", []):
+            slim_mesh_destroy(m)
+        self.states, self.meshes = [], []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
