@@ -20,8 +20,8 @@ namespace slim {
 struct SplitBufs {
   // 2D (double): running external state A and two stage buffers
   double *Ae, *AU, *AV, *Be, *BU, *BV, *Ce, *CU, *CV;
-  double *S3x, *S3y, *Sqx, *Sqy, *Gb, *F2x, *F2y, *eta_half, *cw, *icw, *iw6;
-  float *cw_f, *icw_f;
+  double *S3x, *S3y, *Sqx, *Sqy, *Gb, *F2x, *F2y, *eta_half, *cw, *iw6;
+  float *cw_f;
   void *Ae_r, *AU_r, *AV_r, *Be_r, *BU_r, *BV_r, *Ce_r, *CU_r, *CV_r;  // compute-type shadows
   void *S3x_r, *S3y_r;
   double* tide;  // open-boundary elevation per external stage of the step (+1 slot)
@@ -37,6 +37,10 @@ struct SplitBufs {
   int n_tide;
   // mixed form: FP32 stage-increment sums of the 2D subcycle and FP32 1/(w/6)
   float *Dacc, *Eacc, *Gacc, *iw6_f;
+  // 2D adjacency in one word per edge ([3][n_tri]): neighbour << 4 | neighbour-local
+  // vertices of the edge (l0 | l1 << 2), or -1 (wall) / -2 (open boundary); a quarter
+  // of the bytes of the 3D adjacency, which the 2D stages re-read every stage
+  int* adj2;
   // non-advective momentum terms (viscosity, Coriolis, -r/rho0, drag) of the stage's
   // evaluation state, [6][P] each: written by the prediction, read by the update
   void *Ex, *Ey;
@@ -208,15 +212,15 @@ __global__ void k_ext_sums(DevMesh m, const R* __restrict__ Uxa, const R* __rest
 // ---------------------------------------------------------------------------
 // wave speed of the 2D flux at every edge point: c = sqrt(g (h^- + h^+)/2)
 // ---------------------------------------------------------------------------
-__global__ void k_wave_speed(DevMesh m, double g, double* __restrict__ cw, double* __restrict__ icw,
-                             float* __restrict__ cw_f, float* __restrict__ icw_f,
-                             double* __restrict__ iw6, float* __restrict__ iw6_f) {
+__global__ void k_wave_speed(DevMesh m, double g, double* __restrict__ cw, float* __restrict__ cw_f,
+                             double* __restrict__ iw6, float* __restrict__ iw6_f, int* __restrict__ adj2) {
   const int nt = m.n_tri;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
     iw6[t] = 6.0 / m.jh[t];
     iw6_f[t] = (float)iw6[t];
     for (int e = 0; e < 3; ++e) {
       const int4 ei = m.einfo[e * nt + t];
+      adj2[e * nt + t] = ei.x >= 0 ? ((ei.x << 4) | (ei.w & 15)) : ei.x;
       const int a0 = e, a1 = (e + 1) % 3;
       for (int gs = 0; gs < 2; ++gs) {
         const double b0 = gs ? SLIM_GL2 : SLIM_GL1, b1 = gs ? SLIM_GL1 : SLIM_GL2;
@@ -229,9 +233,7 @@ __global__ void k_wave_speed(DevMesh m, double g, double* __restrict__ cw, doubl
         const double c = sqrt(g * 0.5 * (ho + hn));
         const int ip = (e * nt + t) * 2 + gs;
         cw[ip] = c;
-        icw[ip] = 1.0 / (2.0 * c);
         cw_f[ip] = (float)c;
-        icw_f[ip] = (float)(1.0 / (2.0 * c));
       }
     }
   }
@@ -576,12 +578,10 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
 template <typename RC> struct Ext2dGeo;
 template <> struct Ext2dGeo<double> {
   static __device__ __forceinline__ double c(const SplitBufs& b, int i) { return b.cw[i]; }
-  static __device__ __forceinline__ double ic(const SplitBufs& b, int i) { return b.icw[i]; }
   static __device__ __forceinline__ const double* Q(const SplitBufs& b) { return b.Qext; }
 };
 template <> struct Ext2dGeo<float> {
   static __device__ __forceinline__ float c(const SplitBufs& b, int i) { return b.cw_f[i]; }
-  static __device__ __forceinline__ float ic(const SplitBufs& b, int i) { return b.icw_f[i]; }
   static __device__ __forceinline__ const float* Q(const SplitBufs& b) { return b.Qext_f; }
 };
 
@@ -648,14 +648,15 @@ __device__ __forceinline__ void ext2d_residual(const DevMesh& m, const SplitBufs
   }
 #pragma unroll
   for (int ed = 0; ed < 3; ++ed) {
-    const int4 ei = m.einfo[ed * nt + t];
+    const int code = bf.adj2[ed * nt + t];
+    const int nb = code >= 0 ? code >> 4 : code;
     const int a0 = ed, a1 = (ed + 1) % 3;
     const RC nx = Geo<RC>::nx(m, ed * nt + t), ny = Geo<RC>::ny(m, ed * nt + t);
     const RC hl = (RC)0.5 * Geo<RC>::len(m, ed * nt + t);
     RC en0 = 0, en1 = 0, qn0 = 0, qn1 = 0;
-    if (ei.x >= 0) {
-      const int l0 = ei.w & 3, l1 = (ei.w >> 2) & 3;
-      const int i0 = l0 * nt + ei.x, i1 = l1 * nt + ei.x;
+    if (nb >= 0) {
+      const int l0 = code & 3, l1 = (code >> 2) & 3;
+      const int i0 = l0 * nt + nb, i1 = l1 * nt + nb;
       en0 = LD::ld(er + i0); en1 = LD::ld(er + i1);
       qn0 = LD::ld(Ur + i0) * nx + LD::ld(Vr + i0) * ny;
       qn1 = LD::ld(Ur + i1) * nx + LD::ld(Vr + i1) * ny;
@@ -668,10 +669,10 @@ __device__ __forceinline__ void ext2d_residual(const DevMesh& m, const SplitBufs
       const RC Ho = b0 * H[a0] + b1 * H[a1];
       const RC qo = b0 * qo0 + b1 * qo1;
       RC ex, qx;
-      if (ei.x >= 0) {
+      if (nb >= 0) {
         ex = b0 * en0 + b1 * en1;
         qx = b0 * qn0 + b1 * qn1;
-      } else if (ei.x == -2) {
+      } else if (nb == -2) {
         // open boundary: exterior state from data alone (tide, and the prescribed
         // transport or none), a characteristic condition that only removes energy
         ex = tide;
@@ -683,7 +684,8 @@ __device__ __forceinline__ void ext2d_residual(const DevMesh& m, const SplitBufs
       const int ip = (ed * nt + t) * 2 + gs;
       const RC c = Ext2dGeo<RC>::c(bf, ip);
       const RC fe = (RC)0.5 * (qo + qx) + (RC)0.5 * c * (eo_ - ex);
-      const RC eh = (RC)0.5 * (eo_ + ex) + (qo - qx) * Ext2dGeo<RC>::ic(bf, ip);
+      // 1/(2c) divided out here instead of read from a table: fewer bytes per stage
+      const RC eh = (RC)0.5 * (eo_ + ex) + (qo - qx) * ((RC)0.5 / c);
       Fe[ed * 2 + gs] = fe;
       const RC gq = g * Ho * eh;
       Re[a0] -= hl * b0 * fe; Re[a1] -= hl * b1 * fe;
@@ -774,7 +776,7 @@ __device__ __forceinline__ void ext2d_mx_tri(const DevMesh& m, const SplitBufs& 
   const int nt = m.n_tri;
   float Re[3], RU[3], RV[3], Fe[6];
   ext2d_residual<float, LD>(m, bf, io.er, io.Ur, io.Vr, g, tide, th, t, Re, RU, RV, Fe);
-  const float bdw = dt * bf.iw6_f[t];
+  const float bdw = dt * ((float)6 / Geo<float>::jh(m, t));   // 1 / (J_h/6), divided out here
   const float* S3x = (const float*)bf.S3x_r;
   const float* S3y = (const float*)bf.S3y_r;
   const size_t n2 = (size_t)3 * nt;
@@ -1556,7 +1558,7 @@ slim_status split_alloc(slim_state* s) {
     SLIM_CU(cudaMemset(*p, 0, n2 * 8));
     s->allocs.push_back(*p);
   }
-  double** d6[] = {&b->Gb, &b->cw, &b->icw};
+  double** d6[] = {&b->Gb, &b->cw};
   for (double** p : d6) {
     SLIM_CU(cudaMalloc((void**)p, n2 * 2 * 8));
     SLIM_CU(cudaMemset(*p, 0, n2 * 2 * 8));
@@ -1570,7 +1572,7 @@ slim_status split_alloc(slim_state* s) {
     SLIM_CU(cudaMemset(*p, 0, n2 * s->esz));
     s->allocs.push_back(*p);
   }
-  float** f6[] = {&b->cw_f, &b->icw_f};
+  float** f6[] = {&b->cw_f};
   for (float** p : f6) {
     SLIM_CU(cudaMalloc((void**)p, n2 * 2 * sizeof(float)));
     s->allocs.push_back(*p);
@@ -1594,6 +1596,9 @@ slim_status split_alloc(slim_state* s) {
   s->allocs.push_back(b->iw6);
   SLIM_CU(cudaMalloc((void**)&b->iw6_f, (size_t)m.n_tri * sizeof(float)));
   s->allocs.push_back(b->iw6_f);
+  if (m.n_tri >= (1 << 27)) { set_error("too many triangles for the 2D adjacency word"); return SLIM_ERR_ARG; }
+  SLIM_CU(cudaMalloc((void**)&b->adj2, (size_t)3 * m.n_tri * sizeof(int)));
+  s->allocs.push_back(b->adj2);
   b->Dacc = b->Eacc = b->Gacc = nullptr;
   b->bar = nullptr;
   b->run_blocks = 0;
@@ -1625,7 +1630,7 @@ slim_status split_alloc(slim_state* s) {
   SLIM_CU(cudaMemset(b->gcor_r, 0, n2 * 2 * s->esz));
   s->allocs.push_back(b->gcor_r);
   const int grd = (m.n_tri + 255) / 256;
-  k_wave_speed<<<grd, 256>>>(m, s->par.g, b->cw, b->icw, b->cw_f, b->icw_f, b->iw6, b->iw6_f);
+  k_wave_speed<<<grd, 256>>>(m, s->par.g, b->cw, b->cw_f, b->iw6, b->iw6_f, b->adj2);
   SLIM_CU(cudaGetLastError());
   return SLIM_OK;
 }
