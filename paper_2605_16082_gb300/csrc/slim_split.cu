@@ -1236,8 +1236,10 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
 size_t tile_smem(const DevMesh& m, int TP, size_t esz, int rows) {
   return ((TP + 1) * sizeof(int) + 15) / 16 * 16 + (size_t)rows * (TP + m.max_tile_tris) * esz;
 }
-// s_b [12], s_W [6], s_C [12] x TPX, s_st [3] x TP
-size_t update_smem(const DevMesh& m, int TP, size_t esz, bool) {
+// implicit: s_b [12], s_W [6], s_C [12] x TPX, s_st [3] x TP; explicit: the offsets only
+size_t update_smem(const DevMesh& m, int TP, size_t esz, bool impl) {
+  // the explicit update stages nothing in shared memory (more of it stays L1 cache)
+  if (!impl) return ((TP + 1) * sizeof(int) + 15) / 16 * 16;
   return ((TP + 1) * sizeof(int) + 15) / 16 * 16 + (size_t)30 * (TP + m.max_tile_tris) * esz +
          (size_t)3 * TP * esz;
 }
