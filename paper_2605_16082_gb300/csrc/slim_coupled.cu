@@ -20,10 +20,11 @@
 // Kernels (one thread block per tile of whole columns, as the 2x2-block path):
 //   phase 1  thread per prism: horizontal residual and right-hand side into
 //            shared memory (coalesced node planes)
-//   phase 2  thread per triangle column: the column's 6x6 blocks are assembled
-//            layer by layer and eliminated at once (block Thomas: a 6x6 Gauss-
-//            Jordan per layer on [D' | U | b], the 36-value factor C_k kept in
-//            shared memory for the back substitution)
+//   phase 2  the column's 6x6 blocks are assembled layer by layer and
+//            eliminated at once (block Thomas: a 6x6 Gauss-Jordan per layer on
+//            [D' | U | b], the 36-value factor C_k kept in shared memory for the
+//            back substitution); FP32: one thread per column, FP64: eight lanes
+//            per column, one block row each, with shuffles (no register spills)
 //   phase 3  thread per prism: coalesced write-back.
 #include <algorithm>
 #include <cmath>
@@ -467,6 +468,283 @@ __device__ void column_solve6(const DevMesh& m, int t, int N, int base, int TPX,
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same column solve by eight lanes of a warp per column (four columns per
+// warp): lane r < 6 owns block row r = (c, a) of every layer, assembles its row of
+// D_k, L_k, U_k and the right-hand side, and the block-Thomas elimination runs row-
+// parallel: the factor C_{k-1} and y_{k-1} of the layer above come from the other
+// lanes by shuffles, the Gauss-Jordan pivot rows are broadcast by shuffles, and
+// C_k is kept in shared memory for the back substitution.  Lanes 6 and 7 of a
+// group and groups past the tile's last column follow the shuffles without
+// touching memory.  The layer loop runs to the warp's deepest column, so every
+// shuffle is executed by all 32 lanes.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R shfl(R v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+
+template <typename R>
+__device__ void column_solve6_warp(const DevMesh& m, const Tile& tl, const int* s_off, int TPX,
+                                   const R* st_tile, int TPst, R* __restrict__ sb,
+                                   const R* __restrict__ sW, const R* __restrict__ sx,
+                                   R* __restrict__ sC, R kap, R pen, R bdt, R flux_top, R flux_bot,
+                                   int col_begin) {
+  const int lane = threadIdx.x & 31, r = lane & 7, gbase = lane & ~7;
+  const int col = col_begin + (lane >> 3);
+  const bool active = col < tl.nt;
+  const int nt = m.n_tri;
+  int t = tl.t0, base = 0, N = 0;
+  if (active) {
+    t = tl.t0 + col;
+    base = s_off[col] + col;
+    N = s_off[col + 1] - s_off[col];
+  }
+  int Nmax = N;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) Nmax = max(Nmax, __shfl_xor_sync(0xffffffffu, Nmax, o));
+  const bool row_on = active && r < 6;
+  const int c = (r % 6) / 3, a = r % 3;   // block row (node level, vertex); rows 6, 7 mirror 0, 1
+  const R jh = Geo<R>::jh(m, t);
+  const R G2 = (R)(2.0 / 3.0), G1 = (R)(1.0 / 3.0);
+  const R dps = c == 0 ? (R)0.5 : (R)-0.5;
+  R st[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) st[e] = active ? st_tile[e * TPst + col] : (R)1;
+  auto layer_dz = [&](int k, R dz[3]) {
+#pragma unroll
+    for (int e = 0; e < 3; ++e) dz[e] = (k < N) ? dz_rest_r<R>(m, e * nt + t, k, N) * st[e] : (R)1;
+  };
+  // row a of M_h
+  R Mh[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) Mh[b] = jh * (a == b ? (R)(2.0 / 24.0) : (R)(1.0 / 24.0));
+  // row a of Q(f) for the rule's point values f
+  auto qrow = [&](const R f[6], R out[3]) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) out[b] = 0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      double l0, l1, l2, w;
+      rule4_point(q, l0, l1, l2, w);
+      const R lam[3] = {(R)l0, (R)l1, (R)l2};
+      const R sf = (R)0.5 * jh * (R)w * f[q] * lam[a];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) out[b] += sf * lam[b];
+    }
+  };
+  // row a of K(w)
+  auto krow = [&](const R w[3], R out[3]) {
+    const R S = w[0] + w[1] + w[2];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      out[b] = (a == b) ? jh * (w[a] * (R)(1.0 / 30.0) + S * (R)(1.0 / 60.0))
+                        : jh * (w[a] + w[b] + S) * (R)(1.0 / 120.0);
+  };
+  R dz_c[3], rq_c[6], rq_p[6], rq_n[6];
+  layer_dz(0, dz_c);
+  recip_at_points<R>(dz_c, rq_c);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) rq_p[q] = rq_c[q];
+  R Cprev[6] = {0, 0, 0, 0, 0, 0}, yprev = 0;
+  for (int k = 0; k < Nmax; ++k) {
+    const bool on = k < N;          // this group's column has layer k
+    const int ks = on ? k : 0;      // a safe layer index for the loads
+    R dz_n[3] = {dz_c[0], dz_c[1], dz_c[2]};
+    if (k + 1 < N) {
+      layer_dz(k + 1, dz_n);
+      recip_at_points<R>(dz_n, rq_n);
+    }
+    R D[6], L[6], U[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) { D[j] = 0; L[j] = 0; U[j] = 0; }
+    R Om_t[3], Om_b[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      Om_t[e] = active ? sW[e * TPX + base + ks] : (R)0;
+      Om_b[e] = active ? sW[(3 + e) * TPX + base + ks] : (R)0;
+    }
+    // advection, volume
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      R w[3], Kw[3];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) w[e] = d == 0 ? G2 * Om_t[e] + G1 * Om_b[e] : G1 * Om_t[e] + G2 * Om_b[e];
+      krow(w, Kw);
+#pragma unroll
+      for (int e = 0; e < 3; ++e) D[d * 3 + e] += dps * Kw[e];
+    }
+    // advection, top interface (rows of the top nodes)
+    if (c == 0) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const R Wb = Om_t[b];
+        const R cf = Mh[b] * Wb;
+        if (k == 0 || Wb > (R)0) D[b] -= cf; else L[3 + b] -= cf;
+      }
+    }
+    // advection, bottom interface (rows of the bottom nodes)
+    if (c == 1 && k + 1 < N) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const R Wb = sW[b * TPX + base + k + 1];
+        const R cf = Mh[b] * Wb;
+        if (Wb > (R)0) U[b] += cf; else D[3 + b] += cf;
+      }
+    }
+    // diffusion, element
+    R Qc[3];
+    qrow(rq_c, Qc);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const R sq = kap * Qc[b];
+      D[c * 3 + b] -= sq;
+      D[(1 - c) * 3 + b] += sq;
+    }
+    const R h = (R)0.5 * kap;
+    if (k > 0) {  // interface above
+      R Qa[3], Qs[3], sg[6];
+      qrow(rq_p, Qa);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) sg[q] = pen * kap * fmax(rq_p[q], rq_c[q]);
+      qrow(sg, Qs);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (c == 0) {
+          L[b] += h * Qa[b];
+          L[3 + b] -= h * Qa[b];
+          D[b] += h * Qc[b];
+          D[3 + b] -= h * Qc[b];
+          D[b] -= Qs[b];
+          L[3 + b] += Qs[b];
+          D[b] += h * Qc[b];
+          L[3 + b] -= h * Qc[b];
+        } else {
+          D[b] -= h * Qc[b];
+          L[3 + b] += h * Qc[b];
+        }
+      }
+    }
+    if (k + 1 < N) {  // interface below
+      R Qb[3], Qs[3], sg[6];
+      qrow(rq_n, Qb);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) sg[q] = pen * kap * fmax(rq_c[q], rq_n[q]);
+      qrow(sg, Qs);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (c == 1) {
+          D[b] -= h * Qc[b];
+          D[3 + b] += h * Qc[b];
+          U[b] -= h * Qb[b];
+          U[3 + b] += h * Qb[b];
+          U[b] += Qs[b];
+          D[3 + b] -= Qs[b];
+          U[b] -= h * Qc[b];
+          D[3 + b] += h * Qc[b];
+        } else {
+          U[b] += h * Qc[b];
+          D[3 + b] -= h * Qc[b];
+        }
+      }
+    }
+    // right-hand side of this row (+ bdt A x0 in the increment form)
+    R rhs = row_on && on ? sb[r * TPX + base + k] : (R)0;
+    if (sx && active && on) {
+      R acc = 0;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        acc += D[j] * sx[j * TPX + base + k];
+        if (k > 0) acc += L[j] * sx[j * TPX + base + k - 1];
+        if (k + 1 < N) acc += U[j] * sx[j * TPX + base + k + 1];
+      }
+      rhs += bdt * acc;
+    }
+    if (k == 0 && c == 0) rhs += bdt * jh * (R)(1.0 / 6.0) * flux_top;
+    if (k == N - 1 && c == 1) rhs -= bdt * jh * (R)(1.0 / 6.0) * flux_bot;
+    // K = M - bdt A (row of M: G_cd K(hz)_ab)
+    {
+      R hz[3], Km[3];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) hz[e] = (R)0.5 * dz_c[e];
+      krow(hz, Km);
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const R g = (j / 3 == c) ? G2 : G1;
+        D[j] = g * Km[j % 3] - bdt * D[j];
+        L[j] = -bdt * L[j];
+        U[j] = -bdt * U[j];
+      }
+    }
+    // D' = D - L C_{k-1},  b' = b - L y_{k-1}  (rows of C_{k-1} and y_{k-1} from the group's lanes)
+#pragma unroll
+    for (int mr = 0; mr < 6; ++mr) {
+      const R yl = shfl<R>(yprev, gbase + mr);
+      rhs -= L[mr] * yl;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) D[j] -= L[mr] * shfl<R>(Cprev[j], gbase + mr);
+    }
+    // Gauss-Jordan on [D' | U | b'] across the six rows (no pivoting, as the serial form)
+#pragma unroll
+    for (int pv = 0; pv < 6; ++pv) {
+      const R dpp = shfl<R>(D[pv], gbase + pv);
+      const R ip = rcp<R>(dpp);
+      if (r == pv) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) { D[j] *= ip; U[j] *= ip; }
+        rhs *= ip;
+      }
+      R Dp[6], Up[6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        Dp[j] = shfl<R>(D[j], gbase + pv);
+        Up[j] = shfl<R>(U[j], gbase + pv);
+      }
+      const R rp = shfl<R>(rhs, gbase + pv);
+      if (r != pv) {
+        const R f = D[pv];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) { D[j] -= f * Dp[j]; U[j] -= f * Up[j]; }
+        rhs -= f * rp;
+      }
+    }
+    if (row_on && on) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) sC[(r * 6 + j) * TPX + base + k] = U[j];
+      sb[r * TPX + base + k] = rhs;
+    }
+    if (on) {  // past its last layer a group keeps that layer's factor and y
+#pragma unroll
+      for (int j = 0; j < 6; ++j) Cprev[j] = U[j];
+      yprev = rhs;
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) dz_c[e] = dz_n[e];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) { rq_p[q] = rq_c[q]; rq_c[q] = rq_n[q]; }
+  }
+  // back substitution x_k = y_k - C_k x_{k+1}, from the last layer of each column up
+  R xn = yprev;   // x of the layer below (each group starts at its own last layer)
+  for (int k = Nmax - 2; k >= 0; --k) {
+    const bool on = k + 1 < N;     // layer k exists and is not the column's last
+    R acc = 0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const R xj = shfl<R>(xn, gbase + j);
+      if (row_on && on) acc += sC[(r * 6 + j) * TPX + base + k] * xj;
+    }
+    if (row_on && on) {
+      const R x = sb[r * TPX + base + k] - acc;
+      sb[r * TPX + base + k] = x;
+      xn = x;
+    }
+  }
+  __syncwarp();
+  if (sx && row_on) {
+    for (int k = 0; k < N; ++k) sb[r * TPX + base + k] += sx[r * TPX + base + k];
+  }
+}
+
 // shared memory: offsets | sb [6] | sW [6] | sx [6] | sC [36] (x TPX) | st [3][TP]
 template <typename R>
 struct CplSmem {
@@ -576,11 +854,20 @@ __global__ void __launch_bounds__(TP) k_tracer_stage_cpl(
     for (int r = 0; r < 6; ++r) s_W[r * TPX + slot] = W[(size_t)r * m.P + p];
   }
   __syncthreads();
-  for (int lt = threadIdx.x; lt < tl.nt; lt += TP) {
-    const int t = tl.t0 + lt, base = s_off[lt] + lt, N = s_off[lt + 1] - s_off[lt];
-    const R st[3] = {s_st[lt], s_st[TP + lt], s_st[2 * TP + lt]};
-    column_solve6<R>(m, t, N, base, TPX, st, s_b, s_W, s_x, s_C, (R)sp.kappa, (R)sp.penalty, beta * dt,
-                     (R)sp.flux_top, (R)sp.flux_bot);
+  if (sizeof(R) == 8) {
+    // FP64: eight lanes per column, four columns per warp (the thread-per-column
+    // elimination spills its FP64 blocks)
+    for (int c0 = (threadIdx.x >> 5) * 4; c0 < tl.nt; c0 += (TP / 32) * 4)
+      column_solve6_warp<R>(m, tl, s_off, TPX, s_st, TP, s_b, s_W, s_x, s_C, (R)sp.kappa, (R)sp.penalty,
+                            beta * dt, (R)sp.flux_top, (R)sp.flux_bot, c0);
+  } else {
+    // FP32: one thread per column holds the blocks in registers (shorter dependence chain)
+    for (int lt = threadIdx.x; lt < tl.nt; lt += TP) {
+      const int t = tl.t0 + lt, base = s_off[lt] + lt, N = s_off[lt + 1] - s_off[lt];
+      const R st[3] = {s_st[lt], s_st[TP + lt], s_st[2 * TP + lt]};
+      column_solve6<R>(m, t, N, base, TPX, st, s_b, s_W, s_x, s_C, (R)sp.kappa, (R)sp.penalty, beta * dt,
+                       (R)sp.flux_top, (R)sp.flux_bot);
+    }
   }
   __syncthreads();
   write_tile6<R>(m, tl, TPX, slot, s_b, Tout, err);
@@ -612,11 +899,23 @@ __global__ void __launch_bounds__(TP) k_vertical_solve_cpl(DevMesh m, const R* _
   }
   __syncthreads();
   const int nt = m.n_tri;
-  for (int lt = threadIdx.x; lt < tl.nt; lt += TP) {
-    const int t = tl.t0 + lt, base = s_off[lt] + lt, N = s_off[lt + 1] - s_off[lt];
-    const R stv[3] = {st[t], st[nt + t], st[2 * nt + t]};
-    column_solve6<R>(m, t, N, base, TPX, stv, s_b, s_W, nullptr, s_C, (R)sp.kappa, (R)sp.penalty, bdt,
-                     (R)sp.flux_top, (R)sp.flux_bot);
+  R* s_st = reinterpret_cast<R*>(smem + L.off_st);
+  for (int j = threadIdx.x; j < 3 * tl.nt; j += TP) {
+    const int a = j / tl.nt, lt = j - a * tl.nt;
+    s_st[a * TP + lt] = st[a * nt + tl.t0 + lt];
+  }
+  __syncthreads();
+  if (sizeof(R) == 8) {
+    for (int c0 = (threadIdx.x >> 5) * 4; c0 < tl.nt; c0 += (TP / 32) * 4)
+      column_solve6_warp<R>(m, tl, s_off, TPX, s_st, TP, s_b, s_W, nullptr, s_C, (R)sp.kappa, (R)sp.penalty,
+                            bdt, (R)sp.flux_top, (R)sp.flux_bot, c0);
+  } else {
+    for (int lt = threadIdx.x; lt < tl.nt; lt += TP) {
+      const int t = tl.t0 + lt, base = s_off[lt] + lt, N = s_off[lt + 1] - s_off[lt];
+      const R stv[3] = {s_st[lt], s_st[TP + lt], s_st[2 * TP + lt]};
+      column_solve6<R>(m, t, N, base, TPX, stv, s_b, s_W, nullptr, s_C, (R)sp.kappa, (R)sp.penalty, bdt,
+                       (R)sp.flux_top, (R)sp.flux_bot);
+    }
   }
   __syncthreads();
   write_tile6<R>(m, tl, TPX, slot, s_b, out, err);
