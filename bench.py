@@ -177,8 +177,8 @@ KERNEL_OF = {"split": {"continuity": "k_cont_split", "hpg": "k_hpg", "mom_pred":
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
 # capture, valid only while the kernel sources hash to ``src``; see profiles/.
 TRAFFIC = {
-    ("k_update", "mixed", "basin_baroclinic"): dict(bytes=745.8e6, src="b776c25d0ef34a00"),
-    ("k_update", "fp64", "basin_baroclinic"): dict(bytes=1399.8e6, src="b776c25d0ef34a00"),
+    # quarter-size basin capture (4 instances, 198.4 MB per launch) scaled by the prisms
+    ("k_update", "mixed", "basin_baroclinic"): dict(bytes=786.6e6, src="016ee0be8b111ad9"),
 }
 KSRC = ["paper_2605_16082_gb300/csrc/slim_split.cu", "paper_2605_16082_gb300/csrc/slim_split_device.cuh",
         "paper_2605_16082_gb300/csrc/slim_device.cuh", "paper_2605_16082_gb300/csrc/slim_tracer.cu",
@@ -229,7 +229,10 @@ def rooflines(r: dict, m, scheme: str, pname: str, workload: str, hbm: float, pe
 # FP64 arithmetic of the dominant FP64 kernel per launch, counted by ncu on the same
 # sources (2 x DFMA + DADD + DMUL executed, sm__sass_thread_inst_executed_op_d*),
 # valid only while the kernel sources hash to ``src``; see profiles/.
-FP64_FLOPS = {}
+FP64_FLOPS = {
+    # quarter-size basin capture (2,344 FLOP per prism per launch) scaled by the prisms
+    ("k_update", "basin_baroclinic"): dict(flops_per_launch=9.2578e9, src="016ee0be8b111ad9"),
+}
 
 
 def alu_peaks(slim, sms: int) -> dict:
