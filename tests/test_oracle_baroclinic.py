@@ -454,3 +454,47 @@ def test_split_forcing_steady_data_does_not_depend_on_its_times():
         outs.append(bc.split_step(om, par, st, 0.0, 20.0))
     for name in ("u", "v", "T", "S", "eta", "U", "V"):
         assert np.array_equal(getattr(outs[0], name), getattr(outs[1], name)), name
+
+
+def _stratified_noise_run(om, m, par, dt, hours):
+    """max|u| every hour of a run from the stratified rest state plus seeded
+    1e-3 degC tracer noise."""
+    ini = wl.c2_initial_state(m)
+    P, nt = om.P, m.n_tri
+    st = bc.State(u=tr.to3(ini["u"], P), v=tr.to3(ini["v"], P), T=tr.to3(ini["T"], P),
+                  S=tr.to3(ini["S"], P), eta=tr.to2(ini["eta"], nt), U=tr.to2(ini["U"], nt),
+                  V=tr.to2(ini["V"], nt))
+    st.T_ext = st.T.copy(); st.S_ext = st.S.copy()
+    st.T = st.T + 1e-3 * np.random.default_rng(0).standard_normal(st.T.shape)
+    per_hour = int(round(3600.0 / dt))
+    out = []
+    for k in range(hours * per_hour):
+        st = bc.split_step(om, par, st, k * dt, dt)
+        if (k + 1) % per_hour == 0:
+            out.append(float(np.abs(st.u).max()))
+    return np.array(out)
+
+
+def test_split_stratified_rest_state_grows_a_semi_discrete_mode():
+    # The slow mode of long runs without tide, reproduced small: a flat closed basin
+    # (830 graded triangles x 3 layers, 100 m), no Coriolis, no viscosity or
+    # diffusion, strong linear stratification (N = 0.028 1/s).  Linearised about the
+    # rest state nothing dissipates velocity (upwinding is second order in the
+    # perturbation), and vertically sheared modes of grid-scale horizontal structure
+    # grow: the speed multiplies by > 4 between hours 1 and 4.  The trajectory does
+    # not depend on the step (dt = 300 s and 600 s agree within 8%; measured 2-4%), so the growth
+    # belongs to the space discretisation, not to the split-IMEX stages; vertical
+    # viscosity 0.1 m^2/s removes it.
+    m = wl.c2_mesh(600, 3, 0)
+    m.h_tri[:] = 100.0
+    m.bnd[m.bnd == 2] = 1
+    om = OMesh(m)
+    base = dict(n_sub=20, kappa_v=0.0, nu_v=0.0, kappa_h=0.0, nu_h=0.0, tide_amp=0.0, f=0.0,
+                alpha=8e-4, beta=3.04e-3)
+    dt = 80.0 * wl.fields.dt_2d(m)
+    a = _stratified_noise_run(om, m, bc.Params(**base), dt, 4)
+    b = _stratified_noise_run(om, m, bc.Params(**base), 2.0 * dt, 4)
+    assert a[3] > 4.0 * a[0] and b[3] > 4.0 * b[0], (a, b)
+    assert np.abs(a / b - 1.0).max() < 0.08, (a, b)
+    c = _stratified_noise_run(om, m, bc.Params(**dict(base, nu_v=0.1)), 2.0 * dt, 4)
+    assert c[3] < c[0], c
