@@ -768,59 +768,105 @@ struct Mx2dIO {
 };
 
 // one stage for triangle t (its own accumulators and FP64 state are only touched by
-// the thread that owns t)
+// the thread that owns t).  The stage runs in three phases: every load of the
+// triangle's own data, then the arithmetic, then every store.  None of these arrays
+// is declared restrict, so a load written after a store could not be moved above
+// it; with the loads first, the own data (stage start, increments, sums) are in
+// flight together with the residual's neighbour gathers, and the FP64 state of
+// the last stage costs one more round trip instead of one per field and node.
 template <int KIND, typename LD>
 __device__ __forceinline__ void ext2d_mx_tri(const DevMesh& m, const SplitBufs& bf, const Mx2dIO& io,
                                              float g, float tide, float th, float dt, float wq,
                                              double wn, int t) {
   const int nt = m.n_tri;
-  float Re[3], RU[3], RV[3], Fe[6];
-  ext2d_residual<float, LD>(m, bf, io.er, io.Ur, io.Vr, g, tide, th, t, Re, RU, RV, Fe);
-  const float bdw = dt * ((float)6 / Geo<float>::jh(m, t));   // 1 / (J_h/6), divided out here
+  const size_t n2 = (size_t)3 * nt;
   const float* S3x = (const float*)bf.S3x_r;
   const float* S3y = (const float*)bf.S3y_r;
-  const size_t n2 = (size_t)3 * nt;
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    const int ip = ((j >> 1) * nt + t) * 2 + (j & 1);
-    if (KIND == 0) bf.Gacc[ip] = Fe[j];
-    if (KIND == 1) bf.Gacc[ip] += Fe[j];
-    if (KIND == 2) bf.Gb[ip] += f2d_bits((bf.Gacc[ip] + 4.0f * Fe[j]) * wq);
-  }
+  // phase 1a: FP32 own data (before the residual, so they overlap its loads)
+  float s3[2][3], q0[3][3], dacc[3][3], eacc[2][3], gacc[6];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int ia = a * nt + t;
-    const float d[3] = {bdw * Re[a], bdw * (RU[a] + S3x[ia]), bdw * (RV[a] + S3y[ia])};
-    if (KIND == 0) {
-      const float q[3] = {io.en[ia], io.Un[ia], io.Vn[ia]};
-      float* o[3] = {io.eo, io.Uo, io.Vo};
+    s3[0][a] = S3x[ia];
+    s3[1][a] = S3y[ia];
+    if (KIND < 2) {
+      q0[0][a] = io.en[ia]; q0[1][a] = io.Un[ia]; q0[2][a] = io.Vn[ia];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (KIND >= 1) dacc[c][a] = bf.Dacc[c * n2 + ia];
+    if (KIND == 2) {
+      eacc[0][a] = bf.Eacc[ia];
+      eacc[1][a] = bf.Eacc[n2 + ia];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 6; ++j)
+    if (KIND >= 1) gacc[j] = bf.Gacc[((j >> 1) * nt + t) * 2 + (j & 1)];
+  float Re[3], RU[3], RV[3], Fe[6];
+  ext2d_residual<float, LD>(m, bf, io.er, io.Ur, io.Vr, g, tide, th, t, Re, RU, RV, Fe);
+  const float bdw = dt * ((float)6 / Geo<float>::jh(m, t));   // 1 / (J_h/6), divided out here
+  // the stage increments D = (dt / (J_h/6)) R, with the column sums S3 for U, V
+  float d[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    d[0][a] = bdw * Re[a];
+    d[1][a] = bdw * (RU[a] + s3[0][a]);
+    d[2][a] = bdw * (RV[a] + s3[1][a]);
+  }
+  double* x[3] = {io.e, io.U, io.V};
+  float* o[3] = {io.eo, io.Uo, io.Vo};
+  if (KIND == 0) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) bf.Gacc[((j >> 1) * nt + t) * 2 + (j & 1)] = Fe[j];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        bf.Dacc[c * n2 + ia] = d[c];
-        o[c][ia] = q[c] + d[c];
+        const int ia = a * nt + t;
+        bf.Dacc[c * n2 + ia] = d[c][a];
+        o[c][ia] = q0[c][a] + d[c][a];
       }
-    } else if (KIND == 1) {
-      const float q[3] = {io.en[ia], io.Un[ia], io.Vn[ia]};
-      float* o[3] = {io.eo, io.Uo, io.Vo};
+  } else if (KIND == 1) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) bf.Gacc[((j >> 1) * nt + t) * 2 + (j & 1)] = gacc[j] + Fe[j];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float d1 = bf.Dacc[c * n2 + ia];
-        const float s12 = d1 + d[c];
+        const int ia = a * nt + t;
+        const float d1 = dacc[c][a];
+        const float s12 = d1 + d[c][a];
         bf.Dacc[c * n2 + ia] = s12;
         if (c > 0) bf.Eacc[(c - 1) * n2 + ia] = (d1 + s12) * (1.0f / 6.0f);
-        o[c][ia] = q[c] + 0.25f * s12;
+        o[c][ia] = q0[c][a] + 0.25f * s12;
       }
-    } else {
-      double* x[3] = {io.e, io.U, io.V};
-      float* o[3] = {io.eo, io.Uo, io.Vo};
+  } else {
+    // phase 1b: the FP64 state and sums, all loads before the first store
+    double xn[3][3], qb[2][3], gb[6];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int ia = a * nt + t;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) xn[c][a] = x[c][ia];
+      qb[0][a] = bf.Qbx[ia];
+      qb[1][a] = bf.Qby[ia];
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) gb[j] = bf.Gb[((j >> 1) * nt + t) * 2 + (j & 1)];
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+      bf.Gb[((j >> 1) * nt + t) * 2 + (j & 1)] = gb[j] + f2d_bits((gacc[j] + 4.0f * Fe[j]) * wq);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int ia = a * nt + t;
+      // conversions on the integer pipe: the FP64 pipe keeps the three FP64 sums
+      bf.Qbx[ia] = qb[0][a] + wn * (xn[1][a] + f2d_bits(eacc[0][a]));
+      bf.Qby[ia] = qb[1][a] + wn * (xn[2][a] + f2d_bits(eacc[1][a]));
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        // conversions on the integer pipe: the FP64 pipe keeps the three FP64 sums
-        const double qn = x[c][ia];
-        if (c == 1) bf.Qbx[ia] += wn * (qn + f2d_bits(bf.Eacc[ia]));
-        if (c == 2) bf.Qby[ia] += wn * (qn + f2d_bits(bf.Eacc[n2 + ia]));
-        const float inc = bf.Dacc[c * n2 + ia] * (1.0f / 6.0f) + d[c] * (2.0f / 3.0f);
-        const double qnew = qn + f2d_bits(inc);
+        const float inc = dacc[c][a] * (1.0f / 6.0f) + d[c][a] * (2.0f / 3.0f);
+        const double qnew = xn[c][a] + f2d_bits(inc);
         x[c][ia] = qnew;
         o[c][ia] = d2f_bits(qnew);
       }
