@@ -36,7 +36,7 @@ struct SplitBufs {
   int forcing;
   int n_tide;
   // mixed form: FP32 stage-increment sums of the 2D subcycle and FP32 1/(w/6)
-  float *Dacc, *Eacc, *Gacc, *iw6_f;
+  float *Dacc, *Eacc, *Gacc, *Gacc2, *iw6_f;
   // 2D adjacency in one word per edge ([3][n_tri]): neighbour << 4 | neighbour-local
   // vertices of the edge (l0 | l1 << 2), or -1 (wall) / -2 (open boundary); a quarter
   // of the bytes of the 3D adjacency, which the 2D stages re-read every stage
@@ -756,9 +756,10 @@ __global__ void __launch_bounds__(256)
 // and Gbar by the last stage as well.
 //   KIND 0: residual at Q^n (shadow), Dacc = D_1, out = Q_2, Gacc = F_1
 //   KIND 1: residual at Q_2, Dacc = D_1 + D_2, Eacc = (2 D_1 + D_2)/6 (U, V),
-//           out = Q_3, Gacc = F_1 + F_2
+//           out = Q_3, Gacc2 = F_2 (a second array, so that this stage loads
+//           nothing it does not need before its stores)
 //   KIND 2: residual at Q_3; FP64 Q^n += Dacc/6 + 2 D_3/3, out = shadow of it;
-//           Qbar += wn (Q^n + Eacc), Gbar += (Gacc + 4 F_3) wq
+//           Qbar += wn (Q^n + Eacc), Gbar += ((Gacc + Gacc2) + 4 F_3) wq
 // ---------------------------------------------------------------------------
 struct Mx2dIO {
   const float *er, *Ur, *Vr;     // stage value
@@ -772,8 +773,9 @@ struct Mx2dIO {
 // triangle's own data, then the arithmetic, then every store.  None of these arrays
 // is declared restrict, so a load written after a store could not be moved above
 // it; with the loads first, the own data (stage start, increments, sums) are in
-// flight together with the residual's neighbour gathers, and the FP64 state of
-// the last stage costs one more round trip instead of one per field and node.
+// flight together with the residual's neighbour gathers, and the FP64 sums and
+// state of the last stage cost two more round trips (edge fluxes, then state and
+// transport sums) instead of one per field and node.
 template <int KIND, typename LD>
 __device__ __forceinline__ void ext2d_mx_tri(const DevMesh& m, const SplitBufs& bf, const Mx2dIO& io,
                                              float g, float tide, float th, float dt, float wq,
@@ -783,7 +785,7 @@ __device__ __forceinline__ void ext2d_mx_tri(const DevMesh& m, const SplitBufs& 
   const float* S3x = (const float*)bf.S3x_r;
   const float* S3y = (const float*)bf.S3y_r;
   // phase 1a: FP32 own data (before the residual, so they overlap its loads)
-  float s3[2][3], q0[3][3], dacc[3][3], eacc[2][3], gacc[6];
+  float s3[2][3], q0[3][3], dacc[3][3], eacc[2][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int ia = a * nt + t;
@@ -800,9 +802,6 @@ __device__ __forceinline__ void ext2d_mx_tri(const DevMesh& m, const SplitBufs& 
       eacc[1][a] = bf.Eacc[n2 + ia];
     }
   }
-#pragma unroll
-  for (int j = 0; j < 6; ++j)
-    if (KIND >= 1) gacc[j] = bf.Gacc[((j >> 1) * nt + t) * 2 + (j & 1)];
   float Re[3], RU[3], RV[3], Fe[6];
   ext2d_residual<float, LD>(m, bf, io.er, io.Ur, io.Vr, g, tide, th, t, Re, RU, RV, Fe);
   const float bdw = dt * ((float)6 / Geo<float>::jh(m, t));   // 1 / (J_h/6), divided out here
@@ -829,7 +828,7 @@ __device__ __forceinline__ void ext2d_mx_tri(const DevMesh& m, const SplitBufs& 
       }
   } else if (KIND == 1) {
 #pragma unroll
-    for (int j = 0; j < 6; ++j) bf.Gacc[((j >> 1) * nt + t) * 2 + (j & 1)] = gacc[j] + Fe[j];
+    for (int j = 0; j < 6; ++j) bf.Gacc2[((j >> 1) * nt + t) * 2 + (j & 1)] = Fe[j];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -843,7 +842,19 @@ __device__ __forceinline__ void ext2d_mx_tri(const DevMesh& m, const SplitBufs& 
       }
   } else {
     // phase 1b: the FP64 state and sums, all loads before the first store
-    double xn[3][3], qb[2][3], gb[6];
+    double gb[6];
+    float g1[6], g2[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const int ip = ((j >> 1) * nt + t) * 2 + (j & 1);
+      gb[j] = bf.Gb[ip];
+      g1[j] = bf.Gacc[ip];
+      g2[j] = bf.Gacc2[ip];
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+      bf.Gb[((j >> 1) * nt + t) * 2 + (j & 1)] = gb[j] + f2d_bits(((g1[j] + g2[j]) + 4.0f * Fe[j]) * wq);
+    double xn[3][3], qb[2][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const int ia = a * nt + t;
@@ -852,11 +863,6 @@ __device__ __forceinline__ void ext2d_mx_tri(const DevMesh& m, const SplitBufs& 
       qb[0][a] = bf.Qbx[ia];
       qb[1][a] = bf.Qby[ia];
     }
-#pragma unroll
-    for (int j = 0; j < 6; ++j) gb[j] = bf.Gb[((j >> 1) * nt + t) * 2 + (j & 1)];
-#pragma unroll
-    for (int j = 0; j < 6; ++j)
-      bf.Gb[((j >> 1) * nt + t) * 2 + (j & 1)] = gb[j] + f2d_bits((gacc[j] + 4.0f * Fe[j]) * wq);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const int ia = a * nt + t;
@@ -889,7 +895,9 @@ struct Mx2dRun {
 // Stages [first, first + count) of the run (stage index 3 q + kind); a grid
 // barrier between consecutive stages of one launch.  With count = 1 it is one
 // ordinary launch per stage (no barrier); the whole run is one cooperative launch.
-__global__ void __launch_bounds__(256) k_ext2d_run(DevMesh m, SplitBufs bf, Mx2dRun r, int first,
+// Three blocks of 256 per SM (85 registers, a few values spilled to L1) hide more
+// latency than two blocks without spills.
+__global__ void __launch_bounds__(256, 3) k_ext2d_run(DevMesh m, SplitBufs bf, Mx2dRun r, int first,
                                                    int count) {
   __shared__ int s_fail;
   const int nt = m.n_tri;
@@ -1647,7 +1655,7 @@ slim_status split_alloc(slim_state* s) {
   if (m.n_tri >= (1 << 27)) { set_error("too many triangles for the 2D adjacency word"); return SLIM_ERR_ARG; }
   SLIM_CU(cudaMalloc((void**)&b->adj2, (size_t)3 * m.n_tri * sizeof(int)));
   s->allocs.push_back(b->adj2);
-  b->Dacc = b->Eacc = b->Gacc = nullptr;
+  b->Dacc = b->Eacc = b->Gacc = b->Gacc2 = nullptr;
   b->bar = nullptr;
   b->run_blocks = 0;
   if (s->esz == 4) {
@@ -1659,9 +1667,9 @@ slim_status split_alloc(slim_state* s) {
     SLIM_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     SLIM_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ext2d_run, 256, 0));
     b->run_blocks = std::max(1, std::min(sms * per_sm, (m.n_tri + 255) / 256));
-    float** fa[] = {&b->Dacc, &b->Eacc, &b->Gacc};
-    const size_t cnt[] = {3 * n2, 2 * n2, 2 * n2};
-    for (int j = 0; j < 3; ++j) {
+    float** fa[] = {&b->Dacc, &b->Eacc, &b->Gacc, &b->Gacc2};
+    const size_t cnt[] = {3 * n2, 2 * n2, 2 * n2, 2 * n2};
+    for (int j = 0; j < 4; ++j) {
       SLIM_CU(cudaMalloc((void**)fa[j], cnt[j] * sizeof(float)));
       SLIM_CU(cudaMemset(*fa[j], 0, cnt[j] * sizeof(float)));
       s->allocs.push_back(*fa[j]);
