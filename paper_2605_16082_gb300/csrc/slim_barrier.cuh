@@ -41,4 +41,35 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblk, int* 
   return *s_fail == 0;
 }
 
+// Wait of one block of a cooperative launch for its neighbour blocks only: block b
+// publishes done[b] = k once its stores of stage k are issued, then waits until
+// done[n] >= k for every block n in its list s_nb[0, nn) (the blocks that own a
+// triangle its triangles read).  Blocks that share no data never wait for each
+// other, and no counter is contended.  Bounded like grid_barrier: after
+// kBarrierPolls polls a thread records SLIM_ERRBIT_TIMEOUT and the block returns
+// false.  *s_fail must be 0 on entry.
+__device__ __forceinline__ bool neighbour_wait(unsigned* done, unsigned k, const int* s_nb, int nn, int* err,
+                                               int* s_fail) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicExch(done + blockIdx.x, k);
+  }
+  for (int j = threadIdx.x; j < nn; j += blockDim.x) {
+    volatile unsigned* d = done + s_nb[j];
+    int it = 0;
+    while (*d < k) {
+      if (++it > kBarrierPolls) {
+        *s_fail = 1;
+        atomicOr(err, (int)SLIM_ERRBIT_TIMEOUT);
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  return *s_fail == 0;
+}
+
 }  // namespace slim

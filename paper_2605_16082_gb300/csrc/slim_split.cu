@@ -44,9 +44,15 @@ struct SplitBufs {
   // non-advective momentum terms (viscosity, Coriolis, -r/rho0, drag) of the stage's
   // evaluation state, [6][P] each: written by the prediction, read by the update
   void *Ex, *Ey;
-  // persistent 2D run: grid barrier words (arrival count, generation) and grid size
+  // persistent 2D run: grid barrier words (arrival count, generation) and grid size;
+  // the block graph of the run (bit n of row b: block n owns an edge neighbour of a
+  // triangle of block b; nbw words per row, null when the grid is too large for the
+  // in-kernel list) and the per-block stage counters of the neighbour waits
   unsigned* bar;
   int run_blocks;
+  unsigned* nbits;
+  unsigned* done;
+  int nbw;
   double *Qbx, *Qby;  // the state's time-averaged transport buffers
   // compute-type copies for the 3D kernels
   void *F2x_r, *F2y_r, *Dqx_r, *Dqy_r, *gcor_r, *st_half, *st_end;
@@ -882,15 +888,38 @@ __device__ __forceinline__ void ext2d_mx_tri(const DevMesh& m, const SplitBufs& 
 
 // The whole external run of the mixed form in one cooperative launch: every stage
 // of every subcycle over all triangles (grid-stride, so each triangle keeps its
-// thread), a grid barrier between stages.
+// thread).  Between stages a block waits only for the blocks that own the
+// neighbours of its triangles (a stage reads the previous stage's values of the
+// edge neighbours; the buffer it overwrites was last read two stages earlier, which
+// those blocks have finished too); with no block graph, a grid barrier.
+constexpr int kMaxNbBlocks = 512;
 struct Mx2dRun {
   Mx2dIO io[3];
   int n_sub, tide_base;
   float g, dt, wq;
   double wn;
   unsigned* bar;
+  const unsigned* nbits;
+  unsigned* done;
+  int nbw;
   int* err;
 };
+
+// Block graph of the persistent run: with the grid stride, triangle t belongs to
+// block (t mod stride) / 256.
+__global__ void k_block_graph(DevMesh m, int stride, int nbw, unsigned* __restrict__ bits) {
+  const int nt = m.n_tri;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const int ob = (t % stride) / 256;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int nb = m.einfo[e * nt + t].x;
+    if (nb < 0) continue;
+    const int on = (nb % stride) / 256;
+    if (on != ob) atomicOr(bits + (size_t)ob * nbw + (on >> 5), 1u << (on & 31));
+  }
+}
 
 // Stages [first, first + count) of the run (stage index 3 q + kind); a grid
 // barrier between consecutive stages of one launch.  With count = 1 it is one
@@ -900,8 +929,27 @@ struct Mx2dRun {
 __global__ void __launch_bounds__(256, 3) k_ext2d_run(DevMesh m, SplitBufs bf, Mx2dRun r, int first,
                                                    int count) {
   __shared__ int s_fail;
+  __shared__ int s_nn;
+  __shared__ int s_nb[kMaxNbBlocks];
   const int nt = m.n_tri;
   const int stride = gridDim.x * blockDim.x;
+  const bool nbw = r.nbits != nullptr && count > 1;
+  if (nbw) {  // this block's neighbour blocks, from its row of the block graph
+    if (threadIdx.x == 0) {
+      s_nn = 0;
+      s_fail = 0;
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < r.nbw; w += blockDim.x) {
+      unsigned x = r.nbits[(size_t)blockIdx.x * r.nbw + w];
+      while (x) {
+        const int n = w * 32 + __ffs(x) - 1;
+        x &= x - 1;
+        s_nb[atomicAdd(&s_nn, 1)] = n;
+      }
+    }
+    __syncthreads();
+  }
   for (int gs = first; gs < first + count; ++gs) {
     const int st = gs % 3;
     const float tide = bf.tide_f[r.tide_base + gs], th = bf.theta_f[r.tide_base + gs];
@@ -910,7 +958,11 @@ __global__ void __launch_bounds__(256, 3) k_ext2d_run(DevMesh m, SplitBufs bf, M
       else if (st == 1) ext2d_mx_tri<1, LdL2>(m, bf, r.io[1], r.g, tide, th, r.dt, r.wq, r.wn, t);
       else ext2d_mx_tri<2, LdL2>(m, bf, r.io[2], r.g, tide, th, r.dt, r.wq, r.wn, t);
     }
-    if (gs + 1 < first + count && !grid_barrier(r.bar, gridDim.x, r.err, &s_fail)) return;
+    if (gs + 1 < first + count) {
+      const bool ok = nbw ? neighbour_wait(r.done, (unsigned)(gs - first + 1), s_nb, s_nn, r.err, &s_fail)
+                          : grid_barrier(r.bar, gridDim.x, r.err, &s_fail);
+      if (!ok) return;
+    }
   }
 }
 
@@ -1463,9 +1515,13 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, int tide_base,
     run.wq = (float)(1.0 / (6.0 * n_sub));
     run.wn = 1.0 / n_sub;
     run.bar = b->bar;
+    run.nbits = b->nbits;
+    run.done = b->done;
+    run.nbw = b->nbw;
     run.err = s->err;
     if (s->par.persistent_2d) {
       SLIM_CU(cudaMemsetAsync(b->bar, 0, sizeof(unsigned), stm));  // arrival count
+      if (b->done) SLIM_CU(cudaMemsetAsync(b->done, 0, (size_t)b->run_blocks * sizeof(unsigned), stm));
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeCooperative;
       attr[0].val.cooperative = 1;
@@ -1658,6 +1714,8 @@ slim_status split_alloc(slim_state* s) {
   b->Dacc = b->Eacc = b->Gacc = b->Gacc2 = nullptr;
   b->bar = nullptr;
   b->run_blocks = 0;
+  b->nbits = b->done = nullptr;
+  b->nbw = 0;
   if (s->esz == 4) {
     SLIM_CU(cudaMalloc((void**)&b->bar, 2 * sizeof(unsigned)));
     SLIM_CU(cudaMemset(b->bar, 0, 2 * sizeof(unsigned)));
@@ -1667,6 +1725,19 @@ slim_status split_alloc(slim_state* s) {
     SLIM_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     SLIM_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ext2d_run, 256, 0));
     b->run_blocks = std::max(1, std::min(sms * per_sm, (m.n_tri + 255) / 256));
+    if (b->run_blocks <= kMaxNbBlocks) {
+      b->nbw = (b->run_blocks + 31) / 32;
+      const size_t nbits = (size_t)b->run_blocks * b->nbw;
+      SLIM_CU(cudaMalloc((void**)&b->nbits, nbits * sizeof(unsigned)));
+      s->allocs.push_back(b->nbits);
+      SLIM_CU(cudaMalloc((void**)&b->done, (size_t)b->run_blocks * sizeof(unsigned)));
+      s->allocs.push_back(b->done);
+      SLIM_CU(cudaMemset(b->nbits, 0, nbits * sizeof(unsigned)));
+      SLIM_CU(cudaMemset(b->done, 0, (size_t)b->run_blocks * sizeof(unsigned)));
+      k_block_graph<<<(m.n_tri + 255) / 256, 256>>>(m, b->run_blocks * 256, b->nbw, b->nbits);
+      SLIM_CU(cudaGetLastError());
+      SLIM_CU(cudaDeviceSynchronize());
+    }
     float** fa[] = {&b->Dacc, &b->Eacc, &b->Gacc, &b->Gacc2};
     const size_t cnt[] = {3 * n2, 2 * n2, 2 * n2, 2 * n2};
     for (int j = 0; j < 4; ++j) {
