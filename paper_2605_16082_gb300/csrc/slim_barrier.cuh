@@ -67,7 +67,9 @@ __device__ __forceinline__ bool neighbour_wait(unsigned* done, unsigned k, const
       __nanosleep(64);
     }
   }
-  __threadfence();
+  // only the threads that observed a counter fence; the block barrier then orders
+  // every thread of the block after them
+  if (threadIdx.x < nn) __threadfence();
   __syncthreads();
   return *s_fail == 0;
 }
