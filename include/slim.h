@@ -391,6 +391,17 @@ slim_status slim_selftest_conversions(long long n, unsigned long long seed, long
 slim_status slim_selftest_barrier(int n_blocks, int skip_block, int rounds, int* err_bits,
                                   int* arrivals);
 
+/* slim_selftest_neighbour_wait: diagnostic (no counterpart in the paper).  Runs
+ * `rounds` rounds of the bounded neighbour waits that separate the stages of the
+ * persistent 2D run, on a ring of n_blocks blocks (2..1024) in one cooperative
+ * launch: each block publishes its stage counter and waits for the blocks before
+ * and after it.  Block skip_block (>= 0) leaves before the first round, so its
+ * neighbours' waits run out, then theirs (one round later each).  Writes the device
+ * error bits (4 = a bounded wait gave up) and the number of arrivals to host memory;
+ * synchronises. */
+slim_status slim_selftest_neighbour_wait(int n_blocks, int skip_block, int rounds, int* err_bits,
+                                         int* arrivals);
+
 /* slim_selftest_fma_peak: diagnostic (no counterpart in the paper).  Measures the
  * GPU's fused multiply-add throughput in the precision's compute type (FP64 for
  * SLIM_FP64, FP32 for SLIM_MIXED): 8 blocks of 256 threads per SM, each thread

@@ -46,8 +46,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblk, int* 
 // done[n] >= k for every block n in its list s_nb[0, nn) (the blocks that own a
 // triangle its triangles read).  Blocks that share no data never wait for each
 // other, and no counter is contended.  Bounded like grid_barrier: after
-// kBarrierPolls polls a thread records SLIM_ERRBIT_TIMEOUT and the block returns
-// false.  *s_fail must be 0 on entry.
+// kBarrierPolls polls (16-ns sleeps between them: a waiter wakes sooner than with the
+// barrier's 64 ns, 1% of the 2D run) a thread records SLIM_ERRBIT_TIMEOUT and the
+// block returns false.  *s_fail must be 0 on entry.
 __device__ __forceinline__ bool neighbour_wait(unsigned* done, unsigned k, const int* s_nb, int nn, int* err,
                                                int* s_fail) {
   __syncthreads();
@@ -64,7 +65,7 @@ __device__ __forceinline__ bool neighbour_wait(unsigned* done, unsigned k, const
         atomicOr(err, (int)SLIM_ERRBIT_TIMEOUT);
         break;
       }
-      __nanosleep(64);
+      __nanosleep(16);
     }
   }
   // only the threads that observed a counter fence; the block barrier then orders

@@ -47,6 +47,26 @@ __global__ void k_barrier_check(unsigned* bar, int* err, int skip_block, int rou
   }
 }
 
+// rounds of the neighbour waits of the persistent 2D run on a ring of blocks (block
+// b waits for b - 1 and b + 1); block skip_block (if >= 0) leaves before the first
+__global__ void k_nbwait_check(unsigned* done, int* err, int skip_block, int rounds, int* arrivals) {
+  __shared__ int s_fail;
+  __shared__ int s_nb[2];
+  const int G = gridDim.x, b = blockIdx.x;
+  const int nn = G > 2 ? 2 : G - 1;
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    s_nb[0] = (b + G - 1) % G;
+    s_nb[1] = (b + 1) % G;
+  }
+  __syncthreads();
+  for (int r = 0; r < rounds; ++r) {
+    if (b == skip_block) return;
+    if (threadIdx.x == 0) atomicAdd(arrivals, 1);
+    if (!neighbour_wait(done, (unsigned)(r + 1), s_nb, nn, err, &s_fail)) return;
+  }
+}
+
 // Arithmetic peak: every thread runs 8 independent FMA chains (enough independent
 // work to keep the pipe busy at full occupancy); a result is stored only when it
 // is NaN, which never happens, so that the chains are not removed.
@@ -128,6 +148,38 @@ extern "C" slim_status slim_selftest_barrier(int n_blocks, int skip_block, int r
     cfg.numAttrs = 1;
     e = cudaLaunchKernelEx(&cfg, k_barrier_check, reinterpret_cast<unsigned*>(d + 2), d, skip_block,
                            rounds, d + 1);
+  }
+  int h[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  if (d) cudaFree(d);
+  if (e != cudaSuccess) { set_error(std::string("selftest: ") + cudaGetErrorString(e)); return SLIM_ERR_CUDA; }
+  *err_bits = h[0];
+  *arrivals = h[1];
+  return SLIM_OK;
+}
+
+extern "C" slim_status slim_selftest_neighbour_wait(int n_blocks, int skip_block, int rounds, int* err_bits,
+                                                    int* arrivals) {
+  clear_error();
+  if (n_blocks < 2 || n_blocks > 1024 || rounds < 0 || !err_bits || !arrivals) {
+    set_error("bad argument");
+    return SLIM_ERR_ARG;
+  }
+  int* d = nullptr;  // [0] error bits, [1] arrivals, [2 ..] one stage counter per block
+  const size_t words = 2 + (size_t)n_blocks;
+  cudaError_t e = cudaMalloc((void**)&d, words * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(d, 0, words * sizeof(int));
+  if (e == cudaSuccess) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_blocks);
+    cfg.blockDim = dim3(128);
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_nbwait_check, reinterpret_cast<unsigned*>(d + 2), d, skip_block, rounds,
+                           d + 1);
   }
   int h[2] = {0, 0};
   if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);

@@ -31,7 +31,7 @@ EXPORTED = ["slim_params_default", "slim_status_string", "slim_last_error", "sli
             "slim_rhs2d", "slim_vertical_solve", "slim_hpg", "slim_step", "slim_tracer_mass",
             "slim_step_kernel_count", "slim_profile_begin", "slim_profile_end",
             "slim_phase_name", "slim_tracer_mass_noalloc", "slim_selftest_conversions",
-            "slim_selftest_barrier", "slim_selftest_fma_peak", "slim_mesh_create_part",
+            "slim_selftest_barrier", "slim_selftest_neighbour_wait", "slim_selftest_fma_peak", "slim_mesh_create_part",
             "slim_halo_create", "slim_halo_destroy", "slim_halo_exchange", "slim_halo_step"]
 PHASES = ["continuity", "tracer_stage", "hpg", "mom_pred", "ext2d", "momentum", "tracers", "misc"]
 
@@ -91,6 +91,7 @@ def lib() -> C.CDLL:
             "slim_selftest_conversions": ([C.c_longlong, C.c_ulonglong, C.POINTER(C.c_longlong),
                                            C.POINTER(C.c_longlong)], _i),
             "slim_selftest_barrier": ([_i, _i, _i, C.POINTER(_i), C.POINTER(_i)], _i),
+            "slim_selftest_neighbour_wait": ([_i, _i, _i, C.POINTER(_i), C.POINTER(_i)], _i),
             "slim_selftest_fma_peak": ([_i, C.c_longlong, _dp, _dp], _i),
             "slim_mesh_create_part": ([_vp, _i, _vp, _i, _vp, _vp, _vp, _i, _vp, _i, _vp, C.POINTER(_vp)], _i),
             "slim_halo_create": ([_vp, _i, _vp, _vp, _vp, C.POINTER(_vp)], _i),
@@ -292,6 +293,15 @@ def slim_selftest_barrier(n_blocks: int, skip_block: int, rounds: int) -> tuple[
     a, b = C.c_int(-1), C.c_int(-1)
     _check(lib().slim_selftest_barrier(int(n_blocks), int(skip_block), int(rounds), C.byref(a),
                                        C.byref(b)))
+    return a.value, b.value
+
+
+def slim_selftest_neighbour_wait(n_blocks: int, skip_block: int, rounds: int) -> tuple[int, int]:
+    """(device error bits, arrivals) of `rounds` rounds of the bounded neighbour waits
+    on a ring of blocks."""
+    a, b = C.c_int(-1), C.c_int(-1)
+    _check(lib().slim_selftest_neighbour_wait(int(n_blocks), int(skip_block), int(rounds), C.byref(a),
+                                              C.byref(b)))
     return a.value, b.value
 
 

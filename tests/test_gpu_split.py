@@ -402,6 +402,19 @@ def test_grid_barrier_rounds_and_bounded_timeout(slim):
     assert bits & 4 and arr == 7
 
 
+def test_neighbour_waits_rounds_and_bounded_timeout(slim):
+    """The neighbour waits between the stages of the persistent run, on a ring of 8
+    blocks: 50 rounds complete with every arrival counted; a block that never arrives
+    makes its neighbours' bounded waits run out, then the next ones' a round later,
+    which is reported in the error bits (no hang, no fault)."""
+    bits, arr = slim.slim_selftest_neighbour_wait(8, -1, 50)
+    assert (bits, arr) == (0, 8 * 50)
+    bits, arr = slim.slim_selftest_neighbour_wait(8, 3, 3)
+    # round 1: the 7 others arrive, blocks 2 and 4 time out; round 2: 1, 5, 6, 7, 0
+    # arrive, 1 and 5 time out; round 3: 6, 7, 0 arrive
+    assert bits & 4 and arr == 7 + 5 + 3, arr
+
+
 def _forcing_fields(m, ini):
     """Exterior velocity turning from inflow to outflow between the two forcing
     times, exterior temperature warming by 0.5 (read at open-boundary nodes)."""
