@@ -1179,7 +1179,11 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
     const int p = tl.p0 + i;
     slot = i + lt;
     R F0[2][3] = {{0, 0, 0}, {0, 0, 0}}, F1[2][3] = {{0, 0, 0}, {0, 0, 0}}, qx[2][3], qy[2][3];
-    prism_adv<R, false>(m, t, k, p, N, own, in, F0, F1, qx, qy);
+    // tracers: advection and horizontal SIPG in one pass over the faces
+    if (KIND == 1 && ua.kap_h > (R)0)
+      prism_adv<R, false, true>(m, t, k, p, N, own, in, F0, F1, qx, qy, ua.kap_h, pp.pen_h);
+    else
+      prism_adv<R, false>(m, t, k, p, N, own, in, F0, F1, qx, qy);
     const R w6 = Geo<R>::jh(m, t) * (R)(1.0 / 6.0);
     if (KIND == 0) {
       // viscosity, Coriolis, -r/rho0 and drag of this state, from the prediction
@@ -1190,8 +1194,6 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
           F0[c][a] += Ex[(size_t)(c * 3 + a) * P + p];
           F1[c][a] += Ey[(size_t)(c * 3 + a) * P + p];
         }
-    } else if (ua.kap_h > (R)0) {
-      prism_sipg2<R>(m, t, k, N, own.f0, own.f1, in.F0, in.F1, in.st, ua.kap_h, pp.pen_h, F0, F1);
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {

@@ -89,15 +89,173 @@ __device__ __forceinline__ void adv_volume(const DevMesh& m, int t, const R qx[2
   }
 }
 
+// Horizontal SIPG of two fields on coordinate surfaces (weight nu z_zeta):
+//   -int nu z_zeta grad f . grad v + oint [{nu z_zeta grad f}.n v
+//                                          + 1/2 nu z_zeta^- grad v.n [f] - sigma {z_zeta}[f] v]
+// sigma = pen nu / min(r_in^-, r_in^+), interior faces only (natural elsewhere).
+// The two fields share the geometry: the layer thicknesses, the penalty and the
+// normal derivatives of both triangles' basis functions (the gradient of a P1
+// field dotted with n is the sum of its nodal values times those derivatives).
+// Volume part (hz: the prism's half layer thickness at its three vertices).
+template <typename R>
+__device__ __forceinline__ void sipg_volume2(const DevMesh& m, int t, const R hz[3], const R f0[2][3],
+                                             const R f1[2][3], R nu, R out0[2][3], R out1[2][3]) {
+  const int nt = m.n_tri;
+  R gx[3], gy[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    gx[a] = Geo<R>::gx(m, a * nt + t);
+    gy[a] = Geo<R>::gy(m, a * nt + t);
+  }
+  const R(*fs[2])[3] = {f0, f1};
+  R(*outs[2])[3] = {out0, out1};
+  // -nu (J_h/6)(sum hz) sum_d G_dc grad f_d . grad phi_a
+  const R w = nu * Geo<R>::jh(m, t) * (R)(1.0 / 6.0) * (hz[0] + hz[1] + hz[2]);
+  const R G2 = (R)(2.0 / 3.0), G1 = (R)(1.0 / 3.0);
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    R gux[2], guy[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      gux[c] = fs[q][c][0] * gx[0] + fs[q][c][1] * gx[1] + fs[q][c][2] * gx[2];
+      guy[c] = fs[q][c][0] * gy[0] + fs[q][c][1] * gy[1] + fs[q][c][2] * gy[2];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const R d0 = gux[0] * gx[a] + guy[0] * gy[a];
+      const R d1 = gux[1] * gx[a] + guy[1] * gy[a];
+      outs[q][0][a] -= w * (G2 * d0 + G1 * d1);
+      outs[q][1][a] -= w * (G1 * d0 + G2 * d1);
+    }
+  }
+}
+
+// Face part on lateral face e (own vertices a0 = e, a1 = e + 1) against neighbour
+// triangle nb (prism pn, its vertices l0, l1 on the face and l2 the third):
+// hzo / hzn the half thicknesses at the face vertices on both sides, fn0 / fn1 the
+// neighbour's values of the two fields at (l_j, level c), already loaded by the
+// caller (the advection reads the same values).
+template <typename R>
+__device__ __forceinline__ void sipg_face2(const DevMesh& m, int t, int e, int nb, int pn, int l0, int l1, R nxe,
+                                           R nye, R half_len, const R hzo[2], const R hzn[2],
+                                           const R f0[2][3], const R f1[2][3], const R fn0[2][2],
+                                           const R fn1[2][2], const R* __restrict__ F0,
+                                           const R* __restrict__ F1, R nu, R pen, R out0[2][3],
+                                           R out1[2][3]) {
+  const int nt = m.n_tri, P = m.P;
+  const int a0 = e, a1 = (e + 1) % 3, l2 = 3 - l0 - l1;
+  const R isig = (sizeof(R) == 4) ? (R)m.esig_f[e * nt + t] : (R)m.esig[e * nt + t];
+  R dno[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) dno[b] = Geo<R>::gx(m, b * nt + t) * nxe + Geo<R>::gy(m, b * nt + t) * nye;
+  const R dn0 = Geo<R>::gx(m, l0 * nt + nb) * nxe + Geo<R>::gy(m, l0 * nt + nb) * nye;
+  const R dn1 = Geo<R>::gx(m, l1 * nt + nb) * nxe + Geo<R>::gy(m, l1 * nt + nb) * nye;
+  const R dn2 = Geo<R>::gx(m, l2 * nt + nb) * nxe + Geo<R>::gy(m, l2 * nt + nb) * nye;
+  // The face integrals are polynomials of degree <= 3 per direction, integrated
+  // exactly in closed form: with the edge basis b_i and psi_c,
+  //   int b_i b_j = E2_ij (2/3, 1/3), int b_i b_j b_k = 1/2 (all equal) or 1/6,
+  //   int psi_d psi_c = G_dc (2/3, 1/3).
+  const R t3 = (R)(1.0 / 3.0), t6 = (R)(1.0 / 6.0);
+  const R Zo[2] = {t3 * ((R)2 * hzo[0] + hzo[1]), t3 * ((R)2 * hzo[1] + hzo[0])};
+  const R Zn[2] = {t3 * ((R)2 * hzn[0] + hzn[1]), t3 * ((R)2 * hzn[1] + hzn[0])};
+  const R hs0 = hzo[0] + hzn[0], hs1 = hzo[1] + hzn[1];
+  const R M00 = (R)0.5 * hs0 + t6 * hs1, M11 = (R)0.5 * hs1 + t6 * hs0, M01 = t6 * (hs0 + hs1);
+  const R hnu = half_len * (R)0.5 * nu;
+  const R hsig = half_len * (R)0.5 * pen * nu * isig;
+  const R(*fs[2])[3] = {f0, f1};
+  const R(*fns[2])[2] = {fn0, fn1};
+  const R* Fs[2] = {F0, F1};
+  R(*outs[2])[3] = {out0, out1};
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const R(*f)[3] = fs[q];
+    R gno[2], gnn[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const R fl2 = Fs[q][(size_t)(c * 3 + l2) * P + pn];
+      gno[c] = f[c][0] * dno[0] + f[c][1] * dno[1] + f[c][2] * dno[2];
+      gnn[c] = fns[q][0][c] * dn0 + fns[q][1][c] * dn1 + fl2 * dn2;
+    }
+    const R Go[2] = {t3 * ((R)2 * gno[0] + gno[1]), t3 * ((R)2 * gno[1] + gno[0])};
+    const R Gn[2] = {t3 * ((R)2 * gnn[0] + gnn[1]), t3 * ((R)2 * gnn[1] + gnn[0])};
+    // jumps at the face nodes (own vertex j <-> neighbour vertex l_j), G-weighted in zeta
+    R J[2][2], gJ[2][2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      J[0][c] = f[c][a0] - fns[q][0][c];
+      J[1][c] = f[c][a1] - fns[q][1][c];
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      gJ[i][0] = t3 * ((R)2 * J[i][0] + J[i][1]);
+      gJ[i][1] = t3 * ((R)2 * J[i][1] + J[i][0]);
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const R zj = hnu * (Zo[0] * gJ[0][c] + Zo[1] * gJ[1][c]);
+      // flux {nu z_zeta grad f}.n tested with the edge functions, minus the penalty
+      outs[q][c][a0] += hnu * (Zo[0] * Go[c] + Zn[0] * Gn[c]) - hsig * (M00 * gJ[0][c] + M01 * gJ[1][c]);
+      outs[q][c][a1] += hnu * (Zo[1] * Go[c] + Zn[1] * Gn[c]) - hsig * (M01 * gJ[0][c] + M11 * gJ[1][c]);
+      // symmetry term 1/2 nu z_zeta grad v.n [f] for every own test function
+#pragma unroll
+      for (int a = 0; a < 3; ++a) outs[q][c][a] += dno[a] * zj;
+    }
+  }
+}
+
+// Both parts, face by face with its own loads (when no advection pass shares them).
+template <typename R>
+__device__ __forceinline__ void prism_sipg2(const DevMesh& m, int t, int k, int N, const R f0[2][3],
+                                            const R f1[2][3], const R* __restrict__ F0,
+                                            const R* __restrict__ F1, const R* __restrict__ st,
+                                            R nu, R pen, R out0[2][3], R out1[2][3]) {
+  const int nt = m.n_tri, P = m.P;
+  R hz[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) hz[a] = (R)0.5 * dz_rest_r<R>(m, a * nt + t, k, N) * st[a * nt + t];
+  sipg_volume2<R>(m, t, hz, f0, f1, nu, out0, out1);
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int4 ei = m.einfo[e * nt + t];
+    const int nb = ei.x;
+    if (nb < 0) continue;
+    const int Nn = ei.z;
+    if (k >= Nn) continue;
+    const int pn = ei.y + k;
+    const int l0 = ei.w & 3, l1 = (ei.w >> 2) & 3;
+    const int a0 = e, a1 = (e + 1) % 3;
+    const R nxe = Geo<R>::nx(m, e * nt + t), nye = Geo<R>::ny(m, e * nt + t);
+    const R half_len = (R)0.5 * Geo<R>::len(m, e * nt + t);
+    const R hzo[2] = {hz[a0], hz[a1]};
+    const R hzn[2] = {(R)0.5 * dz_rest_r<R>(m, l0 * nt + nb, k, Nn) * st[l0 * nt + nb],
+                      (R)0.5 * dz_rest_r<R>(m, l1 * nt + nb, k, Nn) * st[l1 * nt + nb]};
+    R fn0[2][2], fn1[2][2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const size_t idx = (size_t)(c * 3 + (j ? l1 : l0)) * P + pn;
+        fn0[j][c] = F0[idx];
+        fn1[j][c] = F1[idx];
+      }
+    sipg_face2<R>(m, t, e, nb, pn, l0, l1, nxe, nye, half_len, hzo, hzn, f0, f1, fn0, fn1, F0, F1, nu, pen,
+                  out0, out1);
+  }
+}
+
 // Horizontal advection residual of two fields (NF = 2) or of T = 1 (UNIT) by the
 // transport q = (dz/2) u (+ the node correction (dz_rest/h)(Qbar - sum q)/2), with
 // the lateral normal transport {q}.n + (hz^- + hz^+)(s) gcor(s) on faces where a
 // face correction is given.  Accumulates into out0 / out1 and returns the nodal
 // transport of the prism in qxo / qyo.
-template <typename R, bool UNIT>
+// With SIPG, the horizontal SIPG of the two fields (viscosity nu, penalty pen) is
+// added in the same pass: its face part shares the face's geometry and the
+// neighbour's values with the advection.
+template <typename R, bool UNIT, bool SIPG = false>
 __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p, int N,
                                           const Own2<R>& own, const AdvIn<R>& in, R out0[2][3],
-                                          R out1[2][3], R qxo[2][3], R qyo[2][3]) {
+                                          R out1[2][3], R qxo[2][3], R qyo[2][3], R nu = 0,
+                                          R pen = 0) {
   const int nt = m.n_tri, P = m.P;
   R hz[3];
 #pragma unroll
@@ -123,6 +281,7 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
   } else {
     adv_volume<R>(m, t, qxo, qyo, own.f0, out0);
     adv_volume<R>(m, t, qxo, qyo, own.f1, out1);
+    if (SIPG) sipg_volume2<R>(m, t, hz, own.f0, own.f1, nu, out0, out1);
   }
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
@@ -143,12 +302,13 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
       }
     }
     bool has_nb = false, is_open = false;
+    int pn = 0, loc = 0;
     if (nb >= 0) {
       const int Nn = ei.z;
       if (k >= Nn) continue;  // wall against a shallower neighbour column
       has_nb = true;
-      const int pn = ei.y + k;
-      const int loc = ei.w;
+      pn = ei.y + k;
+      loc = ei.w;
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int l = j ? ((loc >> 2) & 3) : (loc & 3);
@@ -234,125 +394,10 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
         }
       }
     }
-  }
-}
-
-// Horizontal SIPG of two fields on coordinate surfaces (weight nu z_zeta):
-//   -int nu z_zeta grad f . grad v + oint [{nu z_zeta grad f}.n v
-//                                          + 1/2 nu z_zeta^- grad v.n [f] - sigma {z_zeta}[f] v]
-// sigma = pen nu / min(r_in^-, r_in^+), interior faces only (natural elsewhere).
-// The two fields share the geometry: the layer thicknesses, the penalty and the
-// normal derivatives of both triangles' basis functions (the gradient of a P1
-// field dotted with n is the sum of its nodal values times those derivatives).
-template <typename R>
-__device__ __forceinline__ void prism_sipg2(const DevMesh& m, int t, int k, int N, const R f0[2][3],
-                                            const R f1[2][3], const R* __restrict__ F0,
-                                            const R* __restrict__ F1, const R* __restrict__ st,
-                                            R nu, R pen, R out0[2][3], R out1[2][3]) {
-  const int nt = m.n_tri, P = m.P;
-  R gx[3], gy[3], hz[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    gx[a] = Geo<R>::gx(m, a * nt + t);
-    gy[a] = Geo<R>::gy(m, a * nt + t);
-    hz[a] = (R)0.5 * dz_rest_r<R>(m, a * nt + t, k, N) * st[a * nt + t];
-  }
-  const R(*fs[2])[3] = {f0, f1};
-  R(*outs[2])[3] = {out0, out1};
-  // volume: -nu (J_h/6)(sum hz) sum_d G_dc grad f_d . grad phi_a
-  {
-    const R w = nu * Geo<R>::jh(m, t) * (R)(1.0 / 6.0) * (hz[0] + hz[1] + hz[2]);
-    const R G2 = (R)(2.0 / 3.0), G1 = (R)(1.0 / 3.0);
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      R gux[2], guy[2];
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        gux[c] = fs[q][c][0] * gx[0] + fs[q][c][1] * gx[1] + fs[q][c][2] * gx[2];
-        guy[c] = fs[q][c][0] * gy[0] + fs[q][c][1] * gy[1] + fs[q][c][2] * gy[2];
-      }
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const R d0 = gux[0] * gx[a] + guy[0] * gy[a];
-        const R d1 = gux[1] * gx[a] + guy[1] * gy[a];
-        outs[q][0][a] -= w * (G2 * d0 + G1 * d1);
-        outs[q][1][a] -= w * (G1 * d0 + G2 * d1);
-      }
-    }
-  }
-  const R* Fs[2] = {F0, F1};
-#pragma unroll
-  for (int e = 0; e < 3; ++e) {
-    const int4 ei = m.einfo[e * nt + t];
-    const int nb = ei.x;
-    if (nb < 0) continue;
-    const int Nn = ei.z;
-    if (k >= Nn) continue;
-    const int pn = ei.y + k;
-    const int loc = ei.w;
-    const int l0 = loc & 3, l1 = (loc >> 2) & 3;
-    const int a0 = e, a1 = (e + 1) % 3;
-    const R nxe = Geo<R>::nx(m, e * nt + t), nye = Geo<R>::ny(m, e * nt + t);
-    const R half_len = (R)0.5 * Geo<R>::len(m, e * nt + t);
-    const R isig = (sizeof(R) == 4) ? (R)m.esig_f[e * nt + t] : (R)m.esig[e * nt + t];
-    R dno[3], dnn[3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      dno[b] = gx[b] * nxe + gy[b] * nye;
-      dnn[b] = Geo<R>::gx(m, b * nt + nb) * nxe + Geo<R>::gy(m, b * nt + nb) * nye;
-    }
-    const R hzn0 = (R)0.5 * dz_rest_r<R>(m, l0 * nt + nb, k, Nn) * st[l0 * nt + nb];
-    const R hzn1 = (R)0.5 * dz_rest_r<R>(m, l1 * nt + nb, k, Nn) * st[l1 * nt + nb];
-    // The face integrals are polynomials of degree <= 3 per direction, integrated
-    // exactly in closed form: with the edge basis b_i and psi_c,
-    //   int b_i b_j = E2_ij (2/3, 1/3), int b_i b_j b_k = 1/2 (all equal) or 1/6,
-    //   int psi_d psi_c = G_dc (2/3, 1/3).
-    const R t3 = (R)(1.0 / 3.0), t6 = (R)(1.0 / 6.0);
-    const R hzo[2] = {hz[a0], hz[a1]}, hzn[2] = {hzn0, hzn1};
-    const R Zo[2] = {t3 * ((R)2 * hzo[0] + hzo[1]), t3 * ((R)2 * hzo[1] + hzo[0])};
-    const R Zn[2] = {t3 * ((R)2 * hzn[0] + hzn[1]), t3 * ((R)2 * hzn[1] + hzn[0])};
-    const R hs0 = hzo[0] + hzn[0], hs1 = hzo[1] + hzn[1];
-    const R M00 = (R)0.5 * hs0 + t6 * hs1, M11 = (R)0.5 * hs1 + t6 * hs0, M01 = t6 * (hs0 + hs1);
-    const R hnu = half_len * (R)0.5 * nu;
-    const R hsig = half_len * (R)0.5 * pen * nu * isig;
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const R(*f)[3] = fs[q];
-      R fn[2][3];
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) fn[c][b] = Fs[q][(size_t)(c * 3 + b) * P + pn];
-      R gno[2], gnn[2];
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        gno[c] = f[c][0] * dno[0] + f[c][1] * dno[1] + f[c][2] * dno[2];
-        gnn[c] = fn[c][0] * dnn[0] + fn[c][1] * dnn[1] + fn[c][2] * dnn[2];
-      }
-      const R Go[2] = {t3 * ((R)2 * gno[0] + gno[1]), t3 * ((R)2 * gno[1] + gno[0])};
-      const R Gn[2] = {t3 * ((R)2 * gnn[0] + gnn[1]), t3 * ((R)2 * gnn[1] + gnn[0])};
-      // jumps at the face nodes (own vertex j <-> neighbour vertex l_j), G-weighted in zeta
-      R J[2][2], gJ[2][2];
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        J[0][c] = f[c][a0] - fn[c][l0];
-        J[1][c] = f[c][a1] - fn[c][l1];
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        gJ[i][0] = t3 * ((R)2 * J[i][0] + J[i][1]);
-        gJ[i][1] = t3 * ((R)2 * J[i][1] + J[i][0]);
-      }
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const R zj = hnu * (Zo[0] * gJ[0][c] + Zo[1] * gJ[1][c]);
-        // flux {nu z_zeta grad f}.n tested with the edge functions, minus the penalty
-        outs[q][c][a0] += hnu * (Zo[0] * Go[c] + Zn[0] * Gn[c]) - hsig * (M00 * gJ[0][c] + M01 * gJ[1][c]);
-        outs[q][c][a1] += hnu * (Zo[1] * Go[c] + Zn[1] * Gn[c]) - hsig * (M01 * gJ[0][c] + M11 * gJ[1][c]);
-        // symmetry term 1/2 nu z_zeta grad v.n [f] for every own test function
-#pragma unroll
-        for (int a = 0; a < 3; ++a) outs[q][c][a] += dno[a] * zj;
-      }
+    if (SIPG && !UNIT && has_nb) {
+      const R hzo[2] = {hz[a0], hz[a1]};
+      sipg_face2<R>(m, t, e, nb, pn, loc & 3, (loc >> 2) & 3, nxe, nye, half_len, hzo, hzb, own.f0, own.f1,
+                    fb0, fb1, in.F0 ? in.F0 : in.U, in.F1 ? in.F1 : in.V, nu, pen, out0, out1);
     }
   }
 }
