@@ -448,15 +448,17 @@ __device__ __forceinline__ void lumped(R w6hz, R f0, R f1, R& o0, R& o1) {
   o1 = w6hz * ((R)(1.0 / 3.0) * f0 + (R)(2.0 / 3.0) * f1);
 }
 
-// F_3D^h terms beyond advection: horizontal viscosity, Coriolis, -r/rho0, bed drag
-template <typename R>
+// F_3D^h terms beyond advection: horizontal viscosity (unless the advection pass
+// added it already: SIPG_DONE), Coriolis, -r/rho0, bed drag
+template <typename R, bool SIPG_DONE = false>
 __device__ __forceinline__ void momentum_extras(const DevMesh& m, int t, int k, int p, int N,
                                                 const Own2<R>& own, const R* __restrict__ U,
                                                 const R* __restrict__ V, const R* __restrict__ st,
                                                 const R* __restrict__ Rx, const R* __restrict__ Ry,
                                                 const PP<R>& pp, R Fx[2][3], R Fy[2][3]) {
   const int nt = m.n_tri, P = m.P;
-  if (pp.nu_h > (R)0) prism_sipg2<R>(m, t, k, N, own.u, own.v, U, V, st, pp.nu_h, pp.pen_h, Fx, Fy);
+  if (!SIPG_DONE && pp.nu_h > (R)0)
+    prism_sipg2<R>(m, t, k, N, own.u, own.v, U, V, st, pp.nu_h, pp.pen_h, Fx, Fy);
   const R f = pp.f, irho = pp.irho0;
   const R jh = Geo<R>::jh(m, t);
   const R w6 = jh * (R)(1.0 / 6.0);
@@ -529,10 +531,14 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
     const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
     const int p = tl.p0 + i, slot = i + lt;
     R Fx[2][3] = {{0, 0, 0}, {0, 0, 0}}, Fy[2][3] = {{0, 0, 0}, {0, 0, 0}}, qx[2][3], qy[2][3];
-    prism_adv<R, false>(m, t, k, p, N, own, in, Fx, Fy, qx, qy);
-    // the non-advective terms are the update's too (same state): kept for it
+    // the non-advective terms are the update's too (same state): kept for it; the
+    // horizontal viscosity is added in the advection's pass over the faces
     R ex[2][3] = {{0, 0, 0}, {0, 0, 0}}, ey[2][3] = {{0, 0, 0}, {0, 0, 0}};
-    momentum_extras<R>(m, t, k, p, N, own, in.U, in.V, in.st, Rx, Ry, pp, ex, ey);
+    if (pp.nu_h > (R)0)
+      prism_adv<R, false, true>(m, t, k, p, N, own, in, Fx, Fy, qx, qy, pp.nu_h, pp.pen_h, ex, ey);
+    else
+      prism_adv<R, false>(m, t, k, p, N, own, in, Fx, Fy, qx, qy);
+    momentum_extras<R, true>(m, t, k, p, N, own, in.U, in.V, in.st, Rx, Ry, pp, ex, ey);
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll

@@ -250,12 +250,15 @@ __device__ __forceinline__ void prism_sipg2(const DevMesh& m, int t, int k, int 
 // transport of the prism in qxo / qyo.
 // With SIPG, the horizontal SIPG of the two fields (viscosity nu, penalty pen) is
 // added in the same pass: its face part shares the face's geometry and the
-// neighbour's values with the advection.
+// neighbour's values with the advection.  It accumulates into sout0 / sout1 when
+// given (the momentum prediction keeps it apart), else into out0 / out1.
 template <typename R, bool UNIT, bool SIPG = false>
 __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p, int N,
                                           const Own2<R>& own, const AdvIn<R>& in, R out0[2][3],
                                           R out1[2][3], R qxo[2][3], R qyo[2][3], R nu = 0,
-                                          R pen = 0) {
+                                          R pen = 0, R (*sout0)[3] = nullptr, R (*sout1)[3] = nullptr) {
+  R(*so0)[3] = sout0 ? sout0 : out0;
+  R(*so1)[3] = sout1 ? sout1 : out1;
   const int nt = m.n_tri, P = m.P;
   R hz[3];
 #pragma unroll
@@ -281,7 +284,7 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
   } else {
     adv_volume<R>(m, t, qxo, qyo, own.f0, out0);
     adv_volume<R>(m, t, qxo, qyo, own.f1, out1);
-    if (SIPG) sipg_volume2<R>(m, t, hz, own.f0, own.f1, nu, out0, out1);
+    if (SIPG) sipg_volume2<R>(m, t, hz, own.f0, own.f1, nu, so0, so1);
   }
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
@@ -397,7 +400,7 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
     if (SIPG && !UNIT && has_nb) {
       const R hzo[2] = {hz[a0], hz[a1]};
       sipg_face2<R>(m, t, e, nb, pn, loc & 3, (loc >> 2) & 3, nxe, nye, half_len, hzo, hzb, own.f0, own.f1,
-                    fb0, fb1, in.F0 ? in.F0 : in.U, in.F1 ? in.F1 : in.V, nu, pen, out0, out1);
+                    fb0, fb1, in.F0 ? in.F0 : in.U, in.F1 ? in.F1 : in.V, nu, pen, so0, so1);
     }
   }
 }
