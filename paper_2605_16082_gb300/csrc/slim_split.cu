@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
     // horizontal viscosity is added in the advection's pass over the faces
     R ex[2][3] = {{0, 0, 0}, {0, 0, 0}}, ey[2][3] = {{0, 0, 0}, {0, 0, 0}};
     if (pp.nu_h > (R)0)
-      prism_adv<R, false, true>(m, t, k, p, N, own, in, Fx, Fy, qx, qy, pp.nu_h, pp.pen_h, ex, ey);
+      prism_adv<R, false, true, false>(m, t, k, p, N, own, in, Fx, Fy, qx, qy, pp.nu_h, pp.pen_h, ex, ey);
     else
       prism_adv<R, false>(m, t, k, p, N, own, in, Fx, Fy, qx, qy);
     momentum_extras<R, true>(m, t, k, p, N, own, in.U, in.V, in.st, Rx, Ry, pp, ex, ey);

@@ -58,8 +58,9 @@ __device__ __forceinline__ void load_own2(const DevMesh& m, int p, const AdvIn<R
 
 // Closed-form volume term of -div(q f) tested with phi_a psi_c (see prism_rh).
 template <typename R>
-__device__ __forceinline__ void adv_volume(const DevMesh& m, int t, const R qx[2][3], const R qy[2][3],
-                                           const R f[2][3], R out[2][3]) {
+__device__ __forceinline__ void adv_volume(const DevMesh& m, int t, const R gx[3], const R gy[3],
+                                           const R qx[2][3], const R qy[2][3], const R f[2][3],
+                                           R out[2][3]) {
   const int nt = m.n_tri;
   const R w24 = Geo<R>::jh(m, t) * (R)(1.0 / 24.0);
   R Yx[2][2], Yy[2][2];
@@ -83,9 +84,8 @@ __device__ __forceinline__ void adv_volume(const DevMesh& m, int t, const R qx[2
   const R Xy1 = h2 * Yy[1][1] + h6 * (Yy[0][0] + Yy[0][1] + Yy[1][0]);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const R gxa = Geo<R>::gx(m, a * nt + t), gya = Geo<R>::gy(m, a * nt + t);
-    out[0][a] += gxa * Xx0 + gya * Xy0;
-    out[1][a] += gxa * Xx1 + gya * Xy1;
+    out[0][a] += gx[a] * Xx0 + gy[a] * Xy0;
+    out[1][a] += gx[a] * Xx1 + gy[a] * Xy1;
   }
 }
 
@@ -98,15 +98,9 @@ __device__ __forceinline__ void adv_volume(const DevMesh& m, int t, const R qx[2
 // field dotted with n is the sum of its nodal values times those derivatives).
 // Volume part (hz: the prism's half layer thickness at its three vertices).
 template <typename R>
-__device__ __forceinline__ void sipg_volume2(const DevMesh& m, int t, const R hz[3], const R f0[2][3],
-                                             const R f1[2][3], R nu, R out0[2][3], R out1[2][3]) {
-  const int nt = m.n_tri;
-  R gx[3], gy[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    gx[a] = Geo<R>::gx(m, a * nt + t);
-    gy[a] = Geo<R>::gy(m, a * nt + t);
-  }
+__device__ __forceinline__ void sipg_volume2(const DevMesh& m, int t, const R gx[3], const R gy[3],
+                                             const R hz[3], const R f0[2][3], const R f1[2][3], R nu,
+                                             R out0[2][3], R out1[2][3]) {
   const R(*fs[2])[3] = {f0, f1};
   R(*outs[2])[3] = {out0, out1};
   // -nu (J_h/6)(sum hz) sum_d G_dc grad f_d . grad phi_a
@@ -137,7 +131,8 @@ __device__ __forceinline__ void sipg_volume2(const DevMesh& m, int t, const R hz
 // caller (the advection reads the same values).
 template <typename R>
 __device__ __forceinline__ void sipg_face2(const DevMesh& m, int t, int e, int nb, int pn, int l0, int l1, R nxe,
-                                           R nye, R half_len, const R hzo[2], const R hzn[2],
+                                           R nye, R half_len, const R gx[3], const R gy[3],
+                                           const R hzo[2], const R hzn[2],
                                            const R f0[2][3], const R f1[2][3], const R fn0[2][2],
                                            const R fn1[2][2], const R* __restrict__ F0,
                                            const R* __restrict__ F1, R nu, R pen, R out0[2][3],
@@ -147,7 +142,7 @@ __device__ __forceinline__ void sipg_face2(const DevMesh& m, int t, int e, int n
   const R isig = (sizeof(R) == 4) ? (R)m.esig_f[e * nt + t] : (R)m.esig[e * nt + t];
   R dno[3];
 #pragma unroll
-  for (int b = 0; b < 3; ++b) dno[b] = Geo<R>::gx(m, b * nt + t) * nxe + Geo<R>::gy(m, b * nt + t) * nye;
+  for (int b = 0; b < 3; ++b) dno[b] = gx[b] * nxe + gy[b] * nye;
   const R dn0 = Geo<R>::gx(m, l0 * nt + nb) * nxe + Geo<R>::gy(m, l0 * nt + nb) * nye;
   const R dn1 = Geo<R>::gx(m, l1 * nt + nb) * nxe + Geo<R>::gy(m, l1 * nt + nb) * nye;
   const R dn2 = Geo<R>::gx(m, l2 * nt + nb) * nxe + Geo<R>::gy(m, l2 * nt + nb) * nye;
@@ -210,10 +205,14 @@ __device__ __forceinline__ void prism_sipg2(const DevMesh& m, int t, int k, int 
                                             const R* __restrict__ F1, const R* __restrict__ st,
                                             R nu, R pen, R out0[2][3], R out1[2][3]) {
   const int nt = m.n_tri, P = m.P;
-  R hz[3];
+  R hz[3], gx[3], gy[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) hz[a] = (R)0.5 * dz_rest_r<R>(m, a * nt + t, k, N) * st[a * nt + t];
-  sipg_volume2<R>(m, t, hz, f0, f1, nu, out0, out1);
+  for (int a = 0; a < 3; ++a) {
+    hz[a] = (R)0.5 * dz_rest_r<R>(m, a * nt + t, k, N) * st[a * nt + t];
+    gx[a] = Geo<R>::gx(m, a * nt + t);
+    gy[a] = Geo<R>::gy(m, a * nt + t);
+  }
+  sipg_volume2<R>(m, t, gx, gy, hz, f0, f1, nu, out0, out1);
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     const int4 ei = m.einfo[e * nt + t];
@@ -238,8 +237,8 @@ __device__ __forceinline__ void prism_sipg2(const DevMesh& m, int t, int k, int 
         fn0[j][c] = F0[idx];
         fn1[j][c] = F1[idx];
       }
-    sipg_face2<R>(m, t, e, nb, pn, l0, l1, nxe, nye, half_len, hzo, hzn, f0, f1, fn0, fn1, F0, F1, nu, pen,
-                  out0, out1);
+    sipg_face2<R>(m, t, e, nb, pn, l0, l1, nxe, nye, half_len, gx, gy, hzo, hzn, f0, f1, fn0, fn1, F0, F1, nu,
+                  pen, out0, out1);
   }
 }
 
@@ -251,8 +250,10 @@ __device__ __forceinline__ void prism_sipg2(const DevMesh& m, int t, int k, int 
 // With SIPG, the horizontal SIPG of the two fields (viscosity nu, penalty pen) is
 // added in the same pass: its face part shares the face's geometry and the
 // neighbour's values with the advection.  It accumulates into sout0 / sout1 when
-// given (the momentum prediction keeps it apart), else into out0 / out1.
-template <typename R, bool UNIT, bool SIPG = false>
+// given (the momentum prediction keeps it apart), else into out0 / out1.  GKEEP:
+// the triangle's gradient coefficients stay in registers through the faces (fewer
+// loads; the momentum prediction, short of registers, re-reads them per face).
+template <typename R, bool UNIT, bool SIPG = false, bool GKEEP = true>
 __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p, int N,
                                           const Own2<R>& own, const AdvIn<R>& in, R out0[2][3],
                                           R out1[2][3], R qxo[2][3], R qyo[2][3], R nu = 0,
@@ -260,10 +261,12 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
   R(*so0)[3] = sout0 ? sout0 : out0;
   R(*so1)[3] = sout1 ? sout1 : out1;
   const int nt = m.n_tri, P = m.P;
-  R hz[3];
+  R hz[3], gxo[3], gyo[3];  // gradient coefficients of the triangle
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int ia = a * nt + t;
+    gxo[a] = Geo<R>::gx(m, ia);
+    gyo[a] = Geo<R>::gy(m, ia);
     const R dr = dz_rest_r<R>(m, ia, k, N);
     hz[a] = (R)0.5 * dr * in.st[ia];
     R cx = 0, cy = 0;
@@ -280,11 +283,11 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
   }
   if (UNIT) {
     R one[2][3] = {{1, 1, 1}, {1, 1, 1}};
-    adv_volume<R>(m, t, qxo, qyo, one, out0);
+    adv_volume<R>(m, t, gxo, gyo, qxo, qyo, one, out0);
   } else {
-    adv_volume<R>(m, t, qxo, qyo, own.f0, out0);
-    adv_volume<R>(m, t, qxo, qyo, own.f1, out1);
-    if (SIPG) sipg_volume2<R>(m, t, hz, own.f0, own.f1, nu, so0, so1);
+    adv_volume<R>(m, t, gxo, gyo, qxo, qyo, own.f0, out0);
+    adv_volume<R>(m, t, gxo, gyo, qxo, qyo, own.f1, out1);
+    if (SIPG) sipg_volume2<R>(m, t, gxo, gyo, hz, own.f0, own.f1, nu, so0, so1);
   }
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
@@ -399,8 +402,15 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
     }
     if (SIPG && !UNIT && has_nb) {
       const R hzo[2] = {hz[a0], hz[a1]};
-      sipg_face2<R>(m, t, e, nb, pn, loc & 3, (loc >> 2) & 3, nxe, nye, half_len, hzo, hzb, own.f0, own.f1,
-                    fb0, fb1, in.F0 ? in.F0 : in.U, in.F1 ? in.F1 : in.V, nu, pen, so0, so1);
+      if (!GKEEP) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          gxo[b] = Geo<R>::gx(m, b * nt + t);
+          gyo[b] = Geo<R>::gy(m, b * nt + t);
+        }
+      }
+      sipg_face2<R>(m, t, e, nb, pn, loc & 3, (loc >> 2) & 3, nxe, nye, half_len, gxo, gyo, hzo, hzb, own.f0,
+                    own.f1, fb0, fb1, in.F0 ? in.F0 : in.U, in.F1 ? in.F1 : in.V, nu, pen, so0, so1);
     }
   }
 }
