@@ -44,6 +44,9 @@ struct SplitBufs {
   // non-advective momentum terms (viscosity, Coriolis, -r/rho0, drag) of the stage's
   // evaluation state, [6][P] each: written by the prediction, read by the update
   void *Ex, *Ey;
+  // lateral normal transport of a stage at the face points, [12][P]: written by the
+  // continuity, read by the momentum and tracer updates of the same stage
+  void* qnf;
   // persistent 2D run: grid barrier words (arrival count, generation) and grid size;
   // the block graph of the run (bit n of row b: block n owns an edge neighbour of a
   // triangle of block b; nbw words per row, null when the grid is too large for the
@@ -1101,7 +1104,7 @@ __global__ void __launch_bounds__(TP, (MB<R, TP>::value))
     const int t = tl.t0 + lt, k = i - s_off[lt], N = s_off[lt + 1] - s_off[lt];
     slot = i + lt;
     R o[2][3] = {{0, 0, 0}, {0, 0, 0}}, dummy[2][3], qx[2][3], qy[2][3];
-    prism_adv<R, true>(m, t, k, tl.p0 + i, N, own, in, o, dummy, qx, qy);
+    prism_adv<R, true, false, true, 1>(m, t, k, tl.p0 + i, N, own, in, o, dummy, qx, qy);
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -1186,10 +1189,11 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
     slot = i + lt;
     R F0[2][3] = {{0, 0, 0}, {0, 0, 0}}, F1[2][3] = {{0, 0, 0}, {0, 0, 0}}, qx[2][3], qy[2][3];
     // tracers: advection and horizontal SIPG in one pass over the faces
+    // (the face transports come from the stage's continuity pass)
     if (KIND == 1 && ua.kap_h > (R)0)
-      prism_adv<R, false, true>(m, t, k, p, N, own, in, F0, F1, qx, qy, ua.kap_h, pp.pen_h);
+      prism_adv<R, false, true, true, 2>(m, t, k, p, N, own, in, F0, F1, qx, qy, ua.kap_h, pp.pen_h);
     else
-      prism_adv<R, false>(m, t, k, p, N, own, in, F0, F1, qx, qy);
+      prism_adv<R, false, false, true, 2>(m, t, k, p, N, own, in, F0, F1, qx, qy);
     const R w6 = Geo<R>::jh(m, t) * (R)(1.0 / 6.0);
     if (KIND == 0) {
       // viscosity, Coriolis, -r/rho0 and drag of this state, from the prediction
@@ -1563,8 +1567,12 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, int tide_base,
   AdvIn<R> cin{u_ev, v_ev, nullptr, nullptr, Uxa, Vxa, st_ev, (const R*)b->Dqx_r,
                (const R*)b->Dqy_r, (const R*)b->gcor_r, Uxa, Vxa, Uxb, Vxb, Uxb, Vxb, th_mid};
   {
+    // the continuity computes the face transports of the stage; the two updates read them
+    AdvIn<R> cin_w = cin;
+    cin_w.qn_out = (R*)b->qnf;
+    cin.qn_in = (const R*)b->qnf;
     ProfScope ps(s, SLIM_PHASE_CONTINUITY, stm);
-    SLIM_CU(launch_cont_split<R>(m, TP, cin, s->eta, b->Ae, dt, (R*)s->W, stm));
+    SLIM_CU(launch_cont_split<R>(m, TP, cin_w, s->eta, b->Ae, dt, (R*)s->W, stm));
   }
   const R* st0 = (const R*)s->st_cur;
   const R* st1 = (const R*)b->st_end;
@@ -1572,7 +1580,8 @@ slim_status stage(slim_state* s, double t0, double dt, int n_sub, int tide_base,
   UA<R> ut{(R)dt, (R)s->par.kappa_v, (R)s->par.kappa_h};
   AdvIn<R> tin{u_ev, v_ev, T_ev, S_ev, (const R*)s->Text, (const R*)s->Sext, st_ev,
                (const R*)b->Dqx_r, (const R*)b->Dqy_r, (const R*)b->gcor_r, Uxa, Vxa, Uxb, Vxb,
-               fx ? (const R*)s->Textb : nullptr, fx ? (const R*)s->Sextb : nullptr, th_mid};
+               fx ? (const R*)s->Textb : nullptr, fx ? (const R*)s->Sextb : nullptr, th_mid, nullptr,
+               (const R*)b->qnf};
   const R* U0 = (const R*)s->U;
   const R* V0 = (const R*)s->V;
   const R* T0 = (const R*)s->T;
@@ -1761,6 +1770,9 @@ slim_status split_alloc(slim_state* s) {
     SLIM_CU(cudaMemset(*p, 0, (size_t)6 * m.P * s->esz));
     s->allocs.push_back(*p);
   }
+  SLIM_CU(cudaMalloc(&b->qnf, (size_t)12 * m.P * s->esz));
+  SLIM_CU(cudaMemset(b->qnf, 0, (size_t)12 * m.P * s->esz));
+  s->allocs.push_back(b->qnf);
   SLIM_CU(cudaMalloc(&b->gcor_r, n2 * 2 * s->esz));
   SLIM_CU(cudaMemset(b->gcor_r, 0, n2 * 2 * s->esz));
   s->allocs.push_back(b->gcor_r);

@@ -29,6 +29,12 @@ struct AdvIn {
   const R* E0b;
   const R* E1b;
   const R* th;
+  // lateral normal transport at the 4 points of every face of every prism, [12][P]
+  // (face e, edge point gs, zeta point gz at row 4 e + 2 gs + gz): written by the
+  // pass that computes it (the continuity), read instead of recomputed by the later
+  // passes of the same stage over the same transport (null: none)
+  R* qn_out;
+  const R* qn_in;
 };
 
 template <typename R>
@@ -253,7 +259,10 @@ __device__ __forceinline__ void prism_sipg2(const DevMesh& m, int t, int k, int 
 // given (the momentum prediction keeps it apart), else into out0 / out1.  GKEEP:
 // the triangle's gradient coefficients stay in registers through the faces (fewer
 // loads; the momentum prediction, short of registers, re-reads them per face).
-template <typename R, bool UNIT, bool SIPG = false, bool GKEEP = true>
+// QN: 0 computes the lateral normal transport at the face points, 1 also stores it
+// in in.qn_out, 2 reads it from in.qn_in (computed by an earlier pass of the stage
+// over the same transport) instead of the neighbour's velocities and corrections.
+template <typename R, bool UNIT, bool SIPG = false, bool GKEEP = true, int QN = 0>
 __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p, int N,
                                           const Own2<R>& own, const AdvIn<R>& in, R out0[2][3],
                                           R out1[2][3], R qxo[2][3], R qyo[2][3], R nu = 0,
@@ -297,6 +306,7 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
     const int a0 = e, a1 = (e + 1) % 3;
     const R nxe = Geo<R>::nx(m, e * nt + t), nye = Geo<R>::ny(m, e * nt + t);
     const R half_len = (R)0.5 * Geo<R>::len(m, e * nt + t);
+    constexpr bool ql = QN == 2;  // the face transport is read, not recomputed
     R qo[2][2], qb[2][2], fo0[2][2], fo1[2][2], fb0[2][2], fb1[2][2], hzb[2] = {0, 0};
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
@@ -319,15 +329,18 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
       for (int j = 0; j < 2; ++j) {
         const int l = j ? ((loc >> 2) & 3) : (loc & 3);
         const int il = l * nt + nb;
-        const R dr = dz_rest_r<R>(m, il, k, Nn);
-        const R h = (R)0.5 * dr * in.st[il];
+        R dr = 0, h = 0;
+        if (!ql || SIPG) {
+          dr = dz_rest_r<R>(m, il, k, Nn);
+          h = (R)0.5 * dr * in.st[il];
+        }
         hzb[j] = h;
         R cn = 0;
-        if (in.Dqx) cn = (R)0.5 * dr * Geo<R>::ih(m, il) * (in.Dqx[il] * nxe + in.Dqy[il] * nye);
+        if (!ql && in.Dqx) cn = (R)0.5 * dr * Geo<R>::ih(m, il) * (in.Dqx[il] * nxe + in.Dqy[il] * nye);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const size_t idx = (size_t)(c * 3 + l) * P + pn;
-          qb[j][c] = h * (in.U[idx] * nxe + in.V[idx] * nye) + cn;
+          if (!ql) qb[j][c] = h * (in.U[idx] * nxe + in.V[idx] * nye) + cn;
           if (!UNIT) {
             fb0[j][c] = in.F0 ? in.F0[idx] : in.U[idx];
             fb1[j][c] = in.F1 ? in.F1[idx] : in.V[idx];
@@ -348,7 +361,8 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const size_t idx = (size_t)(c * 3 + la) * P + p;
-          if (in.Uxa) {
+          if (ql) {
+          } else if (in.Uxa) {
             const R ux = in.Uxa[idx] + th * (in.Uxb[idx] - in.Uxa[idx]);
             const R vx = in.Vxa[idx] + th * (in.Vxb[idx] - in.Vxa[idx]);
             qb[j][c] = hr * (ux * nxe + vx * nye);
@@ -363,7 +377,7 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
       }
     }
     R gc[2] = {0, 0};
-    if (in.gcor) {
+    if (!ql && in.gcor) {
       gc[0] = in.gcor[(e * nt + t) * 2 + 0];
       gc[1] = in.gcor[(e * nt + t) * 2 + 1];
     }
@@ -377,12 +391,19 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
         const R z0 = gz ? (R)SLIM_GL2 : (R)SLIM_GL1;  // psi_top at the zeta point
         const R z1 = gz ? (R)SLIM_GL1 : (R)SLIM_GL2;
         const R B00 = b0 * z0, B01 = b0 * z1, B10 = b1 * z0, B11 = b1 * z1;
-        const R qno = B00 * qo[0][0] + B01 * qo[0][1] + B10 * qo[1][0] + B11 * qo[1][1];
-        const R qnb = B00 * qb[0][0] + B01 * qb[0][1] + B10 * qb[1][0] + B11 * qb[1][1];
-        // (the prediction, without a face correction, keeps the uncorrected own
-        // transport at open faces: its estimate of the 2D flux there)
-        R qn = (is_open && in.gcor) ? qnb : (has_nb ? (R)0.5 * (qno + qnb) : qno);
-        qn += corr;
+        const size_t iq = (size_t)(e * 4 + gs * 2 + gz) * P + p;
+        R qn;
+        if (ql) {
+          qn = in.qn_in[iq];
+        } else {
+          const R qno = B00 * qo[0][0] + B01 * qo[0][1] + B10 * qo[1][0] + B11 * qo[1][1];
+          const R qnb = B00 * qb[0][0] + B01 * qb[0][1] + B10 * qb[1][0] + B11 * qb[1][1];
+          // (the prediction, without a face correction, keeps the uncorrected own
+          // transport at open faces: its estimate of the 2D flux there)
+          qn = (is_open && in.gcor) ? qnb : (has_nb ? (R)0.5 * (qno + qnb) : qno);
+          qn += corr;
+          if (QN == 1) in.qn_out[iq] = qn;
+        }
         if (UNIT) {
           const R f = half_len * qn;
           out0[0][a0] -= f * B00; out0[1][a0] -= f * B01;
