@@ -177,8 +177,8 @@ KERNEL_OF = {"split": {"continuity": "k_cont_split", "hpg": "k_hpg", "mom_pred":
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
 # capture, valid only while the kernel sources hash to ``src``; see profiles/.
 TRAFFIC = {
-    # quarter-size basin capture (4 instances, 188.8 MB per launch) scaled by the prisms
-    ("k_update", "mixed", "basin_baroclinic"): dict(bytes=748.8e6, src="e03742e18f179704"),
+    # quarter-size basin capture (4 instances, 232.8 MB per launch) scaled by the prisms
+    ("k_update", "mixed", "basin_baroclinic"): dict(bytes=923.3e6, src="ff01c35ba3a854ab"),
 }
 KSRC = ["paper_2605_16082_gb300/csrc/slim_split.cu", "paper_2605_16082_gb300/csrc/slim_split_device.cuh",
         "paper_2605_16082_gb300/csrc/slim_device.cuh", "paper_2605_16082_gb300/csrc/slim_tracer.cu",
@@ -231,7 +231,7 @@ def rooflines(r: dict, m, scheme: str, pname: str, workload: str, hbm: float, pe
 # valid only while the kernel sources hash to ``src``; see profiles/.
 FP64_FLOPS = {
     # quarter-size basin capture (2,344 FLOP per prism per launch) scaled by the prisms
-    ("k_update", "basin_baroclinic"): dict(flops_per_launch=9.2400e9, src="e03742e18f179704"),
+    ("k_update", "basin_baroclinic"): dict(flops_per_launch=7.8027e+00e9, src="ff01c35ba3a854ab"),
 }
 
 
