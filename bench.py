@@ -231,7 +231,7 @@ def rooflines(r: dict, m, scheme: str, pname: str, workload: str, hbm: float, pe
 # valid only while the kernel sources hash to ``src``; see profiles/.
 FP64_FLOPS = {
     # quarter-size basin capture (2,344 FLOP per prism per launch) scaled by the prisms
-    ("k_update", "basin_baroclinic"): dict(flops_per_launch=7.8027e+00e9, src="ff01c35ba3a854ab"),
+    ("k_update", "basin_baroclinic"): dict(flops_per_launch=7.8027e9, src="ff01c35ba3a854ab"),
 }
 
 
