@@ -542,6 +542,18 @@ __global__ void __launch_bounds__(TP, (MBO<R, TP, OCC>::value))
     else
       prism_adv<R, false>(m, t, k, p, N, own, in, Fx, Fy, qx, qy);
     momentum_extras<R, true>(m, t, k, p, N, own, in.U, in.V, in.st, Rx, Ry, pp, ex, ey);
+    // the nodal transport of the column sums, formed again (not held through the
+    // faces): q = hz u, the prediction's transport has no correction
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int ia = a * m.n_tri + t;
+      const R hza = (R)0.5 * dz_rest_r<R>(m, ia, k, N) * in.st[ia];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        qx[c][a] = hza * own.u[c][a];
+        qy[c][a] = hza * own.v[c][a];
+      }
+    }
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll

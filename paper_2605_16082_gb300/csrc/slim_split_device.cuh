@@ -257,8 +257,10 @@ __device__ __forceinline__ void prism_sipg2(const DevMesh& m, int t, int k, int 
 // added in the same pass: its face part shares the face's geometry and the
 // neighbour's values with the advection.  It accumulates into sout0 / sout1 when
 // given (the momentum prediction keeps it apart), else into out0 / out1.  GKEEP:
-// the triangle's gradient coefficients stay in registers through the faces (fewer
-// loads; the momentum prediction, short of registers, re-reads them per face).
+// the triangle's gradient coefficients and its nodal transport stay in registers
+// through the faces (fewer loads; the momentum prediction, short of registers,
+// re-reads the coefficients and forms the face's own transport again from the
+// velocities, so qxo / qyo are only valid up to the volume term there).
 // QN: 0 computes the lateral normal transport at the face points, 1 also stores it
 // in in.qn_out, 2 reads it from in.qn_in (computed by an earlier pass of the stage
 // over the same transport) instead of the neighbour's velocities and corrections.
@@ -310,8 +312,24 @@ __device__ __forceinline__ void prism_adv(const DevMesh& m, int t, int k, int p,
     R qo[2][2], qb[2][2], fo0[2][2], fo1[2][2], fb0[2][2], fb1[2][2], hzb[2] = {0, 0};
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      qo[0][c] = qxo[c][a0] * nxe + qyo[c][a0] * nye;
-      qo[1][c] = qxo[c][a1] * nxe + qyo[c][a1] * nye;
+      if (GKEEP) {
+        qo[0][c] = qxo[c][a0] * nxe + qyo[c][a0] * nye;
+        qo[1][c] = qxo[c][a1] * nxe + qyo[c][a1] * nye;
+      } else {
+        // the same products as qxo / qyo above, formed again
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int a = j ? a1 : a0;
+          R cx = 0, cy = 0;
+          if (in.Dqx) {
+            const int ia = a * nt + t;
+            const R f = (R)0.5 * dz_rest_r<R>(m, ia, k, N) * Geo<R>::ih(m, ia);
+            cx = f * in.Dqx[ia];
+            cy = f * in.Dqy[ia];
+          }
+          qo[j][c] = (hz[a] * own.u[c][a] + cx) * nxe + (hz[a] * own.v[c][a] + cy) * nye;
+        }
+      }
       if (!UNIT) {
         fo0[0][c] = own.f0[c][a0]; fo0[1][c] = own.f0[c][a1];
         fo1[0][c] = own.f1[c][a0]; fo1[1][c] = own.f1[c][a1];
