@@ -178,7 +178,7 @@ KERNEL_OF = {"split": {"continuity": "k_cont_split", "hpg": "k_hpg", "mom_pred":
 # capture, valid only while the kernel sources hash to ``src``; see profiles/.
 TRAFFIC = {
     # quarter-size basin capture (4 instances, 232.8 MB per launch) scaled by the prisms
-    ("k_update", "mixed", "basin_baroclinic"): dict(bytes=923.3e6, src="ff01c35ba3a854ab"),
+    ("k_update", "mixed", "basin_baroclinic"): dict(bytes=923.2e6, src="ab7ae483b3f24cea"),
 }
 KSRC = ["paper_2605_16082_gb300/csrc/slim_split.cu", "paper_2605_16082_gb300/csrc/slim_split_device.cuh",
         "paper_2605_16082_gb300/csrc/slim_device.cuh", "paper_2605_16082_gb300/csrc/slim_tracer.cu",
@@ -231,7 +231,7 @@ def rooflines(r: dict, m, scheme: str, pname: str, workload: str, hbm: float, pe
 # valid only while the kernel sources hash to ``src``; see profiles/.
 FP64_FLOPS = {
     # quarter-size basin capture (2,344 FLOP per prism per launch) scaled by the prisms
-    ("k_update", "basin_baroclinic"): dict(flops_per_launch=7.8027e9, src="ff01c35ba3a854ab"),
+    ("k_update", "basin_baroclinic"): dict(flops_per_launch=7.8027e9, src="ab7ae483b3f24cea"),
 }
 
 
